@@ -1,0 +1,201 @@
+/*
+ * polfmm -- polarizable fast multipole method on one GB300 GPU (sm_103a).
+ *
+ * C ABI of the hot path of Coles & Masella, "The Fast Multipole Method and
+ * Point Dipole Moment Polarizable Force Fields" (arXiv:1408.6527): the FMM
+ * evaluation of potential, field and field gradient produced by point charges
+ * plus induced point dipoles (Sec. II.B, II.C), called once per iteration of
+ * the self-consistent dipole solve mu_i = alpha_i (E^q_i + E^mu_i) (Sec. II.A,
+ * Eq. dipole moment) and once more for energy and forces (Sec. III, the three
+ * stages).
+ *
+ * Units and conventions (used by every call):
+ *   - lengths in Angstrom, charges in e, polarizabilities in Angstrom^3
+ *     (isotropic scalars, Sec. III); the field is computed with Coulomb
+ *     constant 1 so that mu = alpha E holds directly; energies, forces and
+ *     parameter gradients are multiplied by options.coulomb_k.
+ *   - positions, forces, dipoles and fields are n x 3 row-major float64
+ *     (AoS: x0 y0 z0 x1 ...); potentials, charges and gradients are n float64.
+ *   - field gradients are n x 6 float64 in the order xx xy xz yy yz zz.
+ *   - every per-site output is in the caller's site order.
+ *   - a pointer flagged "on_device" must be a device pointer valid on the
+ *     context's stream; otherwise it is host memory.  The library copies all
+ *     inputs into its own device buffers; the caller keeps ownership of every
+ *     pointer it passes and the library keeps none after a call returns.
+ *   - no call traps, aborts or prints; every int-returning call returns one
+ *     of the POLFMM_* status codes below.
+ *   - calls on one context must not overlap; distinct contexts are independent.
+ */
+#ifndef POLFMM_H
+#define POLFMM_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define POLFMM_API __attribute__((visibility("default")))
+#else
+#define POLFMM_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+#define POLFMM_OK 0
+#define POLFMM_ERR_INVALID_ARG 1   /* n < 1, p outside [1,10], depth outside [1,8], alpha < 0, non-finite input */
+#define POLFMM_ERR_COINCIDENT 2    /* two distinct sites at the same position */
+#define POLFMM_ERR_NOT_CONVERGED 3 /* dipole solve stopped at max_iter or diverged; dipoles stay readable */
+#define POLFMM_ERR_OUT_OF_MEMORY 4
+#define POLFMM_ERR_CUDA 5
+#define POLFMM_ERR_STATE 6         /* call out of order, e.g. energy before a solve */
+
+/* Precision of the FMM arithmetic.  FP64: everything in float64.  MIXED:
+ * expansions, translations and near-field pairs in float32 (the
+ * multipole-to-local translation on tensor cores), while the dipole solver
+ * vectors, its dot products and convergence test, and the energy sums stay in
+ * float64. */
+#define POLFMM_FP64 0
+#define POLFMM_MIXED 1
+
+/* Dipole solver. */
+#define POLFMM_SOLVER_PCG 0    /* conjugate gradients on (diag(1/alpha) - T) mu = E^q, Jacobi preconditioner */
+#define POLFMM_SOLVER_JACOBI 1 /* fixed point mu <- alpha (E^q + T mu) */
+
+/* Multipole-to-local implementation (MIXED only; FP64 always uses the SIMT kernel). */
+#define POLFMM_M2L_AUTO 0
+#define POLFMM_M2L_SIMT 1
+#define POLFMM_M2L_TENSOR 2
+
+typedef struct polfmm_ctx polfmm_ctx; /* opaque; owned by the library */
+
+typedef struct {
+    int mode;            /* POLFMM_FP64 or POLFMM_MIXED */
+    int solver;          /* POLFMM_SOLVER_* */
+    int max_iter;        /* dipole-solve iteration cap (default 100) */
+    double coulomb_k;    /* energy / force scale (default 1.0) */
+    int use_root_box;    /* 1: use root_lo / root_side instead of the bounding cube */
+    double root_lo[3];   /* lower corner of the root cube (Angstrom) */
+    double root_side;    /* side of the root cube (Angstrom) */
+    int m2l_impl;        /* POLFMM_M2L_* */
+    int profile;         /* 1: time kernels with CUDA events (see fmm_profile_get) */
+    void* cuda_stream;   /* cudaStream_t for all work; NULL = the legacy default stream */
+} polfmm_options;
+
+/* Fill *opt with the defaults: FP64, PCG, max_iter 100, coulomb_k 1, bounding
+ * root cube, automatic M2L choice, no profiling, default stream. */
+POLFMM_API void fmm_default_options(polfmm_options* opt);
+
+/*
+ * Build the octree and run the static pass (first stage of Sec. III).
+ *
+ * positions      n x 3 site positions.
+ * charges        n static charges q_i (Sec. II.A, Eq. equ:Uqq).
+ * polarizabilities n isotropic alpha_i >= 0; alpha_i = 0 marks a site without
+ *                an induced dipole.
+ * order_p        expansion order p in [1, 10]: terms with |n| + |m| <= p of the
+ *                two-centre Taylor expansion of Sec. II.B are kept.
+ * tree_depth     leaf level of the uniform octree in [1, 8] (root = level 0).
+ * opt            options (NULL = defaults).
+ * inputs_on_device 1 if the three arrays are device pointers.
+ *
+ * The root cube is the bounding box of the sites, centred, with side equal to
+ * the largest extent times (1 + 1e-6) (1 Angstrom if all coincide), unless
+ * opt->use_root_box.  A site's leaf is floor((x - lo) / h), h = side / 2^depth,
+ * clamped into the cube.  Boxes interact through multipoles when they are not
+ * adjacent but their parents are (or coincide); adjacent leaves interact
+ * directly.  On success *ctx owns all device state and the static field E^q
+ * and potential Phi^q of the charges are available.  On failure *ctx is NULL.
+ */
+POLFMM_API int fmm_build(polfmm_ctx** ctx, int64_t n, const double* positions, const double* charges,
+              const double* polarizabilities, int order_p, int tree_depth,
+              const polfmm_options* opt, int inputs_on_device);
+
+/*
+ * Solve mu_i = alpha_i (E^q_i + E^mu_i) (Sec. II.A, Eq. dipole moment; second
+ * stage of Sec. III) with the FMM dipole-field operator, starting from the
+ * previous dipoles if any (fmm_set_dipoles, fmm_update_positions), else from
+ * mu = alpha E^q.  Stops when ||r||_2 / ||E^q||_2 <= tolerance, r the residual
+ * of (diag(1/alpha) - T) mu = E^q, or after max_iter iterations.
+ * iterations_out / residual_out (nullable) receive the count and final
+ * relative residual.  Returns POLFMM_ERR_NOT_CONVERGED when the cap is hit or
+ * the residual turns non-finite; the dipoles stay readable.
+ */
+POLFMM_API int fmm_solve_induced_dipoles(polfmm_ctx* ctx, double tolerance, int* iterations_out,
+                              double* residual_out);
+
+/*
+ * Energy and gradients at the current dipoles (third stage of Sec. III).
+ * One FMM pass with charges and dipoles as sources gives the total potential
+ * Phi, field E and field gradient G at every site; then
+ *   energy_out[0] = U = U^qq' + U^pol, energy_out[1] = U^qq' = 1/2 sum q Phi^q,
+ *   energy_out[2] = U^pol = sum |mu|^2/(2 alpha) - sum mu.E^q - 1/2 sum mu.E^mu
+ *   (Sec. II.A), all host float64, times coulomb_k;
+ *   forces = -dU/dx = q E + (grad E) mu (n x 3), valid at a converged solve
+ *   because dU^pol/dmu = 0 (Eq. upol_derivatives);
+ *   dU_dq = Phi (total potential, n), dU_dalpha = -|mu|^2/(2 alpha^2) (n;
+ *   -|E|^2/2 where alpha = 0).
+ * forces, dU_dq, dU_dalpha are nullable.  Requires a prior
+ * fmm_solve_induced_dipoles or fmm_set_dipoles (else POLFMM_ERR_STATE).
+ */
+POLFMM_API int fmm_energy_forces(polfmm_ctx* ctx, double* energy_out, double* forces, double* dU_dq,
+                      double* dU_dalpha, int outputs_on_device);
+
+/* Copy the current induced dipoles (n x 3) out; POLFMM_ERR_STATE before any. */
+POLFMM_API int fmm_get_dipoles(polfmm_ctx* ctx, double* mu, int on_device);
+
+/* Set the induced dipoles (n x 3), e.g. a warm start or a fixed set for an
+ * energy evaluation; entries at sites with alpha = 0 are ignored (set to 0). */
+POLFMM_API int fmm_set_dipoles(polfmm_ctx* ctx, const double* mu, int on_device);
+
+/* New positions for the same sites: rebuild the tree and the static pass,
+ * keeping the current dipoles as the next solve's starting guess. */
+POLFMM_API int fmm_update_positions(polfmm_ctx* ctx, const double* positions, int on_device);
+
+/* Static potential Phi^q (n) and field E^q (n x 3) of the charges at every
+ * site, from the build's FMM pass (Sec. III, first stage).  Either nullable. */
+POLFMM_API int fmm_static_field(polfmm_ctx* ctx, double* phi, double* E, int on_device);
+
+/* One application of the FMM dipole-field operator: E = T mu, the field at
+ * every site of the point dipoles mu (n x 3) at the other sites (Sec. II.A,
+ * E^mu; Sec. II.C).  This is the matrix-vector product of every solver
+ * iteration. */
+POLFMM_API int fmm_dipole_field(polfmm_ctx* ctx, const double* mu, double* E, int on_device);
+
+/* One full FMM pass with the build's charges and the given dipoles mu (n x 3,
+ * nullable = none) as sources: total potential (n), field (n x 3) and field
+ * gradient (n x 6) at every site.  Outputs nullable. */
+POLFMM_API int fmm_total_field(polfmm_ctx* ctx, const double* mu, double* phi, double* E, double* G,
+                    int on_device);
+
+/* Leaf cell (integer coordinates in [0, 2^depth)^3, n x 3 int32) of every site. */
+POLFMM_API int fmm_leaf_cells(polfmm_ctx* ctx, int32_t* cells, int on_device);
+
+/* Tree summary: info[0] = depth, info[1] = p, info[2 + l] = occupied boxes at
+ * level l for l = 0..depth.  info must hold depth + 3 entries (at most 11). */
+POLFMM_API int fmm_tree_info(polfmm_ctx* ctx, int64_t* info);
+
+/* Root cube actually used: lo[3] and side. */
+POLFMM_API int fmm_root_box(polfmm_ctx* ctx, double* lo, double* side);
+
+/* Profiling (options.profile = 1): total CUDA-event milliseconds and launch
+ * count of one kernel family since the last reset.  Families: "tree", "p2m",
+ * "m2m", "m2l", "l2l", "leaf" (L2P + near field), "solver", "assemble".
+ * Unknown names return POLFMM_ERR_INVALID_ARG. */
+POLFMM_API int fmm_profile_get(polfmm_ctx* ctx, const char* family, double* total_ms, int64_t* launches);
+POLFMM_API int fmm_profile_reset(polfmm_ctx* ctx);
+
+/* Count of the library's own kernel launches on this context since creation. */
+POLFMM_API int64_t fmm_launch_count(polfmm_ctx* ctx);
+
+/* Release every device buffer of the context; NULL is a no-op. */
+POLFMM_API void fmm_destroy(polfmm_ctx* ctx);
+
+/* Static description of a status code. */
+POLFMM_API const char* fmm_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* POLFMM_H */

@@ -1,0 +1,778 @@
+// C ABI of the polfmm library (declared in include/polfmm.h): context
+// lifetime, the three calls of the paper's force procedure (Sec. III: static
+// pass in fmm_build, iterative dipoles in fmm_solve_induced_dipoles, energy
+// and forces in fmm_energy_forces), and the index / derivative tables.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "internal.cuh"
+
+namespace polfmm {
+int fmm_ops_init_attributes(polfmm_ctx* c);
+size_t m2l_simt_smem(int ncoef, size_t rsize);
+int m2l_tensor_prepare(polfmm_ctx* c);
+void m2l_tensor_release(polfmm_ctx* c);
+}  // namespace polfmm
+
+using namespace polfmm;
+
+// ---------------------------------------------------------------------------
+// launch bookkeeping and profiling
+// ---------------------------------------------------------------------------
+namespace polfmm {
+
+LaunchScope::LaunchScope(polfmm_ctx* ctx, int family) : c(ctx), fam(family), slot(-1) {
+    c->launches++;
+    if (c->opt.profile && c->ev_created) {
+        if (c->ev_used >= 4096) profile_flush(c);
+        slot = c->ev_used++;
+        c->ev_family[slot] = fam;
+        cudaEventRecord(c->ev_pool[2 * slot], c->stream);
+    }
+}
+
+LaunchScope::~LaunchScope() {
+    if (slot >= 0) cudaEventRecord(c->ev_pool[2 * slot + 1], c->stream);
+}
+
+void profile_flush(polfmm_ctx* c) {
+    if (!c->ev_created || c->ev_used == 0) return;
+    cudaStreamSynchronize(c->stream);
+    for (int s = 0; s < c->ev_used; s++) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, c->ev_pool[2 * s], c->ev_pool[2 * s + 1]) == cudaSuccess) {
+            c->prof_ms[c->ev_family[s]] += ms;
+            c->prof_n[c->ev_family[s]]++;
+        }
+    }
+    c->ev_used = 0;
+}
+
+}  // namespace polfmm
+
+// ---------------------------------------------------------------------------
+// tables
+// ---------------------------------------------------------------------------
+namespace {
+
+double factorial(int k) {
+    double f = 1.0;
+    for (int i = 2; i <= k; i++) f *= i;
+    return f;
+}
+
+struct HostMI {
+    int p, nc;
+    std::vector<int> nx, ny, nz, s;
+    std::vector<int> lut;  // (p+1)^3
+    explicit HostMI(int p_) : p(p_) {
+        nc = ncoef_of(p);
+        lut.assign((p + 1) * (p + 1) * (p + 1), -1);
+        for (int o = 0; o <= p; o++)
+            for (int x = o; x >= 0; x--)
+                for (int y = o - x; y >= 0; y--) {
+                    int z = o - x - y;
+                    lut[(x * (p + 1) + y) * (p + 1) + z] = (int)nx.size();
+                    nx.push_back(x);
+                    ny.push_back(y);
+                    nz.push_back(z);
+                    s.push_back(o);
+                }
+    }
+    int at(int x, int y, int z) const {
+        if (x < 0 || y < 0 || z < 0 || x + y + z > p) return -1;
+        return lut[(x * (p + 1) + y) * (p + 1) + z];
+    }
+};
+
+// d^n (1/r) at integer offsets for |n| <= p.  Recurrence from the Euler
+// identity of the degree -1 homogeneous function 1/r and its harmonicity:
+//   |n| r^2 a_n = -(2|n|-1) sum_d n_d R_d a_{n-e_d} - (|n|-1) sum_d n_d (n_d-1) a_{n-2e_d}
+void derivative_table(const HostMI& t, const double R[3], double* a) {
+    double r2 = R[0] * R[0] + R[1] * R[1] + R[2] * R[2];
+    a[0] = 1.0 / sqrt(r2);
+    for (int c = 1; c < t.nc; c++) {
+        int n[3] = {t.nx[c], t.ny[c], t.nz[c]};
+        int s = t.s[c];
+        double acc = 0.0;
+        for (int d = 0; d < 3; d++) {
+            int m[3] = {n[0], n[1], n[2]};
+            if (n[d] >= 1) {
+                m[d] = n[d] - 1;
+                acc += (2.0 * s - 1.0) * n[d] * R[d] * a[t.at(m[0], m[1], m[2])];
+            }
+            if (n[d] >= 2) {
+                m[d] = n[d] - 2;
+                acc += (s - 1.0) * n[d] * (n[d] - 1.0) * a[t.at(m[0], m[1], m[2])];
+            }
+        }
+        a[c] = -acc / (s * r2);
+    }
+}
+
+template <typename T>
+int upload(const std::vector<T>& h, T** d, cudaStream_t st) {
+    if (h.empty()) {
+        *d = nullptr;
+        return POLFMM_OK;
+    }
+    if (cudaMalloc(d, sizeof(T) * h.size()) != cudaSuccess) return POLFMM_ERR_OUT_OF_MEMORY;
+    if (cudaMemcpyAsync(*d, h.data(), sizeof(T) * h.size(), cudaMemcpyHostToDevice, st) != cudaSuccess)
+        return POLFMM_ERR_CUDA;
+    return cudaStreamSynchronize(st) == cudaSuccess ? POLFMM_OK : POLFMM_ERR_CUDA;
+}
+
+int build_tables(polfmm_ctx* c) {
+    const int p = c->p;
+    HostMI t(p);
+    Tables& T = c->tab;
+    T.p = p;
+    T.ncoef = t.nc;
+    T.ld = c->ld;
+    const int nc = t.nc;
+    std::vector<int> mi(nc), pre(nc), up1(3 * nc), up2(6 * nc);
+    std::vector<double> inv_fact(nc);
+    std::vector<float> inv_fact_f(nc);
+    std::vector<short> add((size_t)nc * nc, (short)-1);
+    static const int hd[6][2] = {{0, 0}, {0, 1}, {0, 2}, {1, 1}, {1, 2}, {2, 2}};
+    for (int k = 0; k < nc; k++) {
+        mi[k] = t.nx[k] | (t.ny[k] << 8) | (t.nz[k] << 16) | (t.s[k] << 24);
+        inv_fact[k] = 1.0 / (factorial(t.nx[k]) * factorial(t.ny[k]) * factorial(t.nz[k]));
+        inv_fact_f[k] = (float)inv_fact[k];
+        pre[k] = ncoef_of(p - t.s[k]);
+        for (int d = 0; d < 3; d++) {
+            int m[3] = {t.nx[k], t.ny[k], t.nz[k]};
+            m[d]++;
+            up1[3 * k + d] = t.at(m[0], m[1], m[2]);
+        }
+        for (int e = 0; e < 6; e++) {
+            int m[3] = {t.nx[k], t.ny[k], t.nz[k]};
+            m[hd[e][0]]++;
+            m[hd[e][1]]++;
+            up2[6 * k + e] = t.at(m[0], m[1], m[2]);
+        }
+        for (int j = 0; j < pre[k]; j++) add[(size_t)k * nc + j] = (short)t.at(t.nx[k] + t.nx[j], t.ny[k] + t.ny[j], t.nz[k] + t.nz[j]);
+    }
+    // shift operators
+    std::vector<int> m2m_ptr(nc + 1, 0), m2m_src, m2m_par, l2l_ptr(nc + 1, 0), l2l_src, l2l_par;
+    std::vector<double> m2m_w, l2l_w;
+    for (int k = 0; k < nc; k++) {
+        for (int kx = 0; kx <= t.nx[k]; kx++)
+            for (int ky = 0; ky <= t.ny[k]; ky++)
+                for (int kz = 0; kz <= t.nz[k]; kz++) {
+                    m2m_src.push_back(t.at(t.nx[k] - kx, t.ny[k] - ky, t.nz[k] - kz));
+                    m2m_par.push_back((kx & 1) | ((ky & 1) << 1) | ((kz & 1) << 2));
+                    int ks = kx + ky + kz;
+                    m2m_w.push_back(ldexp(1.0, -(t.s[k] + ks)) / (factorial(kx) * factorial(ky) * factorial(kz)));
+                }
+        m2m_ptr[k + 1] = (int)m2m_src.size();
+        for (int j = 0; j < nc; j++) {
+            if (t.s[j] > p - t.s[k]) continue;
+            l2l_src.push_back(t.at(t.nx[k] + t.nx[j], t.ny[k] + t.ny[j], t.nz[k] + t.nz[j]));
+            l2l_par.push_back((t.nx[j] & 1) | ((t.ny[j] & 1) << 1) | ((t.nz[j] & 1) << 2));
+            l2l_w.push_back(ldexp(1.0, -(t.s[k] + 1 + 2 * t.s[j])) /
+                            (factorial(t.nx[j]) * factorial(t.ny[j]) * factorial(t.nz[j])));
+        }
+        l2l_ptr[k + 1] = (int)l2l_src.size();
+    }
+    // derivative tables at the integer offsets of [-3, 3]^3
+    std::vector<double> D((size_t)343 * nc, 0.0);
+    std::vector<float> Df((size_t)343 * nc, 0.f);
+    for (int oz = -3; oz <= 3; oz++)
+        for (int oy = -3; oy <= 3; oy++)
+            for (int ox = -3; ox <= 3; ox++) {
+                if (!ox && !oy && !oz) continue;
+                int oi = (ox + 3) + 7 * ((oy + 3) + 7 * (oz + 3));
+                double R[3] = {(double)ox, (double)oy, (double)oz};
+                derivative_table(t, R, &D[(size_t)oi * nc]);
+                for (int k = 0; k < nc; k++) Df[(size_t)oi * nc + k] = (float)D[(size_t)oi * nc + k];
+            }
+    // interaction offsets per octant class: o = B - A with o_d in [b_d - 3, b_d + 2], not adjacent
+    std::vector<int> class_off(8 * kNumOffsets);
+    for (int cls = 0; cls < 8; cls++) {
+        int b[3] = {cls & 1, (cls >> 1) & 1, (cls >> 2) & 1};
+        int k = 0;
+        for (int oz = b[2] - 3; oz <= b[2] + 2; oz++)
+            for (int oy = b[1] - 3; oy <= b[1] + 2; oy++)
+                for (int ox = b[0] - 3; ox <= b[0] + 2; ox++) {
+                    if (std::max(abs(ox), std::max(abs(oy), abs(oz))) <= 1) continue;
+                    class_off[cls * kNumOffsets + k++] = (ox + 3) | ((oy + 3) << 4) | ((oz + 3) << 8);
+                }
+        if (k != kNumOffsets) return POLFMM_ERR_INVALID_ARG;
+    }
+    // balanced output lists for the 8 warps of the SIMT M2L kernel (longest first)
+    std::vector<int> order(nc);
+    for (int k = 0; k < nc; k++) order[k] = k;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return pre[a] > pre[b]; });
+    std::vector<std::vector<int>> lists(8);
+    std::vector<long> load(8, 0);
+    for (int k : order) {
+        int w = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+        lists[w].push_back(k);
+        load[w] += pre[k] + 4;
+    }
+    std::vector<int> wptr(9, 0), wout;
+    for (int w = 0; w < 8; w++) {
+        for (int k : lists[w]) wout.push_back(k);
+        wptr[w + 1] = (int)wout.size();
+    }
+    cudaStream_t st = c->stream;
+    int rc;
+#define UP(h, d) \
+    if ((rc = upload(h, &d, st)) != POLFMM_OK) return rc
+    UP(mi, T.mi);
+    UP(inv_fact, T.inv_fact);
+    UP(inv_fact_f, T.inv_fact_f);
+    UP(up1, T.up1);
+    UP(up2, T.up2);
+    UP(pre, T.pre);
+    UP(add, T.add);
+    UP(m2m_ptr, T.m2m_ptr);
+    UP(m2m_src, T.m2m_src);
+    UP(m2m_par, T.m2m_par);
+    UP(m2m_w, T.m2m_w);
+    UP(l2l_ptr, T.l2l_ptr);
+    UP(l2l_src, T.l2l_src);
+    UP(l2l_par, T.l2l_par);
+    UP(l2l_w, T.l2l_w);
+    UP(D, T.D);
+    UP(Df, T.Df);
+    UP(class_off, T.class_off);
+    UP(wptr, T.warp_out_ptr);
+    UP(wout, T.warp_out);
+#undef UP
+    T.h_mi = mi;
+    return POLFMM_OK;
+}
+
+void free_tables(Tables& T) {
+    void* ptrs[] = {T.mi, T.inv_fact, T.inv_fact_f, T.up1, T.up2, T.pre, T.add, T.m2m_ptr, T.m2m_src, T.m2m_par,
+                    T.m2m_w, T.l2l_ptr, T.l2l_src, T.l2l_par, T.l2l_w, T.D, T.Df, T.class_off, T.warp_out_ptr,
+                    T.warp_out};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    T = Tables();
+}
+
+// ---------------------------------------------------------------------------
+// allocation
+// ---------------------------------------------------------------------------
+struct Alloc {
+    std::vector<void*> ptrs;
+    bool ok = true;
+    template <typename T>
+    T* get(size_t count) {
+        if (!ok) return nullptr;
+        void* p = nullptr;
+        if (count == 0) count = 1;
+        if (cudaMalloc(&p, sizeof(T) * count) != cudaSuccess) {
+            cudaGetLastError();
+            ok = false;
+            return nullptr;
+        }
+        ptrs.push_back(p);
+        return (T*)p;
+    }
+};
+
+// device allocations owned by one context
+struct CtxExtra {
+    Alloc alloc;
+    std::vector<void*> lp_bufs;
+    size_t lp_cap_chunks = 0;
+};
+
+CtxExtra* extra_of(polfmm_ctx* c) { return reinterpret_cast<CtxExtra*>(c->extra); }
+
+int allocate(polfmm_ctx* c) {
+    Alloc& A = extra_of(c)->alloc;
+    const int64_t n = c->n;
+    const size_t rsz = c->mixed ? sizeof(float) : sizeof(double);
+    c->pos_s = A.get<double>(3 * n);
+    c->q_s = A.get<double>(n);
+    c->alpha_s = A.get<double>(n);
+    c->perm = A.get<int>(n);
+    c->key_s = A.get<uint32_t>(n);
+    c->ploc = A.get<unsigned char>(3 * n * rsz);
+    c->in_buf = A.get<double>(8 * n);
+    c->out_buf = A.get<double>(10 * n);
+    c->phiq = A.get<double>(n);
+    c->Eq = A.get<double>(3 * n);
+    c->mu = A.get<double>(3 * n);
+    c->r = A.get<double>(3 * n);
+    c->z = A.get<double>(3 * n);
+    c->d = A.get<double>(3 * n);
+    c->Ad = A.get<double>(3 * n);
+    c->Td = A.get<double>(3 * n);
+    c->phi_t = A.get<double>(n);
+    c->E_t = A.get<double>(3 * n);
+    c->G_t = A.get<double>(6 * n);
+    c->partial = A.get<double>((size_t)kRedSlots * kRedBlocks);
+    c->scal = A.get<double>(S_COUNT + 8);
+    c->err = A.get<int>(4);
+    c->key_tmp = A.get<uint32_t>(n);
+    c->val_tmp = A.get<int>(n);
+    c->val_a = A.get<int>(n);
+    c->flags = A.get<int>(n + 64);
+    c->counts_cap = tree_count_scratch(n);
+    c->counts = A.get<int>(c->counts_cap);
+    c->scan_tmp_cap = tree_scan_scratch(n);
+    c->scan_tmp = A.get<int>(c->scan_tmp_cap);
+    c->tree_cnt = A.get<int>((kMaxDepth + 1) * 9);
+    for (int l = 0; l <= c->depth; l++) {
+        Level& B = c->lv[l];
+        int64_t full = (int64_t)1 << (3 * l);
+        B.cap = (int)std::min<int64_t>(full, n);
+        B.key = A.get<int>(B.cap);
+        B.map = A.get<int>(full);
+        B.parent = A.get<int>(B.cap);
+        B.child0 = A.get<int>(B.cap);
+        B.nchild = A.get<int>(B.cap);
+        B.by_class = A.get<int>(B.cap);
+        B.M = A.get<unsigned char>((size_t)B.cap * c->ld * rsz);
+        B.L = A.get<unsigned char>((size_t)B.cap * c->ld * rsz);
+    }
+    c->lstart = A.get<int>(c->lv[c->depth].cap);
+    c->lcount = A.get<int>(c->lv[c->depth].cap);
+    if (!A.ok) return POLFMM_ERR_OUT_OF_MEMORY;
+    if (cudaMallocHost(&c->h_scal, sizeof(double) * (S_COUNT + 8)) != cudaSuccess) return POLFMM_ERR_OUT_OF_MEMORY;
+    if (cudaMallocHost(&c->h_counts, sizeof(int) * (kMaxDepth + 1) * 9) != cudaSuccess) return POLFMM_ERR_OUT_OF_MEMORY;
+    if (cudaMallocHost(&c->h_bbox, sizeof(double) * 8) != cudaSuccess) return POLFMM_ERR_OUT_OF_MEMORY;
+    cudaMemsetAsync(c->err, 0, sizeof(int) * 4, c->stream);
+    cudaMemsetAsync(c->scal, 0, sizeof(double) * (S_COUNT + 8), c->stream);
+    return POLFMM_OK;
+}
+
+// M2L partial-output buffers: chunks x cap x ld per level (grown on demand)
+int ensure_lp(polfmm_ctx* c) {
+    CtxExtra* X = extra_of(c);
+    if ((size_t)c->m2l_chunks <= X->lp_cap_chunks) return POLFMM_OK;
+    for (void* p : X->lp_bufs) cudaFree(p);
+    X->lp_bufs.clear();
+    const size_t rsz = c->mixed ? sizeof(float) : sizeof(double);
+    for (int l = 0; l <= c->depth; l++) {
+        void* p = nullptr;
+        size_t bytes = (size_t)c->m2l_chunks * c->lv[l].cap * c->ld * rsz;
+        if (cudaMalloc(&p, std::max<size_t>(bytes, 16)) != cudaSuccess) {
+            cudaGetLastError();
+            return POLFMM_ERR_OUT_OF_MEMORY;
+        }
+        X->lp_bufs.push_back(p);
+        c->lv[l].Lp = p;
+    }
+    X->lp_cap_chunks = c->m2l_chunks;
+    return POLFMM_OK;
+}
+
+int read_err(polfmm_ctx* c) {
+    int h[4] = {0, 0, 0, 0};
+    if (cudaMemcpyAsync(h, c->err, sizeof(int) * 4, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
+        return POLFMM_ERR_CUDA;
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return POLFMM_ERR_CUDA;
+    if (cudaGetLastError() != cudaSuccess) return POLFMM_ERR_CUDA;
+    if (h[0] & 1) return POLFMM_ERR_INVALID_ARG;
+    if (h[0] & 2) return POLFMM_ERR_COINCIDENT;
+    return POLFMM_OK;
+}
+
+int copy_in(polfmm_ctx* c, double* dst, const double* src, size_t count, int on_device) {
+    cudaError_t e = cudaMemcpyAsync(dst, src, sizeof(double) * count,
+                                    on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream);
+    return e == cudaSuccess ? POLFMM_OK : POLFMM_ERR_CUDA;
+}
+
+// sorted -> caller order, into a device pointer or through out_buf to the host
+int scatter_out(polfmm_ctx* c, const double* src_sorted, double* dst, int comps, int on_device) {
+    if (!dst) return POLFMM_OK;
+    if (on_device) {
+        scatter_sites(c, src_sorted, dst, comps);
+        return POLFMM_OK;
+    }
+    scatter_sites(c, src_sorted, c->out_buf, comps);
+    if (cudaMemcpyAsync(dst, c->out_buf, sizeof(double) * comps * c->n, cudaMemcpyDeviceToHost, c->stream) !=
+        cudaSuccess)
+        return POLFMM_ERR_CUDA;
+    return cudaStreamSynchronize(c->stream) == cudaSuccess ? POLFMM_OK : POLFMM_ERR_CUDA;
+}
+
+__global__ void leaf_cells_kernel(int64_t n, const uint32_t* __restrict__ key, const int* __restrict__ perm,
+                                  int32_t* __restrict__ out) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint32_t k = key[i];
+    int o = perm[i];
+    out[3 * (int64_t)o] = (int32_t)compact3(k);
+    out[3 * (int64_t)o + 1] = (int32_t)compact3(k >> 1);
+    out[3 * (int64_t)o + 2] = (int32_t)compact3(k >> 2);
+}
+
+// build the tree from caller-order inputs staged in in_buf and run the static pass
+int rebuild(polfmm_ctx* c) {
+    const int64_t n = c->n;
+    double* x_in = c->in_buf;
+    double* q_in = c->in_buf + 3 * n;
+    double* a_in = c->in_buf + 4 * n;
+    int rc;
+    if (c->opt.use_root_box) {
+        for (int d = 0; d < 3; d++) c->lo[d] = c->opt.root_lo[d];
+        c->side = c->opt.root_side;
+    } else if ((rc = tree_root_box(c, x_in, c->partial, c->h_bbox)) != POLFMM_OK) {
+        return rc;
+    }
+    if ((rc = tree_build(c, x_in)) != POLFMM_OK) return rc;
+    if ((rc = tree_tables(c, x_in, q_in, a_in)) != POLFMM_OK) return rc;
+    if ((rc = read_err(c)) != POLFMM_OK) return rc;
+    if ((rc = m2l_setup(c)) != POLFMM_OK) return rc;
+    if ((rc = ensure_lp(c)) != POLFMM_OK) return rc;
+    if ((rc = m2l_tensor_prepare(c)) != POLFMM_OK) return rc;
+    fmm_pass(c, LEAF_CHARGE_PHI_E, true, nullptr, c->phiq, c->Eq, nullptr);
+    return read_err(c);
+}
+
+void destroy_impl(polfmm_ctx* c) {
+    if (!c) return;
+    cudaStreamSynchronize(c->stream);
+    CtxExtra* X = extra_of(c);
+    if (X) {
+        for (void* p : X->alloc.ptrs) cudaFree(p);
+        for (void* p : X->lp_bufs) cudaFree(p);
+    }
+    m2l_tensor_release(c);
+    free_tables(c->tab);
+    if (c->tiles) cudaFree(c->tiles);
+    if (c->h_scal) cudaFreeHost(c->h_scal);
+    if (c->h_counts) cudaFreeHost(c->h_counts);
+    if (c->h_bbox) cudaFreeHost(c->h_bbox);
+    if (c->ev_created)
+        for (int i = 0; i < 2 * 4096; i++) cudaEventDestroy(c->ev_pool[i]);
+    delete X;
+    delete c;
+}
+
+bool finite_host(const double* v, size_t count) {
+    for (size_t i = 0; i < count; i++)
+        if (!isfinite(v[i])) return false;
+    return true;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+void fmm_default_options(polfmm_options* o) {
+    if (!o) return;
+    memset(o, 0, sizeof(*o));
+    o->mode = POLFMM_FP64;
+    o->solver = POLFMM_SOLVER_PCG;
+    o->max_iter = 100;
+    o->coulomb_k = 1.0;
+    o->m2l_impl = POLFMM_M2L_AUTO;
+}
+
+int fmm_build(polfmm_ctx** out, int64_t n, const double* positions, const double* charges,
+              const double* polarizabilities, int order_p, int tree_depth, const polfmm_options* opt,
+              int inputs_on_device) {
+    if (!out) return POLFMM_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (n < 1 || n > (int64_t)1 << 30 || !positions || !charges || !polarizabilities) return POLFMM_ERR_INVALID_ARG;
+    if (order_p < 1 || order_p > kMaxP || tree_depth < 1 || tree_depth > kMaxDepth) return POLFMM_ERR_INVALID_ARG;
+    polfmm_options o;
+    if (opt)
+        o = *opt;
+    else
+        fmm_default_options(&o);
+    if (o.mode != POLFMM_FP64 && o.mode != POLFMM_MIXED) return POLFMM_ERR_INVALID_ARG;
+    if (o.solver != POLFMM_SOLVER_PCG && o.solver != POLFMM_SOLVER_JACOBI) return POLFMM_ERR_INVALID_ARG;
+    if (o.max_iter < 0) return POLFMM_ERR_INVALID_ARG;
+    if (!(o.coulomb_k == o.coulomb_k) || !isfinite(o.coulomb_k)) return POLFMM_ERR_INVALID_ARG;
+    if (o.use_root_box && (!(o.root_side > 0.0) || !isfinite(o.root_side) || !finite_host(o.root_lo, 3)))
+        return POLFMM_ERR_INVALID_ARG;
+    if (!inputs_on_device) {
+        if (!finite_host(positions, 3 * (size_t)n) || !finite_host(charges, n) || !finite_host(polarizabilities, n))
+            return POLFMM_ERR_INVALID_ARG;
+        for (int64_t i = 0; i < n; i++)
+            if (polarizabilities[i] < 0.0) return POLFMM_ERR_INVALID_ARG;
+    }
+    polfmm_ctx* c = new (std::nothrow) polfmm_ctx();
+    if (!c) return POLFMM_ERR_OUT_OF_MEMORY;
+    c->extra = new (std::nothrow) CtxExtra();
+    if (!c->extra) {
+        delete c;
+        return POLFMM_ERR_OUT_OF_MEMORY;
+    }
+    c->opt = o;
+    c->n = n;
+    c->p = order_p;
+    c->depth = tree_depth;
+    c->ncoef = ncoef_of(order_p);
+    c->ld = (c->ncoef + 3) & ~3;
+    c->mixed = o.mode == POLFMM_MIXED;
+    c->stream = (cudaStream_t)o.cuda_stream;
+    int dev = 0, rc;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        destroy_impl(c);
+        return POLFMM_ERR_CUDA;
+    }
+    if (o.profile) {
+        for (int i = 0; i < 2 * 4096; i++) cudaEventCreate(&c->ev_pool[i]);
+        c->ev_created = true;
+    }
+    if ((rc = allocate(c)) != POLFMM_OK || (rc = build_tables(c)) != POLFMM_OK ||
+        (rc = fmm_ops_init_attributes(c)) != POLFMM_OK) {
+        destroy_impl(c);
+        return rc;
+    }
+    if ((rc = copy_in(c, c->in_buf, positions, 3 * (size_t)n, inputs_on_device)) != POLFMM_OK ||
+        (rc = copy_in(c, c->in_buf + 3 * n, charges, n, inputs_on_device)) != POLFMM_OK ||
+        (rc = copy_in(c, c->in_buf + 4 * n, polarizabilities, n, inputs_on_device)) != POLFMM_OK ||
+        (rc = rebuild(c)) != POLFMM_OK) {
+        destroy_impl(c);
+        return rc;
+    }
+    *out = c;
+    return POLFMM_OK;
+}
+
+int fmm_solve_induced_dipoles(polfmm_ctx* c, double tol, int* iters_out, double* res_out) {
+    if (!c || !(tol >= 0.0)) return POLFMM_ERR_INVALID_ARG;
+    const bool jacobi = c->opt.solver == POLFMM_SOLVER_JACOBI;
+    solver_init(c, c->have_mu);
+    c->have_mu = true;
+    int it = 0;
+    double res = 0.0;
+    int status = POLFMM_OK;
+    auto fetch = [&](void) -> int {
+        if (cudaMemcpyAsync(c->h_scal, c->scal, sizeof(double) * S_COUNT, cudaMemcpyDeviceToHost, c->stream) !=
+            cudaSuccess)
+            return POLFMM_ERR_CUDA;
+        return cudaStreamSynchronize(c->stream) == cudaSuccess ? POLFMM_OK : POLFMM_ERR_CUDA;
+    };
+    int rc;
+    if ((rc = fetch()) != POLFMM_OK) return rc;
+    const double bb = c->h_scal[S_BB];
+    if (!(bb > 0.0)) {
+        // no field at any polarizable site: the dipoles vanish
+        cudaMemsetAsync(c->mu, 0, sizeof(double) * 3 * c->n, c->stream);
+        if (iters_out) *iters_out = 0;
+        if (res_out) *res_out = 0.0;
+        return read_err(c);
+    }
+    if (!jacobi) {
+        res = sqrt(c->h_scal[S_RR] / bb);
+        while (res > tol && it < c->opt.max_iter) {
+            solver_pcg_step(c);
+            it++;
+            if ((rc = fetch()) != POLFMM_OK) return rc;
+            if (!(c->h_scal[S_DAD] > 0.0)) {  // operator not positive definite (polarization catastrophe)
+                res = sqrt(fabs(c->h_scal[S_RR] / bb));
+                status = POLFMM_ERR_NOT_CONVERGED;
+                break;
+            }
+            res = sqrt(c->h_scal[S_RR] / bb);
+            if (!isfinite(res)) {
+                status = POLFMM_ERR_NOT_CONVERGED;
+                break;
+            }
+        }
+    } else {
+        res = INFINITY;
+        while (it < c->opt.max_iter) {
+            solver_jacobi_step(c);
+            it++;
+            if ((rc = fetch()) != POLFMM_OK) return rc;
+            res = sqrt(c->h_scal[S_RR] / bb);
+            if (!isfinite(res)) {
+                status = POLFMM_ERR_NOT_CONVERGED;
+                break;
+            }
+            if (res <= tol) break;
+        }
+    }
+    if (status == POLFMM_OK && res > tol) status = POLFMM_ERR_NOT_CONVERGED;
+    if (iters_out) *iters_out = it;
+    if (res_out) *res_out = res;
+    rc = read_err(c);
+    return rc != POLFMM_OK ? rc : status;
+}
+
+int fmm_energy_forces(polfmm_ctx* c, double* energy_out, double* forces, double* dU_dq, double* dU_dalpha,
+                      int on_device) {
+    if (!c) return POLFMM_ERR_INVALID_ARG;
+    if (!c->have_mu) return POLFMM_ERR_STATE;
+    const int64_t n = c->n;
+    fmm_pass(c, LEAF_FULL, true, c->mu, c->phi_t, c->E_t, c->G_t);
+    double* F = forces;
+    double* dq = dU_dq;
+    double* da = dU_dalpha;
+    if (!on_device) {
+        F = forces ? c->out_buf : nullptr;
+        dq = dU_dq ? c->out_buf + 3 * n : nullptr;
+        da = dU_dalpha ? c->out_buf + 4 * n : nullptr;
+    }
+    energy_and_gradients(c, F, dq, da, F != nullptr, dq != nullptr, da != nullptr);
+    cudaMemcpyAsync(c->h_scal, c->scal, sizeof(double) * S_COUNT, cudaMemcpyDeviceToHost, c->stream);
+    if (!on_device) {
+        if (forces) cudaMemcpyAsync(forces, F, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, c->stream);
+        if (dU_dq) cudaMemcpyAsync(dU_dq, dq, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream);
+        if (dU_dalpha) cudaMemcpyAsync(dU_dalpha, da, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream);
+    }
+    int rc = read_err(c);
+    if (rc != POLFMM_OK) return rc;
+    const double k = c->opt.coulomb_k;
+    const double uqq = k * c->h_scal[S_UQQ];
+    const double upol = k * (c->h_scal[S_AMU] - c->h_scal[S_MUEQ] - 0.5 * c->h_scal[S_MUEMU]);
+    if (energy_out) {
+        energy_out[0] = uqq + upol;
+        energy_out[1] = uqq;
+        energy_out[2] = upol;
+    }
+    return POLFMM_OK;
+}
+
+int fmm_get_dipoles(polfmm_ctx* c, double* mu, int on_device) {
+    if (!c || !mu) return POLFMM_ERR_INVALID_ARG;
+    if (!c->have_mu) return POLFMM_ERR_STATE;
+    int rc = scatter_out(c, c->mu, mu, 3, on_device);
+    return rc != POLFMM_OK ? rc : read_err(c);
+}
+
+int fmm_set_dipoles(polfmm_ctx* c, const double* mu, int on_device) {
+    if (!c || !mu) return POLFMM_ERR_INVALID_ARG;
+    if (!on_device && !finite_host(mu, 3 * (size_t)c->n)) return POLFMM_ERR_INVALID_ARG;
+    int rc = copy_in(c, c->in_buf + 5 * c->n, mu, 3 * (size_t)c->n, on_device);
+    if (rc != POLFMM_OK) return rc;
+    gather_sites(c, c->in_buf + 5 * c->n, c->mu, 3);
+    mask_dipoles(c, c->mu);
+    c->have_mu = true;
+    return read_err(c);
+}
+
+int fmm_update_positions(polfmm_ctx* c, const double* positions, int on_device) {
+    if (!c || !positions) return POLFMM_ERR_INVALID_ARG;
+    const int64_t n = c->n;
+    if (!on_device && !finite_host(positions, 3 * (size_t)n)) return POLFMM_ERR_INVALID_ARG;
+    // current q, alpha and dipoles back to caller order, then the new positions
+    scatter_sites(c, c->q_s, c->in_buf + 3 * n, 1);
+    scatter_sites(c, c->alpha_s, c->in_buf + 4 * n, 1);
+    if (c->have_mu) scatter_sites(c, c->mu, c->in_buf + 5 * n, 3);
+    int rc = copy_in(c, c->in_buf, positions, 3 * (size_t)n, on_device);
+    if (rc != POLFMM_OK) return rc;
+    if ((rc = rebuild(c)) != POLFMM_OK) return rc;
+    if (c->have_mu) {
+        gather_sites(c, c->in_buf + 5 * n, c->mu, 3);
+        mask_dipoles(c, c->mu);
+    }
+    return read_err(c);
+}
+
+int fmm_static_field(polfmm_ctx* c, double* phi, double* E, int on_device) {
+    if (!c) return POLFMM_ERR_INVALID_ARG;
+    int rc = scatter_out(c, c->phiq, phi, 1, on_device);
+    if (rc == POLFMM_OK) rc = scatter_out(c, c->Eq, E, 3, on_device);
+    return rc != POLFMM_OK ? rc : read_err(c);
+}
+
+int fmm_dipole_field(polfmm_ctx* c, const double* mu, double* E, int on_device) {
+    if (!c || !mu || !E) return POLFMM_ERR_INVALID_ARG;
+    int rc = copy_in(c, c->in_buf + 5 * c->n, mu, 3 * (size_t)c->n, on_device);
+    if (rc != POLFMM_OK) return rc;
+    gather_sites(c, c->in_buf + 5 * c->n, c->d, 3);
+    fmm_pass(c, LEAF_DIPOLE_E, false, c->d, nullptr, c->Td, nullptr);
+    rc = scatter_out(c, c->Td, E, 3, on_device);
+    return rc != POLFMM_OK ? rc : read_err(c);
+}
+
+int fmm_total_field(polfmm_ctx* c, const double* mu, double* phi, double* E, double* G, int on_device) {
+    if (!c) return POLFMM_ERR_INVALID_ARG;
+    int rc;
+    if (mu) {
+        if ((rc = copy_in(c, c->in_buf + 5 * c->n, mu, 3 * (size_t)c->n, on_device)) != POLFMM_OK) return rc;
+        gather_sites(c, c->in_buf + 5 * c->n, c->d, 3);
+    } else {
+        cudaMemsetAsync(c->d, 0, sizeof(double) * 3 * c->n, c->stream);
+    }
+    fmm_pass(c, LEAF_FULL, true, c->d, c->phi_t, c->E_t, c->G_t);
+    if ((rc = scatter_out(c, c->phi_t, phi, 1, on_device)) != POLFMM_OK) return rc;
+    if ((rc = scatter_out(c, c->E_t, E, 3, on_device)) != POLFMM_OK) return rc;
+    if ((rc = scatter_out(c, c->G_t, G, 6, on_device)) != POLFMM_OK) return rc;
+    return read_err(c);
+}
+
+int fmm_leaf_cells(polfmm_ctx* c, int32_t* cells, int on_device) {
+    if (!c || !cells) return POLFMM_ERR_INVALID_ARG;
+    int32_t* dst = on_device ? cells : (int32_t*)c->out_buf;
+    {
+        LaunchScope ls(c, F_TREE);
+        leaf_cells_kernel<<<grid_for(c->n, 256), 256, 0, c->stream>>>(c->n, c->key_s, c->perm, dst);
+    }
+    if (!on_device &&
+        cudaMemcpyAsync(cells, dst, sizeof(int32_t) * 3 * c->n, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
+        return POLFMM_ERR_CUDA;
+    return read_err(c);
+}
+
+int fmm_tree_info(polfmm_ctx* c, int64_t* info) {
+    if (!c || !info) return POLFMM_ERR_INVALID_ARG;
+    info[0] = c->depth;
+    info[1] = c->p;
+    for (int l = 0; l <= c->depth; l++) info[2 + l] = c->lv[l].nbox;
+    return POLFMM_OK;
+}
+
+int fmm_root_box(polfmm_ctx* c, double* lo, double* side) {
+    if (!c || !lo || !side) return POLFMM_ERR_INVALID_ARG;
+    for (int d = 0; d < 3; d++) lo[d] = c->lo[d];
+    *side = c->side;
+    return POLFMM_OK;
+}
+
+int fmm_profile_get(polfmm_ctx* c, const char* family, double* total_ms, int64_t* launches) {
+    static const char* names[F_COUNT] = {"tree", "p2m", "m2m", "m2l", "l2l", "leaf", "solver", "assemble"};
+    if (!c || !family) return POLFMM_ERR_INVALID_ARG;
+    profile_flush(c);
+    for (int f = 0; f < F_COUNT; f++)
+        if (!strcmp(family, names[f])) {
+            if (total_ms) *total_ms = c->prof_ms[f];
+            if (launches) *launches = c->prof_n[f];
+            return POLFMM_OK;
+        }
+    return POLFMM_ERR_INVALID_ARG;
+}
+
+int fmm_profile_reset(polfmm_ctx* c) {
+    if (!c) return POLFMM_ERR_INVALID_ARG;
+    profile_flush(c);
+    for (int f = 0; f < F_COUNT; f++) {
+        c->prof_ms[f] = 0;
+        c->prof_n[f] = 0;
+    }
+    return POLFMM_OK;
+}
+
+int64_t fmm_launch_count(polfmm_ctx* c) { return c ? c->launches : 0; }
+
+void fmm_destroy(polfmm_ctx* c) { destroy_impl(c); }
+
+const char* fmm_status_string(int s) {
+    switch (s) {
+        case POLFMM_OK: return "ok";
+        case POLFMM_ERR_INVALID_ARG: return "invalid argument";
+        case POLFMM_ERR_COINCIDENT: return "coincident sites";
+        case POLFMM_ERR_NOT_CONVERGED: return "dipole solve not converged";
+        case POLFMM_ERR_OUT_OF_MEMORY: return "out of device memory";
+        case POLFMM_ERR_CUDA: return "CUDA error";
+        case POLFMM_ERR_STATE: return "call out of order";
+        default: return "unknown status";
+    }
+}
+
+}  // extern "C"

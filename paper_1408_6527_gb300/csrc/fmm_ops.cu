@@ -1,0 +1,587 @@
+// FMM operators on the GPU (Sec. II.B, II.C of Coles & Masella), in
+// normalised Cartesian coefficients (m_n = M_n / h^|n|, f_n = F_n h^(|n|+1),
+// h the box side of the level), templated on the arithmetic type R
+// (double: FP64 mode, float: MIXED mode).
+//
+//   P2M   multipoles of the charges and point dipoles of each leaf
+//         (Eq. multipole; a point dipole is the dl -> 0 limit of the +-q pair
+//         of Sec. II.C, i.e. the derivative of a charge's multipole)
+//   M2M   children -> parent shift (k <= n componentwise)
+//   M2L   multipole -> local for the 189 well-separated offsets of each
+//         octant class, grouped so that every thread of a warp applies the
+//         same derivative table D_o (SIMT kernel here; the tensor-core kernel
+//         is in m2l_tc.cu)
+//   L2L   parent -> child shift (|k| <= p - |n|), plus the M2L partial sums
+//   leaf  L2P evaluation of potential / field / field gradient fused with
+//         the near-field pair sums over the 27 adjacent leaves
+//         (Phi = Phi^direct + Phi^fmm, Sec. III)
+#include <algorithm>
+
+#include "internal.cuh"
+
+namespace polfmm {
+
+__device__ inline void decode_mi(int packed, int& nx, int& ny, int& nz) {
+    nx = packed & 0xff;
+    ny = (packed >> 8) & 0xff;
+    nz = (packed >> 16) & 0xff;
+}
+
+// ---------------------------------------------------------------------------
+// P2M
+// ---------------------------------------------------------------------------
+constexpr int kP2MChunk = 64;
+constexpr int kP2MThreads = 128;
+
+template <typename R>
+__global__ void __launch_bounds__(kP2MThreads) p2m_kernel(
+    int nleaf, const int* __restrict__ lstart, const int* __restrict__ lcount, const R* __restrict__ ploc,
+    const double* __restrict__ q, const double* __restrict__ mu, R* __restrict__ M, int ld, int ncoef, int p,
+    const int* __restrict__ mi, R inv_h) {
+    const int b = blockIdx.x;
+    if (b >= nleaf) return;
+    const int s0 = lstart[b], cnt = lcount[b];
+    // P[site][axis][k + 1] = v^k / k!, v = -(x - z) / h, P[.][.][0] = 0
+    __shared__ R P[kP2MChunk][3][kMaxP + 2];
+    __shared__ R sq[kP2MChunk];
+    __shared__ R sm[kP2MChunk][3];
+    constexpr int CPT = (286 + kP2MThreads - 1) / kP2MThreads;  // coefficients per thread (p <= 10)
+    R acc[CPT];
+#pragma unroll
+    for (int k = 0; k < CPT; k++) acc[k] = R(0);
+    for (int k0 = 0; k0 < cnt; k0 += kP2MChunk) {
+        int m = min(kP2MChunk, cnt - k0);
+        __syncthreads();
+        if (threadIdx.x < m) {
+            int i = s0 + k0 + threadIdx.x;
+            for (int a = 0; a < 3; a++) {
+                R v = -ploc[3 * i + a] * inv_h;
+                R t = R(1);
+                P[threadIdx.x][a][0] = R(0);
+                P[threadIdx.x][a][1] = t;
+                for (int k = 1; k <= p; k++) {
+                    t = t * v / R(k);
+                    P[threadIdx.x][a][k + 1] = t;
+                }
+                sm[threadIdx.x][a] = mu ? R(mu[3 * i + a]) * inv_h : R(0);
+            }
+            sq[threadIdx.x] = q ? R(q[i]) : R(0);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < CPT; k++) {
+            int cidx = threadIdx.x + k * kP2MThreads;
+            if (cidx >= ncoef) continue;
+            int nx, ny, nz;
+            decode_mi(mi[cidx], nx, ny, nz);
+            R a = acc[k];
+            for (int s = 0; s < m; s++) {
+                R px = P[s][0][nx + 1], py = P[s][1][ny + 1], pz = P[s][2][nz + 1];
+                // m_n = q v^n/n! - sum_d (mu_d/h) v^(n-e_d)/(n-e_d)!
+                a += sq[s] * px * py * pz;
+                a -= sm[s][0] * P[s][0][nx] * py * pz + sm[s][1] * px * P[s][1][ny] * pz +
+                     sm[s][2] * px * py * P[s][2][nz];
+            }
+            acc[k] = a;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < CPT; k++) {
+        int cidx = threadIdx.x + k * kP2MThreads;
+        if (cidx < ncoef) M[(int64_t)b * ld + cidx] = acc[k];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// M2M: m^P_n = sum_children sum_{k <= n} (-1)^(b.k) 2^-(|n|+|k|)/k! m^C_{n-k}
+// (child centre offset from the parent centre is (b - 1/2) h_P / 2 per axis)
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void __launch_bounds__(128) m2m_kernel(int npar, const int* __restrict__ child0,
+                                                  const int* __restrict__ nchild, const int* __restrict__ ckey,
+                                                  const R* __restrict__ Mc, R* __restrict__ Mp, int ld, int ncoef,
+                                                  const int* __restrict__ ptr, const int* __restrict__ src,
+                                                  const int* __restrict__ par, const double* __restrict__ w) {
+    extern __shared__ unsigned char smem_raw[];
+    R* S = reinterpret_cast<R*>(smem_raw);  // [8][ld]
+    __shared__ int oct[8];
+    const int b = blockIdx.x;
+    if (b >= npar) return;
+    const int c0 = child0[b], nc = nchild[b];
+    if (threadIdx.x < nc) oct[threadIdx.x] = ckey[c0 + threadIdx.x] & 7;
+    for (int idx = threadIdx.x; idx < nc * ncoef; idx += blockDim.x) {
+        int j = idx / ncoef, cc = idx - j * ncoef;
+        S[j * ld + cc] = Mc[(int64_t)(c0 + j) * ld + cc];
+    }
+    __syncthreads();
+    for (int cc = threadIdx.x; cc < ncoef; cc += blockDim.x) {
+        R acc = R(0);
+        for (int e = ptr[cc]; e < ptr[cc + 1]; e++) {
+            int s = src[e], pb = par[e];
+            R ww = R(w[e]);
+            for (int j = 0; j < nc; j++) {
+                R v = ww * S[j * ld + s];
+                acc += (__popc(pb & oct[j]) & 1) ? -v : v;
+            }
+        }
+        Mp[(int64_t)b * ld + cc] = acc;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// L2L: f^C_n = sum_chunks M2L partial + 2^-(|n|+1) sum_k (x/h_P)^k/k! f^P_{n+k},
+// x/h_P = +-1/4 per axis (+ where the child bit is 1)
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void __launch_bounds__(128) l2l_kernel(int nbox, int cap, int nchunk, const int* __restrict__ key,
+                                                  const int* __restrict__ parent, const R* __restrict__ Lp,
+                                                  const R* __restrict__ Lpar, R* __restrict__ L, int ld, int ncoef,
+                                                  const int* __restrict__ ptr, const int* __restrict__ src,
+                                                  const int* __restrict__ par, const double* __restrict__ w) {
+    extern __shared__ unsigned char smem_raw[];
+    R* F = reinterpret_cast<R*>(smem_raw);  // parent locals [ld]
+    const int b = blockIdx.x;
+    if (b >= nbox) return;
+    const bool shift = Lpar != nullptr;
+    int noct = 0;
+    if (shift) {
+        int ps = parent[b];
+        noct = (~key[b]) & 7;
+        for (int cc = threadIdx.x; cc < ncoef; cc += blockDim.x) F[cc] = Lpar[(int64_t)ps * ld + cc];
+    }
+    __syncthreads();
+    for (int cc = threadIdx.x; cc < ncoef; cc += blockDim.x) {
+        R acc = R(0);
+        for (int k = 0; k < nchunk; k++) acc += Lp[((int64_t)k * cap + b) * ld + cc];
+        if (shift) {
+            for (int e = ptr[cc]; e < ptr[cc + 1]; e++) {
+                R v = R(w[e]) * F[src[e]];
+                acc += (__popc(par[e] & noct) & 1) ? -v : v;
+            }
+        }
+        L[(int64_t)b * ld + cc] = acc;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// M2L (SIMT): tiles of up to 32 same-level, same-octant-class target boxes;
+// lane = target box, each warp owns a balanced set of output coefficients;
+// the offsets of the class are split into `nchunk` ranges over blockIdx.y,
+// each writing its own partial output (summed in fixed order by l2l_kernel).
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void __launch_bounds__(256) m2l_simt_kernel(const M2LTile* __restrict__ tiles, LevelPtrs lp,
+                                                       const R* __restrict__ D, const int* __restrict__ class_off,
+                                                       const short* __restrict__ add, const int* __restrict__ pre,
+                                                       const int* __restrict__ wptr, const int* __restrict__ wout,
+                                                       int ncoef, int ld, int nchunk) {
+    extern __shared__ unsigned char smem_raw[];
+    const int st = ncoef + 1;
+    R* S = reinterpret_cast<R*>(smem_raw);  // [32][st] source coefficients
+    R* A = S + 32 * st;                      // [32][st] accumulators
+    R* Ds = A + 32 * st;                     // [ncoef] derivative table of the offset
+    int* srcs = reinterpret_cast<int*>(Ds + ncoef);
+    const M2LTile tile = tiles[blockIdx.x];
+    const int chunk = blockIdx.y;
+    const int l = tile.level;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nside = 1 << l;
+    int slot = -1, bx = 0, by = 0, bz = 0;
+    if (lane < tile.count) {
+        slot = lp.by_class[l][tile.first + lane];
+        uint32_t k = (uint32_t)lp.key[l][slot];
+        bx = compact3(k);
+        by = compact3(k >> 1);
+        bz = compact3(k >> 2);
+    }
+    for (int idx = threadIdx.x; idx < 32 * st; idx += blockDim.x) A[idx] = R(0);
+    const R* M = reinterpret_cast<const R*>(lp.M[l]);
+    const int* map = lp.map[l];
+    const int per = (kNumOffsets + nchunk - 1) / nchunk;
+    const int t0 = chunk * per, t1 = min(kNumOffsets, t0 + per);
+    const int w0 = wptr[warp], w1 = wptr[warp + 1];
+    for (int t = t0; t < t1; t++) {
+        const int o = class_off[tile.cls * kNumOffsets + t];
+        const int ox = (o & 15) - 3, oy = ((o >> 4) & 15) - 3, oz = ((o >> 8) & 15) - 3;
+        __syncthreads();
+        if (warp == 0) {
+            int s = -1;
+            int ax = bx - ox, ay = by - oy, az = bz - oz;
+            if (slot >= 0 && ax >= 0 && ay >= 0 && az >= 0 && ax < nside && ay < nside && az < nside)
+                s = map[morton3(ax, ay, az)];
+            srcs[lane] = s;
+        }
+        __syncthreads();
+        if (!__syncthreads_or(srcs[lane] >= 0)) continue;
+        for (int idx = threadIdx.x; idx < 32 * ncoef; idx += blockDim.x) {
+            int r = idx / ncoef, j = idx - r * ncoef;
+            int s = srcs[r];
+            S[r * st + j] = s >= 0 ? M[(int64_t)s * ld + j] : R(0);
+        }
+        const int oidx = (ox + 3) + kOffsetGrid * ((oy + 3) + kOffsetGrid * (oz + 3));
+        for (int j = threadIdx.x; j < ncoef; j += blockDim.x) Ds[j] = D[oidx * ncoef + j];
+        __syncthreads();
+        const R* Srow = S + lane * st;
+        R* Arow = A + lane * st;
+        for (int e = w0; e < w1; e++) {
+            const int nn = wout[e];
+            const int np = pre[nn];
+            const short* ad = add + (int64_t)nn * ncoef;
+            R a = Arow[nn];
+            for (int j = 0; j < np; j++) a += Ds[ad[j]] * Srow[j];
+            Arow[nn] = a;
+        }
+    }
+    __syncthreads();
+    if (slot >= 0) {
+        R* Lp = reinterpret_cast<R*>(lp.Lp[l]) + ((int64_t)chunk * lp.cap[l] + slot) * ld;
+        for (int e = w0; e < w1; e++) {
+            int nn = wout[e];
+            Lp[nn] = A[lane * st + nn];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// leaf evaluation: L2P + near field over the 27 adjacent leaves
+// ---------------------------------------------------------------------------
+constexpr int kLeafThreads = 128;
+constexpr int kLeafChunk = 128;
+
+template <int MODE>
+struct LeafOut {
+    static constexpr int NC = MODE == LEAF_FULL ? 10 : (MODE == LEAF_CHARGE_PHI_E ? 4 : 3);
+};
+
+template <typename R, int MODE>
+__global__ void __launch_bounds__(kLeafThreads) leaf_kernel(
+    int nleaf, const int* __restrict__ lkey, const int* __restrict__ lstart, const int* __restrict__ lcount,
+    const int* __restrict__ lmap, int depth, const R* __restrict__ ploc, const double* __restrict__ q_s,
+    const double* __restrict__ mu_s, const R* __restrict__ Lf, int ld, int ncoef, const int* __restrict__ mi,
+    const double* __restrict__ inv_fact, const int* __restrict__ up1, const int* __restrict__ up2, R h,
+    double* __restrict__ out_phi, double* __restrict__ out_E, double* __restrict__ out_G, int* __restrict__ err) {
+    constexpr int NC = LeafOut<MODE>::NC;
+    constexpr bool HAS_PHI = MODE != LEAF_DIPOLE_E;
+    constexpr bool HAS_G = MODE == LEAF_FULL;
+    constexpr bool SRC_Q = MODE != LEAF_DIPOLE_E;
+    constexpr bool SRC_MU = MODE != LEAF_CHARGE_PHI_E;
+    // component layout: [phi] E(3) [G(6)]
+    constexpr int IE = HAS_PHI ? 1 : 0;
+    constexpr int IG = IE + 3;
+
+    extern __shared__ unsigned char smem_raw[];
+    R* f = reinterpret_cast<R*>(smem_raw);  // [ncoef] leaf locals
+    __shared__ R sx[kLeafChunk], sy[kLeafChunk], sz[kLeafChunk];
+    __shared__ R sq[SRC_Q ? kLeafChunk : 1];
+    __shared__ R smx[SRC_MU ? kLeafChunk : 1], smy[SRC_MU ? kLeafChunk : 1], smz[SRC_MU ? kLeafChunk : 1];
+    __shared__ int sidx[kLeafChunk];
+    __shared__ R part[NC][kLeafThreads];
+
+    const int b = blockIdx.x;
+    if (b >= nleaf) return;
+    const int s0 = lstart[b], cnt = lcount[b];
+    const uint32_t key = (uint32_t)lkey[b];
+    const int bx = compact3(key), by = compact3(key >> 1), bz = compact3(key >> 2);
+    const int nside = 1 << depth;
+    for (int cc = threadIdx.x; cc < ncoef; cc += blockDim.x) f[cc] = Lf[(int64_t)b * ld + cc];
+    const R inv_h = R(1) / h;
+
+    for (int tg = 0; tg < cnt; tg += kLeafThreads) {
+        const int nt = min(kLeafThreads, cnt - tg);
+        const int slices = kLeafThreads / nt;
+        const int t = threadIdx.x % nt, s = threadIdx.x / nt;
+        const bool active = s < slices;
+        const int i = s0 + tg + t;
+        R acc[NC];
+#pragma unroll
+        for (int k = 0; k < NC; k++) acc[k] = R(0);
+        R xi = R(0), yi = R(0), zi = R(0);
+        __syncthreads();
+        if (active) {
+            xi = ploc[3 * i];
+            yi = ploc[3 * i + 1];
+            zi = ploc[3 * i + 2];
+            // far field: L2P of this slice's share of the coefficients
+            const R ux = xi * inv_h, uy = yi * inv_h, uz = zi * inv_h;
+            R dphi[3] = {R(0), R(0), R(0)};
+            R ddphi[6] = {R(0), R(0), R(0), R(0), R(0), R(0)};
+            R phi = R(0);
+            for (int cc = s; cc < ncoef; cc += slices) {
+                int nx, ny, nz;
+                decode_mi(mi[cc], nx, ny, nz);
+                R wgt = R(inv_fact[cc]);
+                for (int k = 0; k < nx; k++) wgt *= ux;
+                for (int k = 0; k < ny; k++) wgt *= uy;
+                for (int k = 0; k < nz; k++) wgt *= uz;
+                if (HAS_PHI) phi += wgt * f[cc];
+                const int u0 = up1[3 * cc];
+                if (u0 >= 0) {
+                    dphi[0] += wgt * f[u0];
+                    dphi[1] += wgt * f[up1[3 * cc + 1]];
+                    dphi[2] += wgt * f[up1[3 * cc + 2]];
+                }
+                if (HAS_G) {
+                    const int v0 = up2[6 * cc];
+                    if (v0 >= 0) {
+                        ddphi[0] += wgt * f[v0];
+#pragma unroll
+                        for (int k = 1; k < 6; k++) ddphi[k] += wgt * f[up2[6 * cc + k]];
+                    }
+                }
+            }
+            // Phi = phi / h, E = -dPhi / h^2, G = -ddPhi / h^3
+            if (HAS_PHI) acc[0] = phi * inv_h;
+            const R s2 = -inv_h * inv_h;
+#pragma unroll
+            for (int d = 0; d < 3; d++) acc[IE + d] = dphi[d] * s2;
+            if (HAS_G) {
+                const R s3 = s2 * inv_h;
+#pragma unroll
+                for (int k = 0; k < 6; k++) acc[IG + k] = ddphi[k] * s3;
+            }
+        }
+        // near field
+        for (int dz = -1; dz <= 1; dz++)
+            for (int dy = -1; dy <= 1; dy++)
+                for (int dx = -1; dx <= 1; dx++) {
+                    const int ax = bx + dx, ay = by + dy, az = bz + dz;
+                    if (ax < 0 || ay < 0 || az < 0 || ax >= nside || ay >= nside || az >= nside) continue;
+                    const int ns = lmap[morton3(ax, ay, az)];
+                    if (ns < 0) continue;
+                    const int js0 = lstart[ns], jc = lcount[ns];
+                    const R shx = R(dx) * h, shy = R(dy) * h, shz = R(dz) * h;
+                    for (int k0 = 0; k0 < jc; k0 += kLeafChunk) {
+                        const int m = min(kLeafChunk, jc - k0);
+                        __syncthreads();
+                        for (int jj = threadIdx.x; jj < m; jj += blockDim.x) {
+                            const int j = js0 + k0 + jj;
+                            sx[jj] = ploc[3 * j] + shx;
+                            sy[jj] = ploc[3 * j + 1] + shy;
+                            sz[jj] = ploc[3 * j + 2] + shz;
+                            if (SRC_Q) sq[jj] = R(q_s[j]);
+                            if (SRC_MU) {
+                                smx[jj] = R(mu_s[3 * j]);
+                                smy[jj] = R(mu_s[3 * j + 1]);
+                                smz[jj] = R(mu_s[3 * j + 2]);
+                            }
+                            sidx[jj] = j;
+                        }
+                        __syncthreads();
+                        if (!active) continue;
+                        for (int jj = s; jj < m; jj += slices) {
+                            const R rx = xi - sx[jj], ry = yi - sy[jj], rz = zi - sz[jj];
+                            const R r2 = rx * rx + ry * ry + rz * rz;
+                            if (sidx[jj] == i) continue;
+                            if (r2 == R(0)) {
+                                atomicOr(err, 2);
+                                continue;
+                            }
+                            const R ri = R(1) / sqrt(r2);
+                            const R ri2 = ri * ri;
+                            const R ri3 = ri * ri2;
+                            if (SRC_Q) {
+                                const R qj = sq[jj];
+                                const R qr3 = qj * ri3;
+                                if (HAS_PHI) acc[0] += qj * ri;
+                                acc[IE + 0] += qr3 * rx;
+                                acc[IE + 1] += qr3 * ry;
+                                acc[IE + 2] += qr3 * rz;
+                                if (HAS_G) {
+                                    const R t5 = R(3) * qr3 * ri2;
+                                    acc[IG + 0] += qr3 - t5 * rx * rx;
+                                    acc[IG + 1] -= t5 * rx * ry;
+                                    acc[IG + 2] -= t5 * rx * rz;
+                                    acc[IG + 3] += qr3 - t5 * ry * ry;
+                                    acc[IG + 4] -= t5 * ry * rz;
+                                    acc[IG + 5] += qr3 - t5 * rz * rz;
+                                }
+                            }
+                            if (SRC_MU) {
+                                const R mx = smx[jj], my = smy[jj], mz = smz[jj];
+                                const R mr = mx * rx + my * ry + mz * rz;
+                                const R ri5 = ri3 * ri2;
+                                const R a3 = R(3) * mr * ri5;
+                                if (HAS_PHI) acc[0] += mr * ri3;
+                                acc[IE + 0] += a3 * rx - mx * ri3;
+                                acc[IE + 1] += a3 * ry - my * ri3;
+                                acc[IE + 2] += a3 * rz - mz * ri3;
+                                if (HAS_G) {
+                                    // G_de = 3 (mu_d r_e + mu_e r_d + mr delta_de) / r^5 - 15 mr r_d r_e / r^7
+                                    const R t5 = R(3) * ri5;
+                                    const R t7 = R(5) * a3 * ri2;
+                                    acc[IG + 0] += t5 * (R(2) * mx * rx + mr) - t7 * rx * rx;
+                                    acc[IG + 1] += t5 * (mx * ry + my * rx) - t7 * rx * ry;
+                                    acc[IG + 2] += t5 * (mx * rz + mz * rx) - t7 * rx * rz;
+                                    acc[IG + 3] += t5 * (R(2) * my * ry + mr) - t7 * ry * ry;
+                                    acc[IG + 4] += t5 * (my * rz + mz * ry) - t7 * ry * rz;
+                                    acc[IG + 5] += t5 * (R(2) * mz * rz + mr) - t7 * rz * rz;
+                                }
+                            }
+                        }
+                    }
+                }
+        // fixed-order reduction over slices
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < NC; k++) part[k][threadIdx.x] = active ? acc[k] : R(0);
+        __syncthreads();
+        if (threadIdx.x < nt) {
+            const int ii = s0 + tg + threadIdx.x;
+            double o[NC];
+#pragma unroll
+            for (int k = 0; k < NC; k++) {
+                R v = R(0);
+                for (int u = 0; u < slices; u++) v += part[k][threadIdx.x + u * nt];
+                o[k] = (double)v;
+            }
+            if (HAS_PHI && out_phi) out_phi[ii] = o[0];
+            if (out_E)
+                for (int d = 0; d < 3; d++) out_E[3 * (int64_t)ii + d] = o[IE + d];
+            if (HAS_G && out_G)
+                for (int k = 0; k < 6; k++) out_G[6 * (int64_t)ii + k] = o[IG + k];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+static LevelPtrs level_ptrs(polfmm_ctx* c) {
+    LevelPtrs lp{};
+    for (int l = 0; l <= c->depth; l++) {
+        lp.key[l] = c->lv[l].key;
+        lp.map[l] = c->lv[l].map;
+        lp.by_class[l] = c->lv[l].by_class;
+        lp.M[l] = c->lv[l].M;
+        lp.Lp[l] = c->lv[l].Lp;
+        lp.cap[l] = c->lv[l].cap;
+    }
+    return lp;
+}
+
+size_t m2l_simt_smem(int ncoef, size_t rsize) {
+    return rsize * (2 * 32 * (size_t)(ncoef + 1) + ncoef) + 32 * sizeof(int) + 16;
+}
+
+int m2l_setup(polfmm_ctx* c) {
+    // tiles of same-level, same-class boxes
+    std::vector<M2LTile> t;
+    for (int l = 2; l <= c->depth; l++)
+        for (int k = 0; k < 8; k++) {
+            int cnt = c->lv[l].class_count[k], st = c->lv[l].class_start[k];
+            for (int f = 0; f < cnt; f += kM2LTileBoxes)
+                t.push_back(M2LTile{l, k, st + f, std::min(kM2LTileBoxes, cnt - f)});
+        }
+    c->ntiles = (int)t.size();
+    if (c->ntiles > c->ntiles_cap) {
+        if (c->tiles) cudaFree(c->tiles);
+        c->tiles = nullptr;
+        c->ntiles_cap = std::max(c->ntiles, 64);
+        if (cudaMalloc(&c->tiles, sizeof(M2LTile) * c->ntiles_cap) != cudaSuccess) return POLFMM_ERR_OUT_OF_MEMORY;
+    }
+    if (c->ntiles)
+        if (cudaMemcpyAsync(c->tiles, t.data(), sizeof(M2LTile) * c->ntiles, cudaMemcpyHostToDevice, c->stream) !=
+            cudaSuccess)
+            return POLFMM_ERR_CUDA;
+    // split the 189 offsets over enough blocks to cover the SMs twice
+    int want = c->ntiles > 0 ? (2 * c->num_sms + c->ntiles - 1) / c->ntiles : 1;
+    c->m2l_chunks = std::max(1, std::min(want, c->mixed ? 7 : 7));
+    return POLFMM_OK;
+}
+
+template <typename R>
+static void launch_leaf(polfmm_ctx* c, int mode, const double* mu_sorted, double* phi, double* E, double* G) {
+    Level& L = c->lv[c->depth];
+    const R h = R(c->side / (double)(1 << c->depth));
+    size_t smem = sizeof(R) * c->ncoef;
+    const Tables& T = c->tab;
+    LaunchScope ls(c, F_LEAF);
+#define LEAF_ARGS                                                                                              \
+    L.nbox, L.key, c->lstart, c->lcount, L.map, c->depth, (const R*)c->ploc, c->q_s, mu_sorted, (const R*)L.L, \
+        c->ld, c->ncoef, T.mi, T.inv_fact, T.up1, T.up2, h, phi, E, G, c->err
+    if (mode == LEAF_DIPOLE_E)
+        leaf_kernel<R, LEAF_DIPOLE_E><<<L.nbox, kLeafThreads, smem, c->stream>>>(LEAF_ARGS);
+    else if (mode == LEAF_CHARGE_PHI_E)
+        leaf_kernel<R, LEAF_CHARGE_PHI_E><<<L.nbox, kLeafThreads, smem, c->stream>>>(LEAF_ARGS);
+    else
+        leaf_kernel<R, LEAF_FULL><<<L.nbox, kLeafThreads, smem, c->stream>>>(LEAF_ARGS);
+#undef LEAF_ARGS
+}
+
+void m2l_tensor_launch(polfmm_ctx* c);  // m2l_tc.cu
+bool m2l_tensor_enabled(polfmm_ctx* c);
+
+template <typename R>
+static void pass_impl(polfmm_ctx* c, int mode, bool use_q, const double* mu_sorted, double* phi, double* E,
+                      double* G) {
+    const int d = c->depth;
+    const Tables& T = c->tab;
+    Level& Lf = c->lv[d];
+    // P2M
+    {
+        LaunchScope ls(c, F_P2M);
+        R inv_h = R((double)(1 << d) / c->side);
+        p2m_kernel<R><<<Lf.nbox, kP2MThreads, 0, c->stream>>>(Lf.nbox, c->lstart, c->lcount, (const R*)c->ploc,
+                                                              use_q ? c->q_s : nullptr, mu_sorted, (R*)Lf.M, c->ld,
+                                                              c->ncoef, c->p, T.mi, inv_h);
+    }
+    if (d >= 2) {
+        // M2M up to level 2
+        for (int l = d - 1; l >= 2; l--) {
+            LaunchScope ls(c, F_M2M);
+            Level& P = c->lv[l];
+            Level& C = c->lv[l + 1];
+            m2m_kernel<R><<<P.nbox, 128, sizeof(R) * 8 * c->ld, c->stream>>>(
+                P.nbox, P.child0, P.nchild, C.key, (const R*)C.M, (R*)P.M, c->ld, c->ncoef, T.m2m_ptr, T.m2m_src,
+                T.m2m_par, T.m2m_w);
+        }
+        // M2L
+        if (c->ntiles > 0) {
+            if (m2l_tensor_enabled(c)) {
+                m2l_tensor_launch(c);
+            } else {
+                LaunchScope ls(c, F_M2L);
+                dim3 grid(c->ntiles, c->m2l_chunks);
+                size_t smem = m2l_simt_smem(c->ncoef, sizeof(R));
+                m2l_simt_kernel<R><<<grid, 256, smem, c->stream>>>(
+                    c->tiles, level_ptrs(c), c->mixed ? (const R*)T.Df : (const R*)T.D, T.class_off, T.add, T.pre,
+                    T.warp_out_ptr, T.warp_out, c->ncoef, c->ld, c->m2l_chunks);
+            }
+        }
+        // L2L (level 2: partial sums only)
+        for (int l = 2; l <= d; l++) {
+            LaunchScope ls(c, F_L2L);
+            Level& B = c->lv[l];
+            const R* Lpar = l >= 3 ? (const R*)c->lv[l - 1].L : nullptr;
+            l2l_kernel<R><<<B.nbox, 128, sizeof(R) * c->ld, c->stream>>>(
+                B.nbox, B.cap, c->m2l_chunks, B.key, B.parent, (const R*)B.Lp, Lpar, (R*)B.L, c->ld, c->ncoef,
+                T.l2l_ptr, T.l2l_src, T.l2l_par, T.l2l_w);
+        }
+    } else {
+        cudaMemsetAsync(Lf.L, 0, sizeof(R) * (size_t)Lf.cap * c->ld, c->stream);
+    }
+    launch_leaf<R>(c, mode, mu_sorted, phi, E, G);
+}
+
+void fmm_pass(polfmm_ctx* c, int mode, bool use_q, const double* mu_sorted, double* phi, double* E, double* G) {
+    if (c->mixed)
+        pass_impl<float>(c, mode, use_q, mu_sorted, phi, E, G);
+    else
+        pass_impl<double>(c, mode, use_q, mu_sorted, phi, E, G);
+}
+
+int fmm_ops_init_attributes(polfmm_ctx*) {
+    // sized for the largest order so that contexts of different p coexist
+    const int nc_max = ncoef_of(kMaxP);
+    size_t need_d = m2l_simt_smem(nc_max, sizeof(double));
+    size_t need_f = m2l_simt_smem(nc_max, sizeof(float));
+    if (cudaFuncSetAttribute(m2l_simt_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need_d) !=
+        cudaSuccess)
+        return POLFMM_ERR_CUDA;
+    if (cudaFuncSetAttribute(m2l_simt_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need_f) !=
+        cudaSuccess)
+        return POLFMM_ERR_CUDA;
+    return POLFMM_OK;
+}
+
+}  // namespace polfmm

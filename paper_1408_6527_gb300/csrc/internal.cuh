@@ -1,0 +1,243 @@
+// Internal declarations of the polfmm CUDA library (not part of the C ABI).
+//
+// Data layout in HBM (all per-site arrays are in Morton-sorted site order):
+//   pos_s  double[3n]   sorted positions             q_s, alpha_s double[n]
+//   perm   int[n]       sorted index -> caller index
+//   ploc   R[3n]        position minus its leaf centre (Angstrom), R = double
+//                       (FP64 mode) or float (MIXED mode)
+//   per level l = 0..depth: occupied boxes in Morton order (key, parent,
+//   first child, child count), a dense Morton-key -> slot map of 8^l int32,
+//   the boxes regrouped by octant class (key & 7), and the normalised
+//   multipole / local coefficients m (nbox x ld) and f (nbox x ld):
+//       m_n = M_n / h^|n|,  f_n = F_n h^(|n|+1),  h = box side at that level,
+//   so that every stored coefficient is O(1) and one table of normalised
+//   derivatives per integer offset serves every level.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "../../include/polfmm.h"
+
+namespace polfmm {
+
+constexpr int kMaxP = 10;
+constexpr int kMaxDepth = 8;
+constexpr int kNumOffsets = 189;    // interaction-list offsets per octant class
+constexpr int kOffsetGrid = 7;      // offsets live in [-3, 3]^3
+constexpr int kM2LTileBoxes = 32;   // target boxes per multipole-to-local tile
+
+inline int ncoef_of(int p) { return (p + 1) * (p + 2) * (p + 3) / 6; }
+
+// ---------------------------------------------------------------------------
+// index tables for one expansion order p (device copies)
+// ---------------------------------------------------------------------------
+struct Tables {
+    int p = 0, ncoef = 0, ld = 0;
+    // multi-index of coefficient c packed as nx | ny << 8 | nz << 16 | |n| << 24
+    int* mi = nullptr;
+    double* inv_fact = nullptr;       // 1 / n!
+    float* inv_fact_f = nullptr;
+    int* up1 = nullptr;               // [ncoef][3]: index of n + e_d or -1
+    int* up2 = nullptr;               // [ncoef][6]: index of n + e_d + e_e (xx xy xz yy yz zz) or -1
+    int* pre = nullptr;               // [ncoef]: number of m with |m| <= p - |n| (a prefix)
+    short* add = nullptr;             // [ncoef][ncoef]: index of n + m (valid for m < pre[n])
+    // shift operators as CSR lists over output coefficient c
+    int* m2m_ptr = nullptr;           // [ncoef + 1]
+    int* m2m_src = nullptr;           // index of n - k
+    int* m2m_par = nullptr;           // parity bits of k (kx&1 | (ky&1)<<1 | (kz&1)<<2)
+    double* m2m_w = nullptr;          // 2^-(|n|+|k|) / k!
+    int* l2l_ptr = nullptr;
+    int* l2l_src = nullptr;           // index of n + k
+    int* l2l_par = nullptr;
+    double* l2l_w = nullptr;          // 2^-(|n|+1+2|k|) / k!
+    double* D = nullptr;              // [343][ncoef] normalised derivatives of 1/r at integer offsets
+    float* Df = nullptr;
+    int* class_off = nullptr;         // [8][189] packed offsets (ox+3) | (oy+3)<<4 | (oz+3)<<8
+    int* warp_out_ptr = nullptr;      // M2L output lists per warp (CSR, 8 warps)
+    int* warp_out = nullptr;
+    std::vector<int> h_mi;            // host copies used by the host code
+};
+
+// one tile of same-level, same-octant-class target boxes for the M2L kernel
+struct M2LTile {
+    int level;
+    int cls;
+    int first;   // index into the level's by_class list
+    int count;   // <= kM2LTileBoxes
+};
+
+struct LevelPtrs {
+    int* key[kMaxDepth + 1];
+    int* map[kMaxDepth + 1];
+    int* by_class[kMaxDepth + 1];
+    void* M[kMaxDepth + 1];
+    void* Lp[kMaxDepth + 1];   // M2L partial outputs [chunk][cap][ld]
+    int cap[kMaxDepth + 1];
+};
+
+struct Level {
+    int nbox = 0, cap = 0;
+    int* key = nullptr;
+    int* map = nullptr;
+    int* parent = nullptr;
+    int* child0 = nullptr;
+    int* nchild = nullptr;
+    int* by_class = nullptr;
+    int class_count[8] = {0};
+    int class_start[8] = {0};
+    void* M = nullptr;    // [cap][ld]
+    void* L = nullptr;    // [cap][ld]
+    void* Lp = nullptr;   // [m2l_chunks][cap][ld]
+};
+
+// profiling families
+enum Family { F_TREE = 0, F_P2M, F_M2M, F_M2L, F_L2L, F_LEAF, F_SOLVER, F_ASSEMBLE, F_COUNT };
+
+// leaf evaluation modes
+enum LeafMode { LEAF_DIPOLE_E = 0, LEAF_CHARGE_PHI_E = 1, LEAF_FULL = 2 };
+
+}  // namespace polfmm
+
+struct polfmm_ctx {
+    polfmm_options opt;
+    int64_t n = 0;
+    int p = 0, depth = 0, ncoef = 0, ld = 0;
+    bool mixed = false;
+    double lo[3] = {0, 0, 0};
+    double side = 0;
+    cudaStream_t stream = nullptr;
+    int num_sms = 0;
+
+    // sorted site data
+    double* pos_s = nullptr;
+    double* q_s = nullptr;
+    double* alpha_s = nullptr;
+    int* perm = nullptr;
+    uint32_t* key_s = nullptr;
+    void* ploc = nullptr;
+    // leaves
+    int* lstart = nullptr;
+    int* lcount = nullptr;
+    polfmm::Level lv[polfmm::kMaxDepth + 1];
+    polfmm::Tables tab;
+    // M2L work list
+    polfmm::M2LTile* tiles = nullptr;
+    int ntiles = 0;
+    int m2l_chunks = 1;
+    int ntiles_cap = 0;
+
+    // caller-order staging
+    double* in_buf = nullptr;     // 6n doubles
+    double* out_buf = nullptr;    // 10n doubles
+    // static pass
+    double* phiq = nullptr;
+    double* Eq = nullptr;
+    // solver vectors (3n each)
+    double *mu = nullptr, *r = nullptr, *z = nullptr, *d = nullptr, *Ad = nullptr, *Td = nullptr;
+    // full pass outputs
+    double *phi_t = nullptr, *E_t = nullptr, *G_t = nullptr;
+    // reductions
+    double* partial = nullptr;    // [kRedSlots][kRedBlocks]
+    double* scal = nullptr;       // device scalars
+    double* h_scal = nullptr;     // pinned host mirror
+    int* err = nullptr;           // device error word
+    // sort / scan scratch
+    uint32_t* key_tmp = nullptr;
+    int* val_tmp = nullptr;
+    int* val_a = nullptr;
+    int* counts = nullptr;
+    int* scan_tmp = nullptr;
+    int* flags = nullptr;
+    size_t counts_cap = 0, scan_tmp_cap = 0;
+    int* tree_cnt = nullptr;      // device tree counts ((kMaxDepth + 1) * 9 ints)
+    int* h_counts = nullptr;      // pinned host copy of tree counts
+    double* h_bbox = nullptr;     // pinned host bounding box
+
+    bool have_mu = false;
+    int64_t launches = 0;
+    void* extra = nullptr;        // host-side bookkeeping of device allocations
+    void* tc = nullptr;           // tensor-core M2L state
+    // profiling
+    cudaEvent_t ev_pool[2 * 4096];
+    int ev_used = 0;
+    int ev_family[4096];
+    bool ev_created = false;
+    double prof_ms[polfmm::F_COUNT] = {0};
+    int64_t prof_n[polfmm::F_COUNT] = {0};
+};
+
+namespace polfmm {
+
+// launch bookkeeping / profiling around one kernel launch
+struct LaunchScope {
+    polfmm_ctx* c;
+    int fam;
+    int slot;
+    LaunchScope(polfmm_ctx* ctx, int family);
+    ~LaunchScope();
+};
+void profile_flush(polfmm_ctx* c);
+
+// tree.cu
+int tree_root_box(polfmm_ctx* c, const double* x_dev, double* part_dev, double* h_pinned);
+int tree_build(polfmm_ctx* c, const double* x_in);
+int tree_tables(polfmm_ctx* c, const double* x_in, const double* q_in, const double* a_in);
+size_t tree_scan_scratch(int64_t n);
+size_t tree_count_scratch(int64_t n);
+int scan_exclusive(polfmm_ctx* c, const int* in, int* out, int n, int* total_dev);
+
+// fmm_ops.cu
+void fmm_pass(polfmm_ctx* c, int mode, bool use_q, const double* mu_sorted, double* phi, double* E,
+              double* G);
+int m2l_setup(polfmm_ctx* c);
+
+// solver.cu
+void gather_sites(polfmm_ctx* c, const double* src_caller, double* dst_sorted, int comps);
+void scatter_sites(polfmm_ctx* c, const double* src_sorted, double* dst_caller, int comps);
+void solver_init(polfmm_ctx* c, bool warm);
+void solver_pcg_step(polfmm_ctx* c);
+void solver_jacobi_step(polfmm_ctx* c);
+void energy_and_gradients(polfmm_ctx* c, double* forces_caller, double* dq_caller,
+                          double* dalpha_caller, bool want_f, bool want_dq, bool want_da);
+void mask_dipoles(polfmm_ctx* c, double* v);
+
+// device scalar slots
+enum Scal {
+    S_RZ = 0, S_RZ_NEW, S_DAD, S_RR, S_BB, S_UQQ, S_MUEQ, S_MUEMU, S_AMU, S_BETA, S_COUNT
+};
+constexpr int kRedBlocks = 256;
+constexpr int kRedSlots = 8;
+
+// helpers
+__host__ __device__ inline uint32_t spread3(uint32_t v) {
+    v &= 0x3ff;
+    v = (v | (v << 16)) & 0x030000FF;
+    v = (v | (v << 8)) & 0x0300F00F;
+    v = (v | (v << 4)) & 0x030C30C3;
+    v = (v | (v << 2)) & 0x09249249;
+    return v;
+}
+__host__ __device__ inline uint32_t compact3(uint32_t v) {
+    v &= 0x09249249;
+    v = (v ^ (v >> 2)) & 0x030C30C3;
+    v = (v ^ (v >> 4)) & 0x0300F00F;
+    v = (v ^ (v >> 8)) & 0x030000FF;
+    v = (v ^ (v >> 16)) & 0x000003FF;
+    return v;
+}
+__host__ __device__ inline uint32_t morton3(uint32_t i, uint32_t j, uint32_t k) {
+    return spread3(i) | (spread3(j) << 1) | (spread3(k) << 2);
+}
+
+inline int grid_for(int64_t n, int block) { return (int)((n + block - 1) / block); }
+
+}  // namespace polfmm
+
+#define POLFMM_CUDA_TRY(expr)                         \
+    do {                                              \
+        cudaError_t e_ = (expr);                      \
+        if (e_ != cudaSuccess) return POLFMM_ERR_CUDA; \
+    } while (0)

@@ -1,0 +1,335 @@
+// Induced-dipole solver and energy / gradient assembly, all in FP64.
+//
+// The dipoles solve mu_i = alpha_i (E^q_i + E^mu_i) (Sec. II.A, Eq. dipole
+// moment), i.e. (diag(1/alpha) - T) mu = E^q with T the (symmetric) FMM
+// dipole-field operator.  Default: preconditioned conjugate gradients with
+// the Jacobi preconditioner diag(alpha), started from mu = alpha E^q; the
+// fixed point mu <- alpha (E^q + T mu) is available as well.  The paper only
+// refers to an earlier publication for its iteration (Sec. III).
+//
+// Reductions are deterministic: a fixed grid of kRedBlocks blocks writes
+// per-block partial sums in a fixed order, and one block adds them up.
+#include <math.h>
+
+#include "internal.cuh"
+
+namespace polfmm {
+
+constexpr int kRedThreads = 256;
+
+__device__ inline double block_sum(double v, double* sh) {
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    for (int w = kRedThreads / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    double r = sh[0];
+    __syncthreads();
+    return r;
+}
+
+// single-block final reduction of nslot partial rows
+// post: 0 = store sums into scal[dst[k]]; 1 = PCG direction update
+// (scal[S_BETA] = sum0 / scal[S_RZ], scal[S_RZ] = sum0, scal[S_RR] = sum1)
+__global__ void reduce_final_kernel(const double* __restrict__ partial, int nslot, int s0, int s1, int s2, int s3,
+                                    double* __restrict__ scal, int post) {
+    __shared__ double sh[kRedThreads];
+    int dst[4] = {s0, s1, s2, s3};
+    double res[4] = {0, 0, 0, 0};
+    for (int k = 0; k < nslot; k++) {
+        double v = 0.0;
+        for (int b = threadIdx.x; b < kRedBlocks; b += kRedThreads) v += partial[k * kRedBlocks + b];
+        res[k] = block_sum(v, sh);
+    }
+    if (threadIdx.x == 0) {
+        if (post == 1) {
+            double rz_old = scal[S_RZ];
+            scal[S_BETA] = res[0] / rz_old;  // beta
+            scal[S_RZ] = res[0];
+            scal[S_RR] = res[1];
+        } else {
+            for (int k = 0; k < nslot; k++) scal[dst[k]] = res[k];
+        }
+    }
+}
+
+#define RED_LOOP(i, n) for (int64_t i = blockIdx.x * (int64_t)kRedThreads + threadIdx.x; i < (n); i += (int64_t)kRedBlocks * kRedThreads)
+
+__device__ inline bool active_site(const double* alpha, int64_t site) { return alpha[site] > 0.0; }
+
+// mu = alpha E^q (masked)
+__global__ void mu_init_kernel(int64_t n, const double* __restrict__ alpha, const double* __restrict__ Eq,
+                               double* __restrict__ mu) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= 3 * n) return;
+    double a = alpha[i / 3];
+    mu[i] = a > 0.0 ? a * Eq[i] : 0.0;
+}
+
+__global__ void mask_kernel(int64_t n, const double* __restrict__ alpha, double* __restrict__ v) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= 3 * n) return;
+    if (!(alpha[i / 3] > 0.0)) v[i] = 0.0;
+}
+
+// r = E^q - (mu/alpha - T mu); z = alpha r; d = z; partials r.z, r.r, Eq.Eq
+__global__ void pcg_init_kernel(int64_t n, const double* __restrict__ alpha, const double* __restrict__ Eq,
+                                const double* __restrict__ mu, const double* __restrict__ Tmu, double* __restrict__ r,
+                                double* __restrict__ z, double* __restrict__ d, double* __restrict__ partial) {
+    __shared__ double sh[kRedThreads];
+    double rz = 0, rr = 0, bb = 0;
+    RED_LOOP(i, 3 * n) {
+        double a = alpha[i / 3];
+        double ri = 0, zi = 0;
+        if (a > 0.0) {
+            ri = Eq[i] - (mu[i] / a - Tmu[i]);
+            zi = a * ri;
+            bb += Eq[i] * Eq[i];
+        }
+        r[i] = ri;
+        z[i] = zi;
+        d[i] = zi;
+        rz += ri * zi;
+        rr += ri * ri;
+    }
+    rz = block_sum(rz, sh);
+    rr = block_sum(rr, sh);
+    bb = block_sum(bb, sh);
+    if (threadIdx.x == 0) {
+        partial[0 * kRedBlocks + blockIdx.x] = rz;
+        partial[1 * kRedBlocks + blockIdx.x] = rr;
+        partial[2 * kRedBlocks + blockIdx.x] = bb;
+    }
+}
+
+// Ad = d/alpha - T d; partial d.Ad
+__global__ void pcg_ad_kernel(int64_t n, const double* __restrict__ alpha, const double* __restrict__ d,
+                              const double* __restrict__ Td, double* __restrict__ Ad, double* __restrict__ partial) {
+    __shared__ double sh[kRedThreads];
+    double s = 0;
+    RED_LOOP(i, 3 * n) {
+        double a = alpha[i / 3];
+        double v = a > 0.0 ? d[i] / a - Td[i] : 0.0;
+        Ad[i] = v;
+        s += d[i] * v;
+    }
+    s = block_sum(s, sh);
+    if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+// step = rz / dAd; mu += step d; r -= step Ad; z = alpha r; partials r.z, r.r
+__global__ void pcg_update_kernel(int64_t n, const double* __restrict__ alpha, const double* __restrict__ scal,
+                                  const double* __restrict__ d, const double* __restrict__ Ad, double* __restrict__ mu,
+                                  double* __restrict__ r, double* __restrict__ z, double* __restrict__ partial) {
+    __shared__ double sh[kRedThreads];
+    const double step = scal[S_RZ] / scal[S_DAD];
+    double rz = 0, rr = 0;
+    RED_LOOP(i, 3 * n) {
+        double a = alpha[i / 3];
+        if (a > 0.0) {
+            mu[i] += step * d[i];
+            double ri = r[i] - step * Ad[i];
+            double zi = a * ri;
+            r[i] = ri;
+            z[i] = zi;
+            rz += ri * zi;
+            rr += ri * ri;
+        }
+    }
+    rz = block_sum(rz, sh);
+    rr = block_sum(rr, sh);
+    if (threadIdx.x == 0) {
+        partial[0 * kRedBlocks + blockIdx.x] = rz;
+        partial[1 * kRedBlocks + blockIdx.x] = rr;
+    }
+}
+
+// d = z + beta d
+__global__ void pcg_direction_kernel(int64_t n, const double* __restrict__ scal, const double* __restrict__ z,
+                                     double* __restrict__ d) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= 3 * n) return;
+    d[i] = z[i] + scal[S_BETA] * d[i];
+}
+
+// Jacobi fixed point: r = E^q + T mu - mu/alpha (residual at the current mu),
+// mu <- alpha (E^q + T mu); partial r.r
+__global__ void jacobi_kernel(int64_t n, const double* __restrict__ alpha, const double* __restrict__ Eq,
+                              const double* __restrict__ Tmu, double* __restrict__ mu, double* __restrict__ partial) {
+    __shared__ double sh[kRedThreads];
+    double rr = 0;
+    RED_LOOP(i, 3 * n) {
+        double a = alpha[i / 3];
+        if (a > 0.0) {
+            double e = Eq[i] + Tmu[i];
+            double ri = e - mu[i] / a;
+            rr += ri * ri;
+            mu[i] = a * e;
+        } else {
+            mu[i] = 0.0;
+        }
+    }
+    rr = block_sum(rr, sh);
+    if (threadIdx.x == 0) partial[blockIdx.x] = rr;
+}
+
+__global__ void norm_b_kernel(int64_t n, const double* __restrict__ alpha, const double* __restrict__ Eq,
+                              double* __restrict__ partial) {
+    __shared__ double sh[kRedThreads];
+    double bb = 0;
+    RED_LOOP(i, 3 * n) {
+        if (alpha[i / 3] > 0.0) bb += Eq[i] * Eq[i];
+    }
+    bb = block_sum(bb, sh);
+    if (threadIdx.x == 0) partial[blockIdx.x] = bb;
+}
+
+// gather / scatter between caller order and sorted order
+__global__ void gather_kernel(int64_t n, int comps, const int* __restrict__ perm, const double* __restrict__ src,
+                              double* __restrict__ dst) {
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= n * comps) return;
+    int64_t i = t / comps;
+    int k = (int)(t - i * comps);
+    dst[t] = src[(int64_t)perm[i] * comps + k];
+}
+
+__global__ void scatter_kernel(int64_t n, int comps, const int* __restrict__ perm, const double* __restrict__ src,
+                               double* __restrict__ dst, double scale) {
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= n * comps) return;
+    int64_t i = t / comps;
+    int k = (int)(t - i * comps);
+    dst[(int64_t)perm[i] * comps + k] = scale * src[t];
+}
+
+// forces, dU/dq, dU/dalpha (caller order) and energy partials
+// F = q E + (grad E) mu;  dU/dq = Phi;  dU/dalpha = -|mu|^2 / (2 alpha^2)
+// (-|E|^2/2 where alpha = 0); energies: 1/2 q Phi^q, mu.E^q, mu.E^mu, |mu|^2/(2 alpha)
+__global__ void assemble_kernel(int64_t n, const int* __restrict__ perm, const double* __restrict__ q,
+                                const double* __restrict__ alpha, const double* __restrict__ mu,
+                                const double* __restrict__ phiq, const double* __restrict__ Eq,
+                                const double* __restrict__ phi, const double* __restrict__ E,
+                                const double* __restrict__ G, double kc, double* __restrict__ F,
+                                double* __restrict__ dq, double* __restrict__ da, double* __restrict__ partial) {
+    __shared__ double sh[kRedThreads];
+    double uqq = 0, mueq = 0, muemu = 0, amu = 0;
+    RED_LOOP(i, n) {
+        const double qi = q[i], ai = alpha[i];
+        const double m0 = mu[3 * i], m1 = mu[3 * i + 1], m2 = mu[3 * i + 2];
+        const double e0 = E[3 * i], e1 = E[3 * i + 1], e2 = E[3 * i + 2];
+        const double* g = G + 6 * i;
+        const int o = perm[i];
+        if (F) {
+            F[3 * (int64_t)o + 0] = kc * (qi * e0 + g[0] * m0 + g[1] * m1 + g[2] * m2);
+            F[3 * (int64_t)o + 1] = kc * (qi * e1 + g[1] * m0 + g[3] * m1 + g[4] * m2);
+            F[3 * (int64_t)o + 2] = kc * (qi * e2 + g[2] * m0 + g[4] * m1 + g[5] * m2);
+        }
+        if (dq) dq[o] = kc * phi[i];
+        const double mm = m0 * m0 + m1 * m1 + m2 * m2;
+        if (da) da[o] = ai > 0.0 ? -kc * mm / (2.0 * ai * ai) : -0.5 * kc * (e0 * e0 + e1 * e1 + e2 * e2);
+        uqq += 0.5 * qi * phiq[i];
+        const double q0 = Eq[3 * i], q1 = Eq[3 * i + 1], q2 = Eq[3 * i + 2];
+        mueq += m0 * q0 + m1 * q1 + m2 * q2;
+        muemu += m0 * (e0 - q0) + m1 * (e1 - q1) + m2 * (e2 - q2);
+        if (ai > 0.0) amu += mm / (2.0 * ai);
+    }
+    uqq = block_sum(uqq, sh);
+    mueq = block_sum(mueq, sh);
+    muemu = block_sum(muemu, sh);
+    amu = block_sum(amu, sh);
+    if (threadIdx.x == 0) {
+        partial[0 * kRedBlocks + blockIdx.x] = uqq;
+        partial[1 * kRedBlocks + blockIdx.x] = mueq;
+        partial[2 * kRedBlocks + blockIdx.x] = muemu;
+        partial[3 * kRedBlocks + blockIdx.x] = amu;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+static void reduce(polfmm_ctx* c, int nslot, int s0, int s1, int s2, int s3, int post, int fam) {
+    LaunchScope ls(c, fam);
+    reduce_final_kernel<<<1, kRedThreads, 0, c->stream>>>(c->partial, nslot, s0, s1, s2, s3, c->scal, post);
+}
+
+void gather_sites(polfmm_ctx* c, const double* src, double* dst, int comps) {
+    LaunchScope ls(c, F_ASSEMBLE);
+    gather_kernel<<<grid_for(c->n * comps, 256), 256, 0, c->stream>>>(c->n, comps, c->perm, src, dst);
+}
+
+void scatter_sites(polfmm_ctx* c, const double* src, double* dst, int comps) {
+    LaunchScope ls(c, F_ASSEMBLE);
+    scatter_kernel<<<grid_for(c->n * comps, 256), 256, 0, c->stream>>>(c->n, comps, c->perm, src, dst, 1.0);
+}
+
+void mask_dipoles(polfmm_ctx* c, double* v) {
+    LaunchScope ls(c, F_SOLVER);
+    mask_kernel<<<grid_for(3 * c->n, 256), 256, 0, c->stream>>>(c->n, c->alpha_s, v);
+}
+
+// PCG start: mu (given or alpha E^q), one operator application, residual
+void solver_init(polfmm_ctx* c, bool warm) {
+    if (!warm) {
+        LaunchScope ls(c, F_SOLVER);
+        mu_init_kernel<<<grid_for(3 * c->n, 256), 256, 0, c->stream>>>(c->n, c->alpha_s, c->Eq, c->mu);
+    }
+    if (c->opt.solver == POLFMM_SOLVER_JACOBI) {
+        {
+            LaunchScope ls(c, F_SOLVER);
+            norm_b_kernel<<<kRedBlocks, kRedThreads, 0, c->stream>>>(c->n, c->alpha_s, c->Eq, c->partial);
+        }
+        reduce(c, 1, S_BB, 0, 0, 0, 0, F_SOLVER);
+        return;
+    }
+    fmm_pass(c, LEAF_DIPOLE_E, false, c->mu, nullptr, c->Td, nullptr);
+    {
+        LaunchScope ls(c, F_SOLVER);
+        pcg_init_kernel<<<kRedBlocks, kRedThreads, 0, c->stream>>>(c->n, c->alpha_s, c->Eq, c->mu, c->Td, c->r,
+                                                                    c->z, c->d, c->partial);
+    }
+    reduce(c, 3, S_RZ, S_RR, S_BB, 0, 0, F_SOLVER);
+}
+
+void solver_pcg_step(polfmm_ctx* c) {
+    fmm_pass(c, LEAF_DIPOLE_E, false, c->d, nullptr, c->Td, nullptr);
+    {
+        LaunchScope ls(c, F_SOLVER);
+        pcg_ad_kernel<<<kRedBlocks, kRedThreads, 0, c->stream>>>(c->n, c->alpha_s, c->d, c->Td, c->Ad, c->partial);
+    }
+    reduce(c, 1, S_DAD, 0, 0, 0, 0, F_SOLVER);
+    {
+        LaunchScope ls(c, F_SOLVER);
+        pcg_update_kernel<<<kRedBlocks, kRedThreads, 0, c->stream>>>(c->n, c->alpha_s, c->scal, c->d, c->Ad, c->mu,
+                                                                      c->r, c->z, c->partial);
+    }
+    reduce(c, 2, 0, 0, 0, 0, 1, F_SOLVER);
+    {
+        LaunchScope ls(c, F_SOLVER);
+        pcg_direction_kernel<<<grid_for(3 * c->n, 256), 256, 0, c->stream>>>(c->n, c->scal, c->z, c->d);
+    }
+}
+
+void solver_jacobi_step(polfmm_ctx* c) {
+    fmm_pass(c, LEAF_DIPOLE_E, false, c->mu, nullptr, c->Td, nullptr);
+    {
+        LaunchScope ls(c, F_SOLVER);
+        jacobi_kernel<<<kRedBlocks, kRedThreads, 0, c->stream>>>(c->n, c->alpha_s, c->Eq, c->Td, c->mu, c->partial);
+    }
+    reduce(c, 1, S_RR, 0, 0, 0, 0, F_SOLVER);
+}
+
+void energy_and_gradients(polfmm_ctx* c, double* F, double* dq, double* da, bool want_f, bool want_dq,
+                          bool want_da) {
+    {
+        LaunchScope ls(c, F_ASSEMBLE);
+        assemble_kernel<<<kRedBlocks, kRedThreads, 0, c->stream>>>(
+            c->n, c->perm, c->q_s, c->alpha_s, c->mu, c->phiq, c->Eq, c->phi_t, c->E_t, c->G_t, c->opt.coulomb_k,
+            want_f ? F : nullptr, want_dq ? dq : nullptr, want_da ? da : nullptr, c->partial);
+    }
+    reduce(c, 4, S_UQQ, S_MUEQ, S_MUEMU, S_AMU, 0, F_ASSEMBLE);
+}
+
+}  // namespace polfmm

@@ -1,0 +1,262 @@
+"""GPU path against the CPU oracle, through the C ABI.
+
+FP64 mode must reproduce the oracle's FMM at the same order and tree to
+round-off (1e-10 relative RMS; the arithmetic is the same truncated expansion,
+only evaluated in a different order and normalisation).  MIXED mode must stay
+within 1e-5 relative RMS force error of FP64.  Integer work (leaf cells, root
+cube) must match bit for bit.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_1408_6527_gb300 import PolFMM, PolFMMError  # noqa: E402
+
+FP64_TOL = 1e-10
+MIXED_FORCE_TOL = 1e-5
+
+
+def dev(a):
+    return torch.as_tensor(np.asarray(a), dtype=torch.float64, device="cuda")
+
+
+def host(t):
+    return t.detach().cpu().numpy() if isinstance(t, torch.Tensor) else np.asarray(t)
+
+
+@pytest.fixture(scope="module")
+def w1():
+    return synth.workload(1)
+
+
+@pytest.fixture(scope="module")
+def w2():
+    return synth.workload(2)
+
+
+# ---------------------------------------------------------------------------
+# tree: integer work is bit-exact
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("depth", [1, 3, 5])
+def test_root_box_and_leaf_cells_bit_exact(w1, depth):
+    with PolFMM(dev(w1.pos), dev(w1.q), dev(w1.alpha), p=4, depth=depth) as f:
+        lo, side = f.root_box()
+        cells = host(f.leaf_cells())
+    rlo, rside = oracle.root_box(w1.pos)
+    assert side == rside and np.array_equal(lo, rlo)
+    np.testing.assert_array_equal(cells, oracle.leaf_cells(w1.pos, depth, rlo, rside))
+
+
+def test_tree_box_counts(w2):
+    with PolFMM(dev(w2.pos), dev(w2.q), dev(w2.alpha), p=6, depth=4) as f:
+        info = f.tree_info()
+        lo, side = f.root_box()
+    cells = oracle.leaf_cells(w2.pos, 4, lo, side)
+    for l in range(5):
+        c = cells >> (4 - l)
+        assert info["boxes"][l] == len(np.unique(c[:, 0] + 64 * (c[:, 1] + 64 * c[:, 2])))
+
+
+# ---------------------------------------------------------------------------
+# single passes, FP64 against the oracle FMM (same p, same tree)
+# ---------------------------------------------------------------------------
+
+def _static_case(pos, q, alpha, p, depth):
+    with PolFMM(dev(pos), dev(q), dev(alpha), p=p, depth=depth) as f:
+        st = f.static_field()
+        lo, side = f.root_box()
+    ref = oracle.fmm_fields(pos, q, None, p=p, depth=depth, root=(lo, side))
+    return st, ref
+
+
+@pytest.mark.parametrize("p,depth", [(1, 2), (4, 3), (6, 3), (8, 2), (10, 3)])
+def test_static_field_fp64(w1, p, depth):
+    st, ref = _static_case(w1.pos, w1.q, w1.alpha, p, depth)
+    assert oracle.rel_rms(host(st["E"]), ref["E"]) < FP64_TOL
+    assert oracle.rel_rms(host(st["phi"]), ref["phi"]) < FP64_TOL
+
+
+def test_static_field_fp64_ragged_small():
+    # 37 sites: one partly filled tile, empty boxes, leaves with a single site
+    pos, q, alpha = synth.small_random(31, 37, box=10.0)
+    st, ref = _static_case(pos, q, alpha, 5, 4)
+    assert oracle.rel_rms(host(st["E"]), ref["E"]) < FP64_TOL
+
+
+def test_static_field_fp64_globule_full_size(w2):
+    st, ref = _static_case(w2.pos, w2.q, w2.alpha, w2.p, w2.depth)
+    assert oracle.rel_rms(host(st["E"]), ref["E"]) < FP64_TOL
+    assert oracle.rel_rms(host(st["phi"]), ref["phi"]) < FP64_TOL
+
+
+@pytest.mark.parametrize("p,depth", [(4, 3), (6, 4)])
+def test_dipole_field_fp64(w1, p, depth):
+    rng = np.random.default_rng(3)
+    mu = rng.normal(size=(w1.n, 3))
+    with PolFMM(dev(w1.pos), dev(w1.q), dev(w1.alpha), p=p, depth=depth) as f:
+        E = host(f.dipole_field(dev(mu)))
+        lo, side = f.root_box()
+    ref = oracle.fmm_fields(w1.pos, None, mu, p=p, depth=depth, root=(lo, side))
+    assert oracle.rel_rms(E, ref["E"]) < FP64_TOL
+
+
+def test_total_field_fp64(w1):
+    rng = np.random.default_rng(4)
+    mu = 0.3 * rng.normal(size=(w1.n, 3))
+    with PolFMM(dev(w1.pos), dev(w1.q), dev(w1.alpha), p=5, depth=3) as f:
+        out = f.total_field(dev(mu))
+        lo, side = f.root_box()
+    ref = oracle.fmm_fields(w1.pos, w1.q, mu, p=5, depth=3, root=(lo, side))
+    for k in ("phi", "E", "G"):
+        assert oracle.rel_rms(host(out[k]), ref[k]) < FP64_TOL, k
+
+
+def test_host_buffers_match_device_buffers(w1):
+    with PolFMM(w1.pos, w1.q, w1.alpha, p=4, depth=3) as f:
+        a = f.static_field()
+    with PolFMM(dev(w1.pos), dev(w1.q), dev(w1.alpha), p=4, depth=3) as g:
+        b = g.static_field()
+    np.testing.assert_array_equal(a["E"], host(b["E"]))
+
+
+# ---------------------------------------------------------------------------
+# the solve and the energy / forces
+# ---------------------------------------------------------------------------
+
+def _oracle_fmm_apply(pos, p, depth, root):
+    return lambda v: oracle.fmm_fields(pos, None, v, p=p, depth=depth, root=root)["E"]
+
+
+@pytest.mark.parametrize("iters", [1, 5])
+def test_fixed_iteration_pcg_fp64(w1, iters):
+    with PolFMM(dev(w1.pos), dev(w1.q), dev(w1.alpha), p=4, depth=3, max_iter=iters) as f:
+        info = f.solve(0.0)
+        mu = host(f.dipoles())
+        lo, side = f.root_box()
+        Eq = host(f.static_field()["E"])
+    assert info["iterations"] == iters and not info["converged"]
+    ref_mu, it, res, _ = oracle.pcg_dipole_solve(w1.alpha, Eq, _oracle_fmm_apply(w1.pos, 4, 3, (lo, side)),
+                                                 tol=0.0, max_iter=iters)
+    assert it == iters
+    assert oracle.rel_rms(mu, ref_mu) < 1e-9
+    assert info["residual"] == pytest.approx(res, rel=1e-6)
+
+
+def test_converged_energy_forces_fp64(w1):
+    with PolFMM(dev(w1.pos), dev(w1.q), dev(w1.alpha), p=4, depth=3) as f:
+        info = f.solve(1e-12)
+        out = f.energy_forces()
+        mu = host(f.dipoles())
+        lo, side = f.root_box()
+    assert info["converged"]
+    ref = oracle.polarizable_energy(w1.pos, w1.q, w1.alpha, method="fmm", p=4, depth=3, root=(lo, side),
+                                    tol=1e-13)
+    assert oracle.rel_rms(mu, ref["mu"]) < 1e-9
+    assert out["U"] == pytest.approx(ref["U"], rel=1e-10)
+    assert out["Uqq"] == pytest.approx(ref["Uqq"], rel=1e-10)
+    assert out["Upol"] == pytest.approx(ref["Upol"], rel=1e-9)
+    assert oracle.rel_rms(host(out["F"]), ref["F"]) < 1e-9
+    assert oracle.rel_rms(host(out["dUdq"]), ref["dUdq"]) < 1e-9
+    assert oracle.rel_rms(host(out["dUdalpha"]), ref["dUdalpha"]) < 1e-9
+
+
+def test_against_direct_sum_and_dense_solve(w1):
+    """Against the exact definition (direct sums + dense dipole solve) the error
+    is the FMM truncation error, which falls with p."""
+    ref = oracle.polarizable_energy(w1.pos, w1.q, w1.alpha, method="direct", solve="dense")
+    errs = []
+    for p in (4, 6, 8):
+        with PolFMM(dev(w1.pos), dev(w1.q), dev(w1.alpha), p=p, depth=3) as f:
+            f.solve(1e-12)
+            out = f.energy_forces()
+        errs.append(oracle.rel_rms(host(out["F"]), ref["F"]))
+    assert errs[0] > errs[1] > errs[2]
+    assert errs[0] < 0.05
+
+
+def test_mixed_vs_fp64_force_error(w2):
+    outs = {}
+    for mode in ("fp64", "mixed"):
+        with PolFMM(dev(w2.pos), dev(w2.q), dev(w2.alpha), p=w2.p, depth=w2.depth, mode=mode) as f:
+            info = f.solve(1e-8 if mode == "fp64" else 1e-7)
+            outs[mode] = (f.energy_forces(), host(f.dipoles()), info)
+    F64, Fmx = host(outs["fp64"][0]["F"]), host(outs["mixed"][0]["F"])
+    assert oracle.rel_rms(Fmx, F64) < MIXED_FORCE_TOL
+    assert oracle.rel_rms(outs["mixed"][1], outs["fp64"][1]) < 1e-5
+    assert outs["mixed"][0]["U"] == pytest.approx(outs["fp64"][0]["U"], rel=1e-6)
+
+
+def test_deterministic_repeat(w1):
+    res = []
+    for _ in range(2):
+        with PolFMM(dev(w1.pos), dev(w1.q), dev(w1.alpha), p=4, depth=3, mode="mixed") as f:
+            f.solve(1e-7)
+            res.append(host(f.energy_forces()["F"]))
+    np.testing.assert_array_equal(res[0], res[1])
+
+
+# ---------------------------------------------------------------------------
+# edge cases and errors
+# ---------------------------------------------------------------------------
+
+def test_single_site():
+    with PolFMM(np.zeros((1, 3)), np.array([0.7]), np.array([1.0]), p=3, depth=2) as f:
+        info = f.solve(1e-10)
+        out = f.energy_forces()
+    assert info["iterations"] == 0
+    assert out["U"] == 0.0 and np.all(out["F"] == 0.0)
+
+
+def test_two_sites_closed_form():
+    x = np.array([[0.0, 0.0, 0.0], [2.5, 0.0, 0.0]])
+    Q, al = 0.8, 1.7
+    with PolFMM(x, np.array([Q, 0.0]), np.array([0.0, al]), p=4, depth=3) as f:
+        f.solve(1e-14)
+        out = f.energy_forces()
+        mu = f.dipoles()
+    np.testing.assert_allclose(mu[1], [al * Q / 2.5**2, 0, 0], rtol=1e-12)
+    assert out["Upol"] == pytest.approx(-al * Q * Q / (2 * 2.5**4), rel=1e-12)
+
+
+def test_coincident_sites_status():
+    x = np.array([[0.0, 0.0, 0.0], [1.0, 1.0, 1.0], [1.0, 1.0, 1.0]])
+    with pytest.raises(PolFMMError) as e:
+        PolFMM(x, np.array([1.0, -0.5, -0.5]), np.ones(3), p=3, depth=2)
+    assert e.value.status == 2
+
+
+def test_energy_before_solve_is_a_state_error(w1):
+    with PolFMM(w1.pos, w1.q, w1.alpha, p=4, depth=3) as f:
+        with pytest.raises(PolFMMError) as e:
+            f.energy_forces()
+    assert e.value.status == 6
+
+
+def test_iteration_cap_reports_not_converged(w1):
+    with PolFMM(w1.pos, w1.q, w1.alpha, p=4, depth=3, max_iter=1) as f:
+        info = f.solve(1e-12)
+        assert not info["converged"] and info["status"] == 3 and info["iterations"] == 1
+        f.energy_forces()  # dipoles stay usable
+
+
+def test_alpha_zero_sites_carry_no_dipole(w1):
+    alpha = w1.alpha.copy()
+    alpha[::3] = 0.0
+    with PolFMM(dev(w1.pos), dev(w1.q), dev(alpha), p=4, depth=3) as f:
+        f.solve(1e-12)
+        mu = host(f.dipoles())
+        out = f.energy_forces()
+        lo, side = f.root_box()
+    assert np.all(mu[::3] == 0.0)
+    ref = oracle.polarizable_energy(w1.pos, w1.q, alpha, method="fmm", p=4, depth=3, root=(lo, side), tol=1e-13)
+    assert oracle.rel_rms(host(out["F"]), ref["F"]) < 1e-9
+    assert oracle.rel_rms(host(out["dUdalpha"]), ref["dUdalpha"]) < 1e-9
