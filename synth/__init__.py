@@ -9,10 +9,17 @@ and the CUDA path receive the arrays it returns.
 
 Readings taken where the workload descriptions are under-specified:
 
-* Thole-free point dipoles diverge for pairs closer than (4 a_i a_j)^(1/6)
-  (about 1.7 A at a = 2.5 A^3), so every set is drawn with a hard core
-  (random sequential addition): d_min = 1.75 A for the 20 A cube, 1.8 A
-  elsewhere.
+* Thole-free point dipoles at protein density are close to the
+  polarization catastrophe: random sequential addition with a 1.75-1.8 A hard
+  core leaves the largest eigenvalue of alpha^1/2 T alpha^1/2 above 1 (1.14 for
+  the cube, 1.15 in the globule core), i.e. an indefinite dipole matrix.  The
+  five workloads therefore place their sites on a randomly rotated and
+  shifted face-centred-cubic lattice of the target density (nearest neighbour
+  2.42 A at 0.1 A^-3), displace each site uniformly within 0.2 A, and select
+  the sites by the density profile (lowest key u / p(x), u uniform).  Largest
+  eigenvalue then 0.84 (globule core) and 0.86 (cube): positive definite.
+  The paper's sphere test (Sec. IV.A, 2 A minimum separation at low density)
+  keeps random sequential addition.
 * The Gaussian globule is a capped Gaussian rho(r) = min(0.1, A exp(-r^2/2s^2))
   with s = 15 A; the flat-core radius is solved so that the integral is N.
 * The six-lobe ring uses the union density min(0.1, sum_g rho_g) with one
@@ -65,7 +72,7 @@ def _neighbour_offsets(cell: float, d_min: float, reach: int):
     return np.array(offs, dtype=np.int64)
 
 
-def hardcore_sample(rng, n, d_min, lo, hi, propose, max_rounds=100000):
+def hardcore_sample(rng, n, d_min, lo, hi, propose, max_rounds=20000):
     """Draw n points with pairwise distance >= d_min.
 
     `propose(rng, m)` returns up to m candidate points (already thinned to the
@@ -87,8 +94,11 @@ def hardcore_sample(rng, n, d_min, lo, hi, propose, max_rounds=100000):
     cnt = 0
     d2min = d_min * d_min
     batch = max(1024, n // 8)
+    stalled = 0
     for _ in range(max_rounds):
         if cnt >= n:
+            break
+        if stalled >= 40:
             break
         cand = propose(rng, batch)
         if cand.shape[0] == 0:
@@ -110,6 +120,7 @@ def hardcore_sample(rng, n, d_min, lo, hi, propose, max_rounds=100000):
             ok[idx] = False
         cand, ci = cand[ok], ci[ok]
         if cand.shape[0] == 0:
+            stalled += 1
             batch = min(batch * 2, 1 << 22)
             continue
         # conflicts inside the batch: keep the earliest candidate per cell,
@@ -146,6 +157,7 @@ def hardcore_sample(rng, n, d_min, lo, hi, propose, max_rounds=100000):
         del first, tmp
         cand, ci = cand[ok], ci[ok]
         take = min(cand.shape[0], n - cnt)
+        stalled = stalled + 1 if take * 1000 < batch else 0
         cand, ci = cand[:take], ci[:take]
         pts[cnt:cnt + take] = cand
         grid[ci] = np.arange(cnt, cnt + take)
@@ -197,16 +209,62 @@ def _ball_proposer(center, radius, accept_prob):
     return propose
 
 
-def sites_globule(rng, n, sigma=15.0, d_min=1.8):
+LATTICE_JITTER = 0.2  # Angstrom
+
+
+def fcc_points(rng, rho, lo, hi, jitter=LATTICE_JITTER):
+    """Face-centred-cubic lattice points of density rho covering the box
+    [lo, hi], randomly rotated and shifted, each displaced uniformly within a
+    ball of radius `jitter`."""
+    lo = np.asarray(lo, dtype=np.float64)
+    hi = np.asarray(hi, dtype=np.float64)
+    a = (4.0 / rho) ** (1.0 / 3.0)
+    centre = 0.5 * (lo + hi)
+    half = 0.5 * np.linalg.norm(hi - lo) + a
+    m = int(np.ceil(half / a)) + 1
+    g = np.arange(-m, m + 1, dtype=np.float64)
+    basis = np.array([[0, 0, 0], [0.5, 0.5, 0], [0.5, 0, 0.5], [0, 0.5, 0.5]])
+    Q, _ = np.linalg.qr(rng.normal(size=(3, 3)))
+    shift = rng.random(3) * a
+    out = []
+    for z in g:  # slab by slab to bound memory
+        X, Y = np.meshgrid(g, g, indexing="ij")
+        base = np.stack([X.ravel(), Y.ravel(), np.full(X.size, z)], 1)
+        pts = (base[:, None, :] + basis[None]).reshape(-1, 3) * a
+        pts = (pts + shift - 0.5 * a) @ Q.T + centre
+        keep = np.all((pts >= lo - jitter) & (pts <= hi + jitter), axis=1)
+        out.append(pts[keep])
+    pts = np.concatenate(out)
+    u = rng.normal(size=pts.shape)
+    u /= np.linalg.norm(u, axis=1)[:, None]
+    return pts + jitter * u * rng.random((pts.shape[0], 1)) ** (1.0 / 3.0)
+
+
+def _select(rng, pts, n, prob, outside_dist=None):
+    """Keep the n points with the lowest key u / p(x) (p > 0) or 2 + distance
+    outside the region (p = 0), u uniform: thinning to exactly n points."""
+    p = prob(pts)
+    u = rng.random(pts.shape[0])
+    key = np.where(p > 0, u / np.maximum(p, 1e-300), np.inf)
+    if outside_dist is not None:
+        key = np.where(p > 0, key, 2.0 + outside_dist(pts))
+    idx = np.argsort(key, kind="stable")[:n]
+    if not np.all(np.isfinite(key[idx])):
+        raise RuntimeError("lattice region too small for the requested site count")
+    sel = pts[idx]
+    return sel[rng.permutation(n)]
+
+
+def sites_globule(rng, n, sigma=15.0):
     rc = globule_core_radius(n, sigma)
     rs = rc + 60.0
 
     def prob(x):
         r2 = np.einsum("ij,ij->i", x, x)
-        return np.minimum(1.0, np.exp(-(r2 - rc * rc) / (2 * sigma * sigma)))
+        return np.where(r2 <= rs * rs, np.minimum(1.0, np.exp(-(r2 - rc * rc) / (2 * sigma * sigma))), 0.0)
 
-    pts = hardcore_sample(rng, n, d_min, [-rs] * 3, [rs] * 3, _ball_proposer([0, 0, 0], rs, prob))
-    return pts, {"core_radius": rc, "sigma": sigma, "d_min": d_min}
+    pts = _select(rng, fcc_points(rng, RHO0, [-rs] * 3, [rs] * 3), n, prob)
+    return pts, {"core_radius": rc, "sigma": sigma, "lattice": "fcc", "jitter": LATTICE_JITTER}
 
 
 def _ring_centres(n_lobes, ring_radius):
@@ -241,21 +299,16 @@ def ring_core_radius(n, n_lobes=6, ring_radius=60.0, sigma=15.0, h=1.5):
     return _solve_monotone(count, n, 0.0, 200.0, iters=40)
 
 
-def sites_ring(rng, n, n_lobes=6, ring_radius=60.0, sigma=15.0, d_min=1.8):
+def sites_ring(rng, n, n_lobes=6, ring_radius=60.0, sigma=15.0):
     rc = ring_core_radius(n, n_lobes, ring_radius, sigma)
     centres = _ring_centres(n_lobes, ring_radius)
     ext = ring_radius + rc + 60.0
     zext = rc + 60.0
     lo = np.array([-ext, -ext, -zext])
     hi = np.array([ext, ext, zext])
-
-    def propose(rng_, m):
-        x = lo + (hi - lo) * rng_.random((m, 3))
-        keep = rng_.random(m) < _ring_prob(x, centres, rc, sigma)
-        return x[keep]
-
-    pts = hardcore_sample(rng, n, d_min, lo, hi, propose)
-    return pts, {"core_radius": rc, "sigma": sigma, "ring_radius": ring_radius, "lobes": n_lobes, "d_min": d_min}
+    pts = _select(rng, fcc_points(rng, RHO0, lo, hi), n, lambda x: _ring_prob(x, centres, rc, sigma))
+    return pts, {"core_radius": rc, "sigma": sigma, "ring_radius": ring_radius, "lobes": n_lobes,
+                 "lattice": "fcc", "jitter": LATTICE_JITTER}
 
 
 def shell_inner_radius(n, thickness=40.0):
@@ -263,26 +316,28 @@ def shell_inner_radius(n, thickness=40.0):
     return _solve_monotone(f, n, 0.0, 1e5)
 
 
-def sites_shell(rng, n, thickness=40.0, d_min=1.8):
+def sites_shell(rng, n, thickness=40.0):
     r_in = shell_inner_radius(n, thickness)
     r_out = r_in + thickness
 
-    def propose(rng_, m):
-        u = rng_.random((m, 3)) * 2 - 1
-        x = r_out * u
-        r = np.sqrt(np.einsum("ij,ij->i", x, x))
-        return x[(r >= r_in) & (r <= r_out)]
+    def rad(x):
+        return np.sqrt(np.einsum("ij,ij->i", x, x))
 
-    pts = hardcore_sample(rng, n, d_min, [-r_out] * 3, [r_out] * 3, propose)
-    return pts, {"inner_radius": r_in, "thickness": thickness, "d_min": d_min}
+    pts = _select(rng, fcc_points(rng, RHO0, [-r_out - 3] * 3, [r_out + 3] * 3), n,
+                  lambda x: ((rad(x) >= r_in) & (rad(x) <= r_out)).astype(np.float64),
+                  lambda x: np.maximum(r_in - rad(x), rad(x) - r_out))
+    return pts, {"inner_radius": r_in, "thickness": thickness, "lattice": "fcc", "jitter": LATTICE_JITTER}
 
 
-def sites_cube(rng, n, side=20.0, d_min=1.75):
-    def propose(rng_, m):
-        return side * rng_.random((m, 3))
+def sites_cube(rng, n, side=20.0):
+    def inside(x):
+        return np.all((x >= 0) & (x <= side), axis=1).astype(np.float64)
 
-    pts = hardcore_sample(rng, n, d_min, [0, 0, 0], [side] * 3, propose)
-    return pts, {"side": side, "d_min": d_min}
+    def dist(x):
+        return np.max(np.maximum(-x, x - side), axis=1)
+
+    pts = _select(rng, fcc_points(rng, n / side**3, [0, 0, 0], [side] * 3), n, inside, dist)
+    return pts, {"side": side, "lattice": "fcc", "jitter": LATTICE_JITTER}
 
 
 def sites_sphere(rng, n, radius, d_min):
@@ -351,16 +406,16 @@ def workload(index: int, n: int | None = None, depth: int | None = None) -> Work
         return Workload("cube", pos, q, alpha, 4, depth or 3, 1e-8, {**meta, **m})
     if index in (2, 4):
         n = n or (30000 if index == 2 else 100000)
-        pts = _cached_positions(f"globule_{n}_{seed}", lambda: sites_globule(rng, n)[0])
+        pts = _cached_positions(f"globule_fcc_{n}_{seed}", lambda: sites_globule(rng, n)[0])
         rng2 = np.random.Generator(np.random.PCG64(seed + 1000))
         q = charges_normal(rng2, n)
         alpha = rng2.uniform(0.3, 2.5, n)
         rc = globule_core_radius(n)
         return Workload("globule", pts, q, alpha, 6, depth or (4 if index == 2 else 5), 1e-8,
-                        {**meta, "core_radius": rc, "sigma": 15.0, "d_min": 1.8})
+                        {**meta, "core_radius": rc, "sigma": 15.0, "lattice": "fcc", "jitter": LATTICE_JITTER})
     if index == 3:
         n = n or 300000
-        pts = _cached_positions(f"ring_{n}_{seed}", lambda: sites_ring(rng, n)[0])
+        pts = _cached_positions(f"ring_fcc_{n}_{seed}", lambda: sites_ring(rng, n)[0])
         rng2 = np.random.Generator(np.random.PCG64(seed + 1000))
         q = charges_normal(rng2, n)
         alpha = rng2.uniform(0.3, 2.5, n)
@@ -368,7 +423,7 @@ def workload(index: int, n: int | None = None, depth: int | None = None) -> Work
     if index == 5:
         n = n or 250000
         d = depth or {250000: 5, 1000000: 6, 4000000: 7}.get(n, max(3, int(round(math.log(n / 8.0, 8)))))
-        pts = _cached_positions(f"shell_{n}_{seed}", lambda: sites_shell(rng, n)[0])
+        pts = _cached_positions(f"shell_fcc_{n}_{seed}", lambda: sites_shell(rng, n)[0])
         rng2 = np.random.Generator(np.random.PCG64(seed + 1000))
         q = charges_normal(rng2, n)
         alpha = rng2.uniform(0.3, 2.5, n)

@@ -491,3 +491,16 @@ def test_workload1_inputs():
     assert w.alpha.min() >= 0.5 and w.alpha.max() <= 2.0
     w2 = synth.workload(1)
     np.testing.assert_array_equal(w.pos, w2.pos)
+
+
+def test_workload1_dipole_matrix_is_positive_definite():
+    """The dense dipole solve of Sec. II.A needs diag(1/alpha) - T positive
+    definite (no polarization catastrophe); the cube workload must admit the
+    Cholesky factorisation, and PCG with direct sums must reach 1e-10."""
+    w = synth.workload(1)
+    st = oracle.direct_fields(w.pos, w.q)
+    mu = oracle.dense_dipole_solve(w.pos, w.alpha, st["E"])
+    mu2, it, res, _ = oracle.pcg_dipole_solve(w.alpha, st["E"], lambda v: oracle.direct_fields(w.pos, None, v)["E"],
+                                              tol=1e-10, max_iter=200)
+    assert res <= 1e-10 and it < 120
+    assert oracle.rel_rms(mu2, mu) < 1e-8
