@@ -1,0 +1,386 @@
+"""Throughput of the polarizable FMM energy + forces step on one GB300 (atoms/s).
+
+Workload: the 30,000-site protein-density globule (Gaussian profile, sigma
+15 A, 0.1 sites/A^3), charges N(0, 0.35) e neutralised, polarizabilities
+U(0.3, 2.5) A^3, expansion order p = 6, octree depth 4.
+
+One step = the whole hot path on a persistent context: rebuild the octree
+from HBM-resident positions and run the static pass (fmm_update_positions),
+solve the induced dipoles from mu = alpha E^q to the relative residual
+tolerance (fmm_solve_induced_dipoles), then one more FMM pass for energy,
+forces and parameter gradients (fmm_energy_forces).  The headline `value` is
+MIXED precision; the all-FP64 GPU form is timed beside it and the relative RMS
+force error of MIXED against FP64 is reported.
+
+The inputs (1.2 MB) are far smaller than L2, so L2 is flushed (a 256 MB write)
+before every timed step, outside the step's CUDA-event interval.
+
+--impl reference times the CPU oracle (test infrastructure) on the host cores
+on the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "atoms/s polarizable FMM energy+forces, mixed vs FP64, at ≤1e-5 RMS force err"
+WORKLOAD_INDEX = 2
+TOL = {"mixed": 1e-6, "fp64": 1e-8}
+FP32_LANES_PER_SM = 128
+NUM_SMS = 152
+SM_MAX_MHZ = 2070.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--mode", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
+    ap.add_argument("--m2l", default="auto", choices=["auto", "simt", "tensor"])
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# algorithmic work of one pass (counted from the tree, not from the kernels)
+# ---------------------------------------------------------------------------
+
+def ncoef(p):
+    return (p + 1) * (p + 2) * (p + 3) // 6
+
+
+def m2l_flops_per_box_pair(p):
+    # 2 flops per retained term of F_n += sum_{|m| <= p-|n|} D_{n+m} M_m
+    return 2 * sum((s + 1) * (s + 2) // 2 * ncoef(p - s) for s in range(p + 1))
+
+
+def tree_work(pos, depth, lo, side):
+    """Near-field pairs (ordered, i != j, adjacent leaves) and far-field box
+    pairs (the 189-offset interaction lists, occupied sources only)."""
+    ns = 1 << depth
+    h = side / ns
+    cell = np.clip(np.floor((pos - lo) / h).astype(np.int64), 0, ns - 1)
+    lin = cell[:, 0] + ns * (cell[:, 1] + ns * cell[:, 2])
+    cnt = np.bincount(lin, minlength=ns ** 3).reshape(ns, ns, ns).transpose(2, 1, 0)  # [x][y][z]
+    pad = np.pad(cnt, 1)
+    nb = np.zeros_like(cnt)
+    for dx in (-1, 0, 1):
+        for dy in (-1, 0, 1):
+            for dz in (-1, 0, 1):
+                nb += pad[1 + dx:1 + dx + ns, 1 + dy:1 + dy + ns, 1 + dz:1 + dz + ns]
+    near_pairs = int(np.sum(cnt * nb) - pos.shape[0])
+    box_pairs = 0
+    for l in range(2, depth + 1):
+        m = 1 << l
+        occ = np.zeros((m, m, m), dtype=bool)
+        c = cell >> (depth - l)
+        occ[c[:, 0], c[:, 1], c[:, 2]] = True
+        tx, ty, tz = np.nonzero(occ)
+        for ox in range(-3, 4):
+            for oy in range(-3, 4):
+                for oz in range(-3, 4):
+                    if max(abs(ox), abs(oy), abs(oz)) <= 1:
+                        continue
+                    ok = np.ones(tx.shape, dtype=bool)
+                    for t, o in ((tx, ox), (ty, oy), (tz, oz)):
+                        b = t & 1
+                        ok &= (o >= b - 3) & (o <= b + 2)
+                    sx, sy, sz = tx - ox, ty - oy, tz - oz
+                    ok &= (sx >= 0) & (sy >= 0) & (sz >= 0) & (sx < m) & (sy < m) & (sz < m)
+                    ok[ok] &= occ[sx[ok], sy[ok], sz[ok]]
+                    box_pairs += int(ok.sum())
+    return near_pairs, box_pairs
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.proc = None
+        self.out = []
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.out.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.out:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for k, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(k)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        return run_reference(args)
+    if world > 1:
+        import torch
+        import torch.distributed as tdist
+
+        torch.cuda.set_device(local_rank)
+        tdist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    out = run_gpu(args, rank, world, local_rank)
+    if rank == 0 and out is not None:
+        print(json.dumps(out))
+    if world > 1:
+        import torch.distributed as tdist
+
+        tdist.destroy_process_group()
+
+
+def run_gpu(args, rank, world, local_rank):
+    import torch
+
+    from paper_1408_6527_gb300 import PolFMM
+    import synth
+
+    torch.cuda.set_device(local_rank)
+    dist = world > 1
+    if dist:
+        import torch.distributed as tdist
+    w = synth.workload(WORKLOAD_INDEX)
+    n = w.n
+    dev = lambda a: torch.as_tensor(a, dtype=torch.float64, device="cuda")
+    pos_d, q_d, a_d = dev(w.pos), dev(w.q), dev(w.alpha)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def make(mode, src=None, profile=False):
+        s = src if src is not None else (pos_d, q_d, a_d)
+        return PolFMM(*s, p=w.p, depth=w.depth, mode=mode, max_iter=500, m2l=args.m2l, profile=profile)
+
+    def step(ctx, mode, pos):
+        ctx.update_positions(pos)
+        ctx.reset_dipoles()
+        info = ctx.solve(TOL[mode])
+        out = ctx.energy_forces()
+        return info, out
+
+    def timed(ctx, mode, steps, warmup, sample_clocks=False):
+        for _ in range(warmup):
+            step(ctx, mode, pos_d)
+        torch.cuda.synchronize()
+        if dist:
+            tdist.barrier()
+        torch.cuda.synchronize()
+        sampler = ClockSampler(local_rank) if sample_clocks else None
+        total_ms, iters = 0.0, []
+        l0 = ctx.launch_count()
+        info = out = None
+        for _ in range(steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            info, out = step(ctx, mode, pos_d)
+            e1.record(stream)
+            e1.synchronize()
+            total_ms += e0.elapsed_time(e1)
+            iters.append(info["iterations"])
+        launches = ctx.launch_count() - l0
+        torch.cuda.synchronize()
+        if dist:
+            tdist.barrier()
+        clocks = sampler.stop() if sampler else None
+        return total_ms, iters, launches, info, out, clocks
+
+    ctx = make(args.mode)
+    total_ms, iters, launches, info, out, clocks = timed(ctx, args.mode, args.steps, args.warmup, True)
+    if dist:
+        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    F_main = out["F"].detach().cpu().numpy()
+    lo, side = ctx.root_box()
+    ctx.close()
+    if rank != 0:
+        return None
+    ms_per_step = total_ms / args.steps
+    value = world * n * args.steps / (total_ms / 1e3)
+
+    # the other precision on the same workload
+    other = "fp64" if args.mode == "mixed" else "mixed"
+    ctx2 = make(other)
+    t2, it2, _, info2, out2, _ = timed(ctx2, other, max(2, args.steps // 2), 1)
+    F_other = out2["F"].detach().cpu().numpy()
+    ctx2.close()
+    F64, Fmx = (F_other, F_main) if other == "fp64" else (F_main, F_other)
+    rms_err = float(np.sqrt(np.sum((Fmx - F64) ** 2) / np.sum(F64 ** 2)))
+    n2 = max(2, args.steps // 2)
+
+    # per-kernel CUDA-event durations, recorded on the launching stream over
+    # separately profiled steps of the same workload
+    ctxp = make(args.mode, profile=True)
+    for _ in range(2):
+        step(ctxp, args.mode, pos_d)
+    ctxp.profile_reset()
+    for _ in range(3):
+        flush.zero_()
+        step(ctxp, args.mode, pos_d)
+    fams = ["tree", "p2m", "m2m", "m2l", "l2l", "leaf_dipole", "leaf_static", "leaf_full", "solver", "assemble"]
+    prof = {f: ctxp.profile(f) for f in fams}
+    ctxp.close()
+    prof_total = sum(v[0] for v in prof.values())
+
+    # roofline of the dominant kernel family (FP32 ALU in MIXED mode)
+    near_pairs, box_pairs = tree_work(w.pos, w.depth, lo, side)
+    dom = max(prof, key=lambda f: prof[f][0])
+    p = w.p
+    flops = {
+        # dipole -> field pair: 34 flops (FMA = 2, rsqrt = 1); L2P field: 6 per coefficient of order <= p-1
+        "leaf_dipole": near_pairs * 34 + n * 6 * ncoef(p - 1),
+        "m2l": box_pairs * m2l_flops_per_box_pair(p),
+    }
+    roof = None
+    if dom in flops and prof[dom][1] > 0:
+        dur_s = prof[dom][0] / prof[dom][1] / 1e3
+        achieved = flops[dom] / dur_s / 1e12
+        sm_mhz = SM_MAX_MHZ
+        peak = NUM_SMS * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12 if args.mode == "mixed" else None
+        if args.mode == "fp64":
+            peak = 1.25  # nominal FP64 TFLOP/s of GB300 (no measured FP64 peak on this machine)
+        roof = {"kernel": dom, "bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 2),
+                "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": None,
+                "peak_note": "FP32 FMA: 152 SMs x 128 lanes x 2 flops x 2070 MHz (nominal)" if args.mode == "mixed"
+                else "FP64 nominal", "avg_launch_ms": round(prof[dom][0] / prof[dom][1], 4),
+                "algorithmic_flops_per_launch": int(flops[dom])}
+
+    # e2e: the same step through the public API with pinned host buffers
+    pos_h = torch.from_numpy(w.pos.copy()).pin_memory()
+    ctxh = PolFMM(w.pos, w.q, w.alpha, p=w.p, depth=w.depth, mode=args.mode, max_iter=500, m2l=args.m2l)
+    for _ in range(args.warmup):
+        step(ctxh, args.mode, pos_h)
+    e2e_s = 0.0
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        s0 = time.perf_counter()
+        step(ctxh, args.mode, pos_h)
+        e2e_s += time.perf_counter() - s0
+    ctxh.close()
+    e2e = {"value": round(world * n * args.steps / e2e_s, 1), "unit": "atoms/s",
+           "h2d_bytes_per_step": 3 * n * 8, "d2h_bytes_per_step": 5 * n * 8 + 24}
+
+    result = {
+        "metric": METRIC, "value": round(value, 1), "unit": "atoms/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64" if args.mode == "mixed" else "f64", "data": "synthetic",
+        "config": {"workload": f"globule {n} sites p={w.p} depth={w.depth} {args.mode}", "n_sites": n, "p": w.p,
+                   "depth": w.depth, "mode": args.mode, "tol": TOL[args.mode], "m2l": args.m2l,
+                   "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "flushed before every step (256 MB write, outside the step interval)"},
+        "iterations": iters[-1], "converged": bool(info["converged"]),
+        "rms_force_err_mixed_vs_fp64": rms_err,
+        other: {"value": round(n * n2 / (t2 / 1e3), 1), "ms_per_step": round(t2 / n2, 4), "iterations": it2[-1]},
+        "gpu_launches": int(launches),
+        "kernel_ms_per_step": {f: round(v[0] / 3, 4) for f, v in prof.items()},
+        "kernel_share": {f: round(v[0] / prof_total, 4) for f, v in prof.items()} if prof_total > 0 else None,
+        "roofline": roof, "clocks": clocks, "e2e": e2e,
+        "tree": {"near_pairs": near_pairs, "m2l_box_pairs": box_pairs},
+    }
+    if world == 1 and not args.no_cpu:
+        result["cpu_baseline"] = cpu_baseline(w, lo, side)
+    return result
+
+
+def cpu_baseline(w, lo, side, tol=None):
+    """The CPU oracle as it stands on the host cores: one complete step on the
+    full workload (FMM static pass, PCG with FMM matrix-vector products to the
+    FP64 tolerance, force pass)."""
+    import oracle
+
+    tol = tol if tol is not None else TOL["fp64"]
+    t0 = time.perf_counter()
+    out = oracle.polarizable_energy(w.pos, w.q, w.alpha, method="fmm", p=w.p, depth=w.depth, root=(lo, side),
+                                    tol=tol, max_iter=500)
+    dt = time.perf_counter() - t0
+    return {"value": round(w.n / dt, 1), "unit": "atoms/s", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"one complete step of the full {w.n}-site workload (FP64 CPU FMM p={w.p} depth={w.depth}, "
+                      f"{out['iterations']} PCG iterations to {tol:g}, force pass): {dt:.2f} s"}
+
+
+def run_reference(args):
+    import synth
+    import oracle
+
+    w = synth.workload(WORKLOAD_INDEX)
+    lo, side = oracle.root_box(w.pos)
+    for _ in range(args.warmup):
+        cpu_baseline(w, lo, side, TOL[args.mode])
+    total = 0.0
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.polarizable_energy(w.pos, w.q, w.alpha, method="fmm", p=w.p, depth=w.depth, root=(lo, side),
+                                  tol=TOL[args.mode], max_iter=500)
+        total += time.perf_counter() - t0
+    value = w.n * args.steps / total
+    cores = oracle.num_threads()
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": round(value, 2), "unit": "atoms/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * total / args.steps, 2),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"globule {w.n} sites p={w.p} depth={w.depth} {args.mode}", "n_sites": w.n,
+                   "p": w.p, "depth": w.depth, "mode": args.mode, "tol": TOL[args.mode]},
+        "cpu_baseline": {"value": round(value, 2), "unit": "atoms/s", "cores": cores, "kind": "oracle",
+                         "sample": "each step one complete oracle step of the full workload"},
+        "e2e": {"value": round(value, 2), "unit": "atoms/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+if __name__ == "__main__":
+    main()

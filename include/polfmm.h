@@ -148,6 +148,9 @@ POLFMM_API int fmm_get_dipoles(polfmm_ctx* ctx, double* mu, int on_device);
  * energy evaluation; entries at sites with alpha = 0 are ignored (set to 0). */
 POLFMM_API int fmm_set_dipoles(polfmm_ctx* ctx, const double* mu, int on_device);
 
+/* Forget the current dipoles: the next solve starts again from mu = alpha E^q. */
+POLFMM_API int fmm_reset_dipoles(polfmm_ctx* ctx);
+
 /* New positions for the same sites: rebuild the tree and the static pass,
  * keeping the current dipoles as the next solve's starting guess. */
 POLFMM_API int fmm_update_positions(polfmm_ctx* ctx, const double* positions, int on_device);
@@ -180,7 +183,9 @@ POLFMM_API int fmm_root_box(polfmm_ctx* ctx, double* lo, double* side);
 
 /* Profiling (options.profile = 1): total CUDA-event milliseconds and launch
  * count of one kernel family since the last reset.  Families: "tree", "p2m",
- * "m2m", "m2l", "l2l", "leaf" (L2P + near field), "solver", "assemble".
+ * "m2m", "m2l", "l2l", "leaf_dipole" (L2P + near field of the solver's
+ * dipole-field pass), "leaf_static" (same, static pass), "leaf_full" (same,
+ * energy / force pass), "solver", "assemble".
  * Unknown names return POLFMM_ERR_INVALID_ARG. */
 POLFMM_API int fmm_profile_get(polfmm_ctx* ctx, const char* family, double* total_ms, int64_t* launches);
 POLFMM_API int fmm_profile_reset(polfmm_ctx* ctx);

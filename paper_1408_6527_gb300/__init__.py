@@ -160,6 +160,9 @@ class PolFMM:
         b = self._in(mu, (self.n, 3))
         _lib.check(self.lib.fmm_set_dipoles(self.h, b.ptr, int(self.device)), "fmm_set_dipoles")
 
+    def reset_dipoles(self):
+        _lib.check(self.lib.fmm_reset_dipoles(self.h), "fmm_reset_dipoles")
+
     def update_positions(self, pos):
         b = self._in(pos, (self.n, 3))
         _lib.check(self.lib.fmm_update_positions(self.h, b.ptr, int(self.device)), "fmm_update_positions")

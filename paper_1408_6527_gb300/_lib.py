@@ -58,6 +58,7 @@ SIGNATURES = {
     "fmm_get_dipoles": (I, [P, P, I]),
     "fmm_set_dipoles": (I, [P, P, I]),
     "fmm_update_positions": (I, [P, P, I]),
+    "fmm_reset_dipoles": (I, [P]),
     "fmm_static_field": (I, [P, P, P, I]),
     "fmm_dipole_field": (I, [P, P, P, I]),
     "fmm_total_field": (I, [P, P, P, P, P, I]),

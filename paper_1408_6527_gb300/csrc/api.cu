@@ -656,6 +656,12 @@ int fmm_set_dipoles(polfmm_ctx* c, const double* mu, int on_device) {
     return read_err(c);
 }
 
+int fmm_reset_dipoles(polfmm_ctx* c) {
+    if (!c) return POLFMM_ERR_INVALID_ARG;
+    c->have_mu = false;
+    return POLFMM_OK;
+}
+
 int fmm_update_positions(polfmm_ctx* c, const double* positions, int on_device) {
     if (!c || !positions) return POLFMM_ERR_INVALID_ARG;
     const int64_t n = c->n;
@@ -736,7 +742,7 @@ int fmm_root_box(polfmm_ctx* c, double* lo, double* side) {
 }
 
 int fmm_profile_get(polfmm_ctx* c, const char* family, double* total_ms, int64_t* launches) {
-    static const char* names[F_COUNT] = {"tree", "p2m", "m2m", "m2l", "l2l", "leaf", "solver", "assemble"};
+    static const char* names[F_COUNT] = {"tree", "p2m", "m2m", "m2l", "l2l", "leaf_dipole", "leaf_static", "leaf_full", "solver", "assemble"};
     if (!c || !family) return POLFMM_ERR_INVALID_ARG;
     profile_flush(c);
     for (int f = 0; f < F_COUNT; f++)

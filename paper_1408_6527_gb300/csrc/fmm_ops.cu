@@ -495,7 +495,7 @@ static void launch_leaf(polfmm_ctx* c, int mode, const double* mu_sorted, double
     const R h = R(c->side / (double)(1 << c->depth));
     size_t smem = sizeof(R) * c->ncoef;
     const Tables& T = c->tab;
-    LaunchScope ls(c, F_LEAF);
+    LaunchScope ls(c, mode == LEAF_DIPOLE_E ? F_LEAF_DIPOLE : (mode == LEAF_CHARGE_PHI_E ? F_LEAF_STATIC : F_LEAF_FULL));
 #define LEAF_ARGS                                                                                              \
     L.nbox, L.key, c->lstart, c->lcount, L.map, c->depth, (const R*)c->ploc, c->q_s, mu_sorted, (const R*)L.L, \
         c->ld, c->ncoef, T.mi, T.inv_fact, T.up1, T.up2, h, phi, E, G, c->err
