@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--mode", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
     ap.add_argument("--m2l", default="auto", choices=["auto", "simt", "tensor"])
+    ap.add_argument("--only-main", action="store_true",
+                    help="time the headline mode only (no FP64 leg, profiling, e2e or CPU leg): for ncu captures")
     return ap.parse_args()
 
 
@@ -252,6 +254,9 @@ def run_gpu(args, rank, world, local_rank):
         return None
     ms_per_step = total_ms / args.steps
     value = world * n * args.steps / (total_ms / 1e3)
+    if args.only_main:
+        return {"metric": METRIC, "value": round(value, 1), "unit": "atoms/s", "ms_per_step": round(ms_per_step, 4),
+                "iterations": iters[-1], "gpu_launches": int(launches), "only_main": True}
 
     # the other precision on the same workload
     other = "fp64" if args.mode == "mixed" else "mixed"
