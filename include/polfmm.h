@@ -193,6 +193,43 @@ POLFMM_API int fmm_profile_reset(polfmm_ctx* ctx);
 /* Count of the library's own kernel launches on this context since creation. */
 POLFMM_API int64_t fmm_launch_count(polfmm_ctx* ctx);
 
+/*
+ * Allocation-free tree set-up.  The paper has no counterpart: this entry point
+ * exists for callers that cannot call cudaMalloc -- code whose host framework
+ * owns all device memory through its own pool, or a time-critical loop that
+ * cannot afford the device-wide synchronisation that cudaMalloc and cudaFree
+ * imply.  It computes, without allocating anything (no cudaMalloc, cudaFree or
+ * allocating library routine), what fmm_build computes first: the root cube
+ * (same rule as fmm_build), the leaf cell of every site, the Morton keys of
+ * the cells and the stable sort of the sites by key.
+ *
+ * n              sites, 1 <= n <= POLFMM_NOALLOC_MAX_SITES (larger n: the call
+ *                returns POLFMM_ERR_INVALID_ARG and does nothing).
+ * positions      device, n x 3 float64 (caller order).
+ * tree_depth     leaf level in [1, 8].
+ * root_lo, root_side  host outputs: lower corner (3) and side of the root cube.
+ * cells          device output, n x 3 int32: leaf cell of each site (caller order).
+ * keys           device output, n uint32: Morton keys of the leaf cells in
+ *                ascending order.
+ * perm           device output, n int32: perm[k] = caller index of the site
+ *                with the k-th key; sites with equal keys keep caller order.
+ * cuda_stream    cudaStream_t (NULL = legacy default stream); the call returns
+ *                after the stream has finished its work.
+ *
+ * All temporaries live in one static device array of about 2.3 MB that every
+ * device which loads the library holds until the process exits.  The first
+ * call on a device looks up that array's device address (cudaGetSymbolAddress,
+ * with that device current), so that first call should come before any stream
+ * capture.  Every call shares the array and it keeps the previous call's
+ * contents: calls that overlap on the GPU (several streams, threads or
+ * devices sharing a context) race and must be serialised by the caller.
+ * Non-finite positions return POLFMM_ERR_INVALID_ARG.
+ */
+#define POLFMM_NOALLOC_MAX_SITES 262144
+POLFMM_API int fmm_sort_sites_noalloc(int64_t n, const double* positions, int tree_depth, double* root_lo,
+                                      double* root_side, int32_t* cells, uint32_t* keys, int32_t* perm,
+                                      void* cuda_stream);
+
 /* Release every device buffer of the context; NULL is a no-op. */
 POLFMM_API void fmm_destroy(polfmm_ctx* ctx);
 

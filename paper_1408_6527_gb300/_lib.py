@@ -25,6 +25,7 @@ SOLVER_JACOBI = 1
 M2L_AUTO = 0
 M2L_SIMT = 1
 M2L_TENSOR = 2
+NOALLOC_MAX_SITES = 262144
 
 
 class Options(ctypes.Structure):
@@ -69,6 +70,7 @@ SIGNATURES = {
     "fmm_profile_reset": (I, [P]),
     "fmm_launch_count": (I64, [P]),
     "fmm_destroy": (None, [P]),
+    "fmm_sort_sites_noalloc": (I, [I64, P, I, P, P, P, P, P, P]),
     "fmm_status_string": (ctypes.c_char_p, [I]),
 }
 

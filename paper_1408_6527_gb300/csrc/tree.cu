@@ -9,6 +9,8 @@
 // integer offset between boxes.
 #include <math.h>
 
+#include <mutex>
+
 #include "internal.cuh"
 
 namespace polfmm {
@@ -541,4 +543,144 @@ int tree_root_box(polfmm_ctx* c, const double* x_dev, double* part_dev, double* 
     return POLFMM_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Allocation-free variant of the tree set-up (fmm_sort_sites_noalloc).
+//
+// Some callers cannot call cudaMalloc: code whose host framework owns every
+// byte of device memory through its own pool, or a time-critical loop that
+// cannot afford the device-wide synchronisation of cudaMalloc / cudaFree.
+// For them this variant runs the bounding-cube reduction, the Morton keys and
+// the stable radix sort with all temporaries in one file-scope device array of
+// fixed size instead of context-owned buffers.  The paper has no counterpart.
+// ---------------------------------------------------------------------------
+constexpr int64_t kNoAllocMaxSites = POLFMM_NOALLOC_MAX_SITES;
+constexpr int kNoAllocTiles = (int)((kNoAllocMaxSites + kSortTile - 1) / kSortTile);
+constexpr size_t kNAKeys = 0;                                                // uint32 [max sites]
+constexpr size_t kNAVals = kNAKeys + 4 * (size_t)kNoAllocMaxSites;          // int32 [max sites]
+constexpr size_t kNACounts = kNAVals + 4 * (size_t)kNoAllocMaxSites;        // int32 [2 * 256 * tiles]
+constexpr size_t kNAScan = kNACounts + 4 * 2 * 256 * (size_t)kNoAllocTiles;  // int32 [4096]
+constexpr size_t kNABBox = kNAScan + 4 * 4096;                               // double [1024]
+constexpr size_t kNAErr = kNABBox + 8 * 1024;                                // int32 [64]
+constexpr size_t kNoAllocBytes = kNAErr + 256;
+
+// Held by every device that loads the library, until the process exits.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+static std::mutex g_noalloc_mutex;
+static void* g_noalloc_ptr[64];
+
+// Device address of the scratch array on the current device.  The host-side
+// name g_noalloc_scratch is not a device address; it is resolved once per
+// device with cudaGetSymbolAddress, with that device current.
+static int noalloc_scratch(unsigned char** out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+        cudaGetLastError();
+        return POLFMM_ERR_CUDA;
+    }
+    std::lock_guard<std::mutex> guard(g_noalloc_mutex);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || p == nullptr) {
+            cudaGetLastError();
+            return POLFMM_ERR_CUDA;
+        }
+        g_noalloc_ptr[dev] = p;
+    }
+    *out = reinterpret_cast<unsigned char*>(g_noalloc_ptr[dev]);
+    return POLFMM_OK;
+}
+
+__global__ void cells_from_keys_kernel(const uint32_t* __restrict__ key, int64_t n, int32_t* __restrict__ cells) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint32_t k = key[i];
+    cells[3 * i] = (int32_t)compact3(k);
+    cells[3 * i + 1] = (int32_t)compact3(k >> 1);
+    cells[3 * i + 2] = (int32_t)compact3(k >> 2);
+}
+
+static void noalloc_scan(cudaStream_t st, const int* in, int* out, int n, int* scratch) {
+    int nb = grid_for(n, kScanTile);
+    int* sums = scratch;
+    int* offs = scratch + nb;
+    scan_block_kernel<<<nb, kScanThreads, 0, st>>>(in, out, nullptr, n, sums);
+    if (nb == 1) return;
+    noalloc_scan(st, sums, offs, nb, scratch + 2 * nb);
+    scan_add_kernel<<<nb, kScanThreads, 0, st>>>(out, nullptr, n, offs);
+}
+
+static void noalloc_radix_pass(cudaStream_t st, const uint32_t* kin, const int* vin, uint32_t* kout, int* vout,
+                               int n, int shift, int* counts, int* scan_scratch) {
+    int ntiles = grid_for(n, kSortTile);
+    radix_hist_kernel<8><<<ntiles, kSortThreads, 0, st>>>(kin, nullptr, n, shift, ntiles, counts);
+    noalloc_scan(st, counts, counts + 256 * ntiles, 256 * ntiles, scan_scratch);
+    radix_scatter_kernel<8><<<ntiles, kSortThreads, 0, st>>>(kin, vin, kout, vout, nullptr, n, shift, ntiles,
+                                                            counts + 256 * ntiles);
+}
+
 }  // namespace polfmm
+
+extern "C" POLFMM_API int fmm_sort_sites_noalloc(int64_t n, const double* positions, int tree_depth, double* root_lo,
+                                      double* root_side, int32_t* cells, uint32_t* keys, int32_t* perm,
+                                      void* cuda_stream) {
+    using namespace polfmm;
+    if (n < 1 || !positions || !root_lo || !root_side || !cells || !keys || !perm) return POLFMM_ERR_INVALID_ARG;
+    if (n > kNoAllocMaxSites) return POLFMM_ERR_INVALID_ARG;
+    if (tree_depth < 1 || tree_depth > kMaxDepth) return POLFMM_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    unsigned char* S = nullptr;
+    int rc = noalloc_scratch(&S);
+    if (rc != POLFMM_OK) return rc;
+    uint32_t* key_tmp = reinterpret_cast<uint32_t*>(S + kNAKeys);
+    int* val_tmp = reinterpret_cast<int*>(S + kNAVals);
+    int* counts = reinterpret_cast<int*>(S + kNACounts);
+    int* scan_scratch = reinterpret_cast<int*>(S + kNAScan);
+    double* bbox = reinterpret_cast<double*>(S + kNABBox);
+    int* err = reinterpret_cast<int*>(S + kNAErr);
+    // the array keeps the previous call's contents: clear the error word
+    if (cudaMemsetAsync(err, 0, sizeof(int) * 4, st) != cudaSuccess) return POLFMM_ERR_CUDA;
+    // root cube: same reduction and the same FP64 rule as fmm_build
+    bbox_partial_kernel<<<kBBoxBlocks, 256, 0, st>>>(positions, n, bbox);
+    bbox_final_kernel<<<1, 32, 0, st>>>(bbox, kBBoxBlocks, bbox + 6 * kBBoxBlocks);
+    double hb[6];
+    if (cudaMemcpyAsync(hb, bbox + 6 * kBBoxBlocks, sizeof(hb), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return POLFMM_ERR_CUDA;
+    double ext = 0.0;
+    for (int d = 0; d < 3; d++) {
+        double e = hb[3 + d] - hb[d];
+        if (!(e == e)) return POLFMM_ERR_INVALID_ARG;
+        if (e > ext) ext = e;
+    }
+    if (!isfinite(ext)) return POLFMM_ERR_INVALID_ARG;
+    double side = ext > 0.0 ? ext * (1.0 + 1e-6) : 1.0;
+    for (int d = 0; d < 3; d++) {
+        volatile double cen = 0.5 * (hb[d] + hb[3 + d]);
+        volatile double half = 0.5 * side;
+        root_lo[d] = cen - half;
+    }
+    *root_side = side;
+    const int nside = 1 << tree_depth;
+    const double h = side / (double)nside;
+    // keys start in the buffer that makes the last pass land in keys / perm
+    const int npass = (3 * tree_depth + 7) / 8;
+    uint32_t* ka = (npass & 1) ? key_tmp : keys;
+    int* va = (npass & 1) ? val_tmp : perm;
+    uint32_t* kb = (npass & 1) ? keys : key_tmp;
+    int* vb = (npass & 1) ? perm : val_tmp;
+    keys_kernel<<<grid_for(n, 256), 256, 0, st>>>(positions, n, root_lo[0], root_lo[1], root_lo[2], h, nside, ka,
+                                                  va, err);
+    cells_from_keys_kernel<<<grid_for(n, 256), 256, 0, st>>>(ka, n, cells);
+    for (int ps = 0; ps < npass; ps++) {
+        noalloc_radix_pass(st, ka, va, kb, vb, (int)n, 8 * ps, counts, scan_scratch);
+        uint32_t* tk = ka; ka = kb; kb = tk;
+        int* tv = va; va = vb; vb = tv;
+    }
+    int herr[4] = {0, 0, 0, 0};
+    if (cudaMemcpyAsync(herr, err, sizeof(herr), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess || cudaGetLastError() != cudaSuccess)
+        return POLFMM_ERR_CUDA;
+    return herr[0] ? POLFMM_ERR_INVALID_ARG : POLFMM_OK;
+}
