@@ -299,6 +299,8 @@ int allocate(polfmm_ctx* c) {
     c->perm = A.get<int>(n);
     c->key_s = A.get<uint32_t>(n);
     c->ploc = A.get<unsigned char>(3 * n * rsz);
+    c->srcA = A.get<unsigned char>(n * source_record_bytes(c->mixed));
+    c->srcB = A.get<unsigned char>(n * source_record_bytes(c->mixed));
     c->in_buf = A.get<double>(8 * n);
     c->out_buf = A.get<double>(10 * n);
     c->phiq = A.get<double>(n);
@@ -377,6 +379,7 @@ int read_err(polfmm_ctx* c) {
     if (cudaGetLastError() != cudaSuccess) return POLFMM_ERR_CUDA;
     if (h[0] & 1) return POLFMM_ERR_INVALID_ARG;
     if (h[0] & 2) return POLFMM_ERR_COINCIDENT;
+    if (h[0] & 4) return POLFMM_ERR_CUDA;  // a bounded device wait timed out
     return POLFMM_OK;
 }
 
@@ -428,8 +431,9 @@ int rebuild(polfmm_ctx* c) {
     if ((rc = tree_tables(c, x_in, q_in, a_in)) != POLFMM_OK) return rc;
     if ((rc = read_err(c)) != POLFMM_OK) return rc;
     if ((rc = m2l_setup(c)) != POLFMM_OK) return rc;
+    if ((rc = m2l_tensor_prepare(c)) != POLFMM_OK) return rc;  // may raise the offset-chunk count
     if ((rc = ensure_lp(c)) != POLFMM_OK) return rc;
-    if ((rc = m2l_tensor_prepare(c)) != POLFMM_OK) return rc;
+    pack_positions(c);
     fmm_pass(c, LEAF_CHARGE_PHI_E, true, nullptr, c->phiq, c->Eq, nullptr);
     return read_err(c);
 }

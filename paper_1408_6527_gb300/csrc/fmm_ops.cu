@@ -244,194 +244,278 @@ __global__ void __launch_bounds__(256) m2l_simt_kernel(const M2LTile* __restrict
 
 // ---------------------------------------------------------------------------
 // leaf evaluation: L2P + near field over the 27 adjacent leaves
+//
+// Sources are packed per site as two 4-vectors: (x, y, z, q) with x relative
+// to the site's own leaf centre, and (mu_x, mu_y, mu_z, 0).  One block per
+// target leaf stages the sources of all 27 neighbour leaves (shifted into the
+// target leaf's frame, exact small-integer multiples of the leaf side) into
+// shared memory with one barrier pair per CAP sources; thread (t, s) owns
+// target t and every slices-th source, and the slices are added in a fixed
+// order at the end.  The self pair has r = 0 exactly and is masked.
 // ---------------------------------------------------------------------------
 constexpr int kLeafThreads = 128;
-constexpr int kLeafChunk = 128;
+
+template <typename R>
+struct alignas(sizeof(R) == 4 ? 16 : 16) Q4 {
+    R x, y, z, w;
+};
+
+template <typename R>
+struct LeafCap;
+template <>
+struct LeafCap<float> {
+    static constexpr int N = 1024;
+};
+template <>
+struct LeafCap<double> {
+    static constexpr int N = 512;
+};
 
 template <int MODE>
 struct LeafOut {
     static constexpr int NC = MODE == LEAF_FULL ? 10 : (MODE == LEAF_CHARGE_PHI_E ? 4 : 3);
 };
 
+__device__ inline float rsqrt_pos(float r2) { return r2 > 0.f ? rsqrtf(r2) : 0.f; }
+__device__ inline double rsqrt_pos(double r2) { return r2 > 0.0 ? rsqrt(r2) : 0.0; }
+
+// dynamic shared memory of leaf_kernel<R, MODE>
+template <typename R, int MODE>
+__host__ __device__ inline size_t leaf_smem_bytes(int ncoef) {
+    constexpr int CAP = LeafCap<R>::N;
+    size_t b = sizeof(Q4<R>) * CAP;                          // positions + charge
+    if (MODE != LEAF_CHARGE_PHI_E) b += sizeof(Q4<R>) * CAP;  // dipoles
+    if (MODE == LEAF_CHARGE_PHI_E) b += sizeof(int) * CAP;    // source index (coincidence check)
+    b += sizeof(R) * 2 * (size_t)ncoef;                      // locals, 1/n!
+    b += sizeof(int) * 4 * (size_t)ncoef;                     // packed n, n + e_d
+    if (MODE == LEAF_FULL) b += sizeof(int) * 6 * (size_t)ncoef;
+    return b;
+}
+
+template <typename R>
+__global__ void pack_positions_kernel(int64_t n, const R* __restrict__ ploc, const double* __restrict__ q,
+                                      Q4<R>* __restrict__ A) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    A[i] = Q4<R>{ploc[3 * i], ploc[3 * i + 1], ploc[3 * i + 2], R(q[i])};
+}
+
+template <typename R>
+__global__ void pack_dipoles_kernel(int64_t n, const double* __restrict__ mu, Q4<R>* __restrict__ B) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    B[i] = Q4<R>{R(mu[3 * i]), R(mu[3 * i + 1]), R(mu[3 * i + 2]), R(0)};
+}
+
 template <typename R, int MODE>
 __global__ void __launch_bounds__(kLeafThreads) leaf_kernel(
     int nleaf, const int* __restrict__ lkey, const int* __restrict__ lstart, const int* __restrict__ lcount,
-    const int* __restrict__ lmap, int depth, const R* __restrict__ ploc, const double* __restrict__ q_s,
-    const double* __restrict__ mu_s, const R* __restrict__ Lf, int ld, int ncoef, const int* __restrict__ mi,
-    const double* __restrict__ inv_fact, const int* __restrict__ up1, const int* __restrict__ up2, R h,
-    double* __restrict__ out_phi, double* __restrict__ out_E, double* __restrict__ out_G, int* __restrict__ err) {
+    const int* __restrict__ lmap, int depth, const Q4<R>* __restrict__ srcA, const Q4<R>* __restrict__ srcB,
+    const R* __restrict__ Lf, int ld, int ncoef, const int* __restrict__ mi, const double* __restrict__ inv_fact,
+    const int* __restrict__ up1, const int* __restrict__ up2, R h, double* __restrict__ out_phi,
+    double* __restrict__ out_E, double* __restrict__ out_G, int* __restrict__ err) {
     constexpr int NC = LeafOut<MODE>::NC;
+    constexpr int CAP = LeafCap<R>::N;
     constexpr bool HAS_PHI = MODE != LEAF_DIPOLE_E;
     constexpr bool HAS_G = MODE == LEAF_FULL;
     constexpr bool SRC_Q = MODE != LEAF_DIPOLE_E;
     constexpr bool SRC_MU = MODE != LEAF_CHARGE_PHI_E;
-    // component layout: [phi] E(3) [G(6)]
-    constexpr int IE = HAS_PHI ? 1 : 0;
+    constexpr bool CHECK = MODE == LEAF_CHARGE_PHI_E;
+    constexpr int IE = HAS_PHI ? 1 : 0;  // component layout: [phi] E(3) [G(6)]
     constexpr int IG = IE + 3;
 
-    extern __shared__ unsigned char smem_raw[];
-    R* f = reinterpret_cast<R*>(smem_raw);  // [ncoef] leaf locals
-    __shared__ R sx[kLeafChunk], sy[kLeafChunk], sz[kLeafChunk];
-    __shared__ R sq[SRC_Q ? kLeafChunk : 1];
-    __shared__ R smx[SRC_MU ? kLeafChunk : 1], smy[SRC_MU ? kLeafChunk : 1], smz[SRC_MU ? kLeafChunk : 1];
-    __shared__ int sidx[kLeafChunk];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Q4<R>* sA = reinterpret_cast<Q4<R>*>(smem_raw);
+    Q4<R>* sB = sA + CAP;
+    unsigned char* tail = reinterpret_cast<unsigned char*>(SRC_MU ? sB + CAP : sA + CAP);
+    int* sidx = reinterpret_cast<int*>(tail);
+    if (CHECK) tail += sizeof(int) * CAP;
+    R* f = reinterpret_cast<R*>(tail);
+    R* ifact = f + ncoef;
+    int* cinfo = reinterpret_cast<int*>(ifact + ncoef);  // [ncoef][4]: packed n, n+e_x, n+e_y, n+e_z
+    int* cup2 = cinfo + 4 * ncoef;                       // [ncoef][6] (FULL only)
+    __shared__ int nb_start[27];
+    __shared__ int nb_pre[28];
+    __shared__ R nb_shift[27][3];
     __shared__ R part[NC][kLeafThreads];
 
     const int b = blockIdx.x;
     if (b >= nleaf) return;
     const int s0 = lstart[b], cnt = lcount[b];
-    const uint32_t key = (uint32_t)lkey[b];
-    const int bx = compact3(key), by = compact3(key >> 1), bz = compact3(key >> 2);
-    const int nside = 1 << depth;
-    for (int cc = threadIdx.x; cc < ncoef; cc += blockDim.x) f[cc] = Lf[(int64_t)b * ld + cc];
+    const int tid = threadIdx.x;
+    if (tid < 32) {
+        int c = 0;
+        if (tid < 27) {
+            const uint32_t key = (uint32_t)lkey[b];
+            const int nside = 1 << depth;
+            const int dx = tid % 3 - 1, dy = (tid / 3) % 3 - 1, dz = tid / 9 - 1;
+            const int ax = (int)compact3(key) + dx, ay = (int)compact3(key >> 1) + dy, az = (int)compact3(key >> 2) + dz;
+            int ns = -1;
+            if (ax >= 0 && ay >= 0 && az >= 0 && ax < nside && ay < nside && az < nside) ns = lmap[morton3(ax, ay, az)];
+            nb_start[tid] = ns >= 0 ? lstart[ns] : 0;
+            c = ns >= 0 ? lcount[ns] : 0;
+            nb_shift[tid][0] = R(dx) * h;
+            nb_shift[tid][1] = R(dy) * h;
+            nb_shift[tid][2] = R(dz) * h;
+        }
+        int incl = c;
+        for (int o = 1; o < 32; o <<= 1) {
+            int v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (tid >= o) incl += v;
+        }
+        if (tid < 27) nb_pre[tid + 1] = incl;
+        if (tid == 0) nb_pre[0] = 0;
+    }
+    for (int cc = tid; cc < ncoef; cc += blockDim.x) {
+        f[cc] = Lf[(int64_t)b * ld + cc];
+        ifact[cc] = R(inv_fact[cc]);
+        cinfo[4 * cc] = mi[cc];
+        cinfo[4 * cc + 1] = up1[3 * cc];
+        cinfo[4 * cc + 2] = up1[3 * cc + 1];
+        cinfo[4 * cc + 3] = up1[3 * cc + 2];
+        if (HAS_G)
+            for (int k = 0; k < 6; k++) cup2[6 * cc + k] = up2[6 * cc + k];
+    }
+    __syncthreads();
+    const int total = nb_pre[27];
     const R inv_h = R(1) / h;
 
     for (int tg = 0; tg < cnt; tg += kLeafThreads) {
         const int nt = min(kLeafThreads, cnt - tg);
         const int slices = kLeafThreads / nt;
-        const int t = threadIdx.x % nt, s = threadIdx.x / nt;
+        const int t = tid % nt, s = tid / nt;
         const bool active = s < slices;
         const int i = s0 + tg + t;
         R acc[NC];
 #pragma unroll
         for (int k = 0; k < NC; k++) acc[k] = R(0);
         R xi = R(0), yi = R(0), zi = R(0);
-        __syncthreads();
         if (active) {
-            xi = ploc[3 * i];
-            yi = ploc[3 * i + 1];
-            zi = ploc[3 * i + 2];
+            const Q4<R> me = srcA[i];
+            xi = me.x;
+            yi = me.y;
+            zi = me.z;
             // far field: L2P of this slice's share of the coefficients
             const R ux = xi * inv_h, uy = yi * inv_h, uz = zi * inv_h;
-            R dphi[3] = {R(0), R(0), R(0)};
-            R ddphi[6] = {R(0), R(0), R(0), R(0), R(0), R(0)};
-            R phi = R(0);
+            R phi = R(0), d0 = R(0), d1 = R(0), d2 = R(0);
+            R dd[6] = {R(0), R(0), R(0), R(0), R(0), R(0)};
             for (int cc = s; cc < ncoef; cc += slices) {
-                int nx, ny, nz;
-                decode_mi(mi[cc], nx, ny, nz);
-                R wgt = R(inv_fact[cc]);
-                for (int k = 0; k < nx; k++) wgt *= ux;
-                for (int k = 0; k < ny; k++) wgt *= uy;
-                for (int k = 0; k < nz; k++) wgt *= uz;
+                const int pk = cinfo[4 * cc];
+                R wgt = ifact[cc];
+                for (int k = pk & 0xff; k > 0; k--) wgt *= ux;
+                for (int k = (pk >> 8) & 0xff; k > 0; k--) wgt *= uy;
+                for (int k = (pk >> 16) & 0xff; k > 0; k--) wgt *= uz;
                 if (HAS_PHI) phi += wgt * f[cc];
-                const int u0 = up1[3 * cc];
+                const int u0 = cinfo[4 * cc + 1];
                 if (u0 >= 0) {
-                    dphi[0] += wgt * f[u0];
-                    dphi[1] += wgt * f[up1[3 * cc + 1]];
-                    dphi[2] += wgt * f[up1[3 * cc + 2]];
+                    d0 += wgt * f[u0];
+                    d1 += wgt * f[cinfo[4 * cc + 2]];
+                    d2 += wgt * f[cinfo[4 * cc + 3]];
                 }
                 if (HAS_G) {
-                    const int v0 = up2[6 * cc];
+                    const int v0 = cup2[6 * cc];
                     if (v0 >= 0) {
-                        ddphi[0] += wgt * f[v0];
+                        dd[0] += wgt * f[v0];
 #pragma unroll
-                        for (int k = 1; k < 6; k++) ddphi[k] += wgt * f[up2[6 * cc + k]];
+                        for (int k = 1; k < 6; k++) dd[k] += wgt * f[cup2[6 * cc + k]];
                     }
                 }
             }
             // Phi = phi / h, E = -dPhi / h^2, G = -ddPhi / h^3
             if (HAS_PHI) acc[0] = phi * inv_h;
             const R s2 = -inv_h * inv_h;
-#pragma unroll
-            for (int d = 0; d < 3; d++) acc[IE + d] = dphi[d] * s2;
+            acc[IE + 0] = d0 * s2;
+            acc[IE + 1] = d1 * s2;
+            acc[IE + 2] = d2 * s2;
             if (HAS_G) {
                 const R s3 = s2 * inv_h;
 #pragma unroll
-                for (int k = 0; k < 6; k++) acc[IG + k] = ddphi[k] * s3;
+                for (int k = 0; k < 6; k++) acc[IG + k] = dd[k] * s3;
             }
         }
         // near field
-        for (int dz = -1; dz <= 1; dz++)
-            for (int dy = -1; dy <= 1; dy++)
-                for (int dx = -1; dx <= 1; dx++) {
-                    const int ax = bx + dx, ay = by + dy, az = bz + dz;
-                    if (ax < 0 || ay < 0 || az < 0 || ax >= nside || ay >= nside || az >= nside) continue;
-                    const int ns = lmap[morton3(ax, ay, az)];
-                    if (ns < 0) continue;
-                    const int js0 = lstart[ns], jc = lcount[ns];
-                    const R shx = R(dx) * h, shy = R(dy) * h, shz = R(dz) * h;
-                    for (int k0 = 0; k0 < jc; k0 += kLeafChunk) {
-                        const int m = min(kLeafChunk, jc - k0);
-                        __syncthreads();
-                        for (int jj = threadIdx.x; jj < m; jj += blockDim.x) {
-                            const int j = js0 + k0 + jj;
-                            sx[jj] = ploc[3 * j] + shx;
-                            sy[jj] = ploc[3 * j + 1] + shy;
-                            sz[jj] = ploc[3 * j + 2] + shz;
-                            if (SRC_Q) sq[jj] = R(q_s[j]);
-                            if (SRC_MU) {
-                                smx[jj] = R(mu_s[3 * j]);
-                                smy[jj] = R(mu_s[3 * j + 1]);
-                                smz[jj] = R(mu_s[3 * j + 2]);
-                            }
-                            sidx[jj] = j;
-                        }
-                        __syncthreads();
-                        if (!active) continue;
-                        for (int jj = s; jj < m; jj += slices) {
-                            const R rx = xi - sx[jj], ry = yi - sy[jj], rz = zi - sz[jj];
-                            const R r2 = rx * rx + ry * ry + rz * rz;
-                            if (sidx[jj] == i) continue;
-                            if (r2 == R(0)) {
-                                atomicOr(err, 2);
-                                continue;
-                            }
-                            const R ri = R(1) / sqrt(r2);
-                            const R ri2 = ri * ri;
-                            const R ri3 = ri * ri2;
-                            if (SRC_Q) {
-                                const R qj = sq[jj];
-                                const R qr3 = qj * ri3;
-                                if (HAS_PHI) acc[0] += qj * ri;
-                                acc[IE + 0] += qr3 * rx;
-                                acc[IE + 1] += qr3 * ry;
-                                acc[IE + 2] += qr3 * rz;
-                                if (HAS_G) {
-                                    const R t5 = R(3) * qr3 * ri2;
-                                    acc[IG + 0] += qr3 - t5 * rx * rx;
-                                    acc[IG + 1] -= t5 * rx * ry;
-                                    acc[IG + 2] -= t5 * rx * rz;
-                                    acc[IG + 3] += qr3 - t5 * ry * ry;
-                                    acc[IG + 4] -= t5 * ry * rz;
-                                    acc[IG + 5] += qr3 - t5 * rz * rz;
-                                }
-                            }
-                            if (SRC_MU) {
-                                const R mx = smx[jj], my = smy[jj], mz = smz[jj];
-                                const R mr = mx * rx + my * ry + mz * rz;
-                                const R ri5 = ri3 * ri2;
-                                const R a3 = R(3) * mr * ri5;
-                                if (HAS_PHI) acc[0] += mr * ri3;
-                                acc[IE + 0] += a3 * rx - mx * ri3;
-                                acc[IE + 1] += a3 * ry - my * ri3;
-                                acc[IE + 2] += a3 * rz - mz * ri3;
-                                if (HAS_G) {
-                                    // G_de = 3 (mu_d r_e + mu_e r_d + mr delta_de) / r^5 - 15 mr r_d r_e / r^7
-                                    const R t5 = R(3) * ri5;
-                                    const R t7 = R(5) * a3 * ri2;
-                                    acc[IG + 0] += t5 * (R(2) * mx * rx + mr) - t7 * rx * rx;
-                                    acc[IG + 1] += t5 * (mx * ry + my * rx) - t7 * rx * ry;
-                                    acc[IG + 2] += t5 * (mx * rz + mz * rx) - t7 * rx * rz;
-                                    acc[IG + 3] += t5 * (R(2) * my * ry + mr) - t7 * ry * ry;
-                                    acc[IG + 4] += t5 * (my * rz + mz * ry) - t7 * ry * rz;
-                                    acc[IG + 5] += t5 * (R(2) * mz * rz + mr) - t7 * rz * rz;
-                                }
-                            }
-                        }
+        for (int base = 0; base < total; base += CAP) {
+            const int m = min(CAP, total - base);
+            __syncthreads();
+            for (int idx = tid; idx < m; idx += blockDim.x) {
+                const int g = base + idx;
+                int lo = 0, hi = 26;  // range r with nb_pre[r] <= g < nb_pre[r + 1]
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (nb_pre[mid] <= g) lo = mid; else hi = mid - 1;
+                }
+                const int j = nb_start[lo] + (g - nb_pre[lo]);
+                Q4<R> a = srcA[j];
+                a.x += nb_shift[lo][0];
+                a.y += nb_shift[lo][1];
+                a.z += nb_shift[lo][2];
+                sA[idx] = a;
+                if (SRC_MU) sB[idx] = srcB[j];
+                if (CHECK) sidx[idx] = j;
+            }
+            __syncthreads();
+            if (!active) continue;
+#pragma unroll 4
+            for (int jj = s; jj < m; jj += slices) {
+                const Q4<R> a = sA[jj];
+                const R rx = xi - a.x, ry = yi - a.y, rz = zi - a.z;
+                const R r2 = rx * rx + ry * ry + rz * rz;
+                if (CHECK && r2 == R(0) && sidx[jj] != i) atomicOr(err, 2);
+                const R ri = rsqrt_pos(r2);  // 0 for the self pair
+                const R ri2 = ri * ri;
+                const R ri3 = ri * ri2;
+                if (SRC_Q) {
+                    const R qj = a.w;
+                    const R qr3 = qj * ri3;
+                    if (HAS_PHI) acc[0] += qj * ri;
+                    acc[IE + 0] += qr3 * rx;
+                    acc[IE + 1] += qr3 * ry;
+                    acc[IE + 2] += qr3 * rz;
+                    if (HAS_G) {
+                        const R t5 = R(3) * qr3 * ri2;
+                        acc[IG + 0] += qr3 - t5 * rx * rx;
+                        acc[IG + 1] -= t5 * rx * ry;
+                        acc[IG + 2] -= t5 * rx * rz;
+                        acc[IG + 3] += qr3 - t5 * ry * ry;
+                        acc[IG + 4] -= t5 * ry * rz;
+                        acc[IG + 5] += qr3 - t5 * rz * rz;
                     }
                 }
+                if (SRC_MU) {
+                    const Q4<R> mv = sB[jj];
+                    const R mr = mv.x * rx + mv.y * ry + mv.z * rz;
+                    const R ri5 = ri3 * ri2;
+                    const R a3 = R(3) * mr * ri5;
+                    if (HAS_PHI) acc[0] += mr * ri3;
+                    acc[IE + 0] += a3 * rx - mv.x * ri3;
+                    acc[IE + 1] += a3 * ry - mv.y * ri3;
+                    acc[IE + 2] += a3 * rz - mv.z * ri3;
+                    if (HAS_G) {
+                        // G_de = 3 (mu_d r_e + mu_e r_d + mr delta_de) / r^5 - 15 mr r_d r_e / r^7
+                        const R t5 = R(3) * ri5;
+                        const R t7 = R(5) * a3 * ri2;
+                        acc[IG + 0] += t5 * (R(2) * mv.x * rx + mr) - t7 * rx * rx;
+                        acc[IG + 1] += t5 * (mv.x * ry + mv.y * rx) - t7 * rx * ry;
+                        acc[IG + 2] += t5 * (mv.x * rz + mv.z * rx) - t7 * rx * rz;
+                        acc[IG + 3] += t5 * (R(2) * mv.y * ry + mr) - t7 * ry * ry;
+                        acc[IG + 4] += t5 * (mv.y * rz + mv.z * ry) - t7 * ry * rz;
+                        acc[IG + 5] += t5 * (R(2) * mv.z * rz + mr) - t7 * rz * rz;
+                    }
+                }
+            }
+        }
         // fixed-order reduction over slices
         __syncthreads();
 #pragma unroll
-        for (int k = 0; k < NC; k++) part[k][threadIdx.x] = active ? acc[k] : R(0);
+        for (int k = 0; k < NC; k++) part[k][tid] = active ? acc[k] : R(0);
         __syncthreads();
-        if (threadIdx.x < nt) {
-            const int ii = s0 + tg + threadIdx.x;
+        if (tid < nt) {
+            const int ii = s0 + tg + tid;
             double o[NC];
 #pragma unroll
             for (int k = 0; k < NC; k++) {
                 R v = R(0);
-                for (int u = 0; u < slices; u++) v += part[k][threadIdx.x + u * nt];
+                for (int u = 0; u < slices; u++) v += part[k][tid + u * nt];
                 o[k] = (double)v;
             }
             if (HAS_PHI && out_phi) out_phi[ii] = o[0];
@@ -493,20 +577,41 @@ template <typename R>
 static void launch_leaf(polfmm_ctx* c, int mode, const double* mu_sorted, double* phi, double* E, double* G) {
     Level& L = c->lv[c->depth];
     const R h = R(c->side / (double)(1 << c->depth));
-    size_t smem = sizeof(R) * c->ncoef;
     const Tables& T = c->tab;
+    Q4<R>* A = reinterpret_cast<Q4<R>*>(c->srcA);
+    Q4<R>* B = reinterpret_cast<Q4<R>*>(c->srcB);
+    if (mode != LEAF_CHARGE_PHI_E) {
+        LaunchScope ls(c, F_P2M);
+        pack_dipoles_kernel<R><<<grid_for(c->n, 256), 256, 0, c->stream>>>(c->n, mu_sorted, B);
+    }
     LaunchScope ls(c, mode == LEAF_DIPOLE_E ? F_LEAF_DIPOLE : (mode == LEAF_CHARGE_PHI_E ? F_LEAF_STATIC : F_LEAF_FULL));
-#define LEAF_ARGS                                                                                              \
-    L.nbox, L.key, c->lstart, c->lcount, L.map, c->depth, (const R*)c->ploc, c->q_s, mu_sorted, (const R*)L.L, \
-        c->ld, c->ncoef, T.mi, T.inv_fact, T.up1, T.up2, h, phi, E, G, c->err
+#define LEAF_ARGS                                                                                                  \
+    L.nbox, L.key, c->lstart, c->lcount, L.map, c->depth, A, B, (const R*)L.L, c->ld, c->ncoef, T.mi, T.inv_fact, \
+        T.up1, T.up2, h, phi, E, G, c->err
     if (mode == LEAF_DIPOLE_E)
-        leaf_kernel<R, LEAF_DIPOLE_E><<<L.nbox, kLeafThreads, smem, c->stream>>>(LEAF_ARGS);
+        leaf_kernel<R, LEAF_DIPOLE_E>
+            <<<L.nbox, kLeafThreads, leaf_smem_bytes<R, LEAF_DIPOLE_E>(c->ncoef), c->stream>>>(LEAF_ARGS);
     else if (mode == LEAF_CHARGE_PHI_E)
-        leaf_kernel<R, LEAF_CHARGE_PHI_E><<<L.nbox, kLeafThreads, smem, c->stream>>>(LEAF_ARGS);
+        leaf_kernel<R, LEAF_CHARGE_PHI_E>
+            <<<L.nbox, kLeafThreads, leaf_smem_bytes<R, LEAF_CHARGE_PHI_E>(c->ncoef), c->stream>>>(LEAF_ARGS);
     else
-        leaf_kernel<R, LEAF_FULL><<<L.nbox, kLeafThreads, smem, c->stream>>>(LEAF_ARGS);
+        leaf_kernel<R, LEAF_FULL><<<L.nbox, kLeafThreads, leaf_smem_bytes<R, LEAF_FULL>(c->ncoef), c->stream>>>(
+            LEAF_ARGS);
 #undef LEAF_ARGS
 }
+
+// positions + charges of the sorted sites, packed once per tree
+void pack_positions(polfmm_ctx* c) {
+    LaunchScope ls(c, F_TREE);
+    if (c->mixed)
+        pack_positions_kernel<float><<<grid_for(c->n, 256), 256, 0, c->stream>>>(
+            c->n, (const float*)c->ploc, c->q_s, (Q4<float>*)c->srcA);
+    else
+        pack_positions_kernel<double><<<grid_for(c->n, 256), 256, 0, c->stream>>>(
+            c->n, (const double*)c->ploc, c->q_s, (Q4<double>*)c->srcA);
+}
+
+size_t source_record_bytes(bool mixed) { return mixed ? sizeof(Q4<float>) : sizeof(Q4<double>); }
 
 void m2l_tensor_launch(polfmm_ctx* c);  // m2l_tc.cu
 bool m2l_tensor_enabled(polfmm_ctx* c);
@@ -581,6 +686,17 @@ int fmm_ops_init_attributes(polfmm_ctx*) {
     if (cudaFuncSetAttribute(m2l_simt_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need_f) !=
         cudaSuccess)
         return POLFMM_ERR_CUDA;
+#define LEAF_ATTR(R, M)                                                                                 \
+    if (cudaFuncSetAttribute(leaf_kernel<R, M>, cudaFuncAttributeMaxDynamicSharedMemorySize,            \
+                             (int)leaf_smem_bytes<R, M>(nc_max)) != cudaSuccess)                        \
+        return POLFMM_ERR_CUDA;
+    LEAF_ATTR(float, LEAF_DIPOLE_E)
+    LEAF_ATTR(float, LEAF_CHARGE_PHI_E)
+    LEAF_ATTR(float, LEAF_FULL)
+    LEAF_ATTR(double, LEAF_DIPOLE_E)
+    LEAF_ATTR(double, LEAF_CHARGE_PHI_E)
+    LEAF_ATTR(double, LEAF_FULL)
+#undef LEAF_ATTR
     return POLFMM_OK;
 }
 

@@ -118,6 +118,8 @@ struct polfmm_ctx {
     int* perm = nullptr;
     uint32_t* key_s = nullptr;
     void* ploc = nullptr;
+    void* srcA = nullptr;         // packed (x, y, z, q) per sorted site, R4
+    void* srcB = nullptr;         // packed (mu_x, mu_y, mu_z, 0) per sorted site, R4
     // leaves
     int* lstart = nullptr;
     int* lcount = nullptr;
@@ -193,6 +195,8 @@ int scan_exclusive(polfmm_ctx* c, const int* in, int* out, int n, int* total_dev
 void fmm_pass(polfmm_ctx* c, int mode, bool use_q, const double* mu_sorted, double* phi, double* E,
               double* G);
 int m2l_setup(polfmm_ctx* c);
+void pack_positions(polfmm_ctx* c);
+size_t source_record_bytes(bool mixed);
 
 // solver.cu
 void gather_sites(polfmm_ctx* c, const double* src_caller, double* dst_sorted, int comps);

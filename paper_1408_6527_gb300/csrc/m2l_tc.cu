@@ -1,12 +1,534 @@
-// Multipole-to-local translation on the tensor cores (placeholder until the
-// tcgen05 kernel lands; MIXED mode uses the SIMT kernel meanwhile).
+// Multipole-to-local translation on the 5th-generation tensor cores (MIXED
+// mode).  Sec. II.B: F_n(z_B) = sum_{|m| <= p-|n|} M_m(z_A) d^{n+m} phi(z_B - z_A).
+// In normalised coefficients and for a fixed integer offset o = B - A the
+// operator is one matrix K_o[n][m] = D_o[n+m] (zero where |n| + |m| > p), so all
+// target boxes of one level and one octant class that share the offset form a
+// dense contraction  C[box][n] += sum_m A[box][m] K_o[n][m].
+//
+// One CTA = one tile of up to 128 same-class target boxes (the M = 128 rows of
+// the MMA) and a range of the class's 189 offsets.  Per offset:
+//   * every thread gathers the multipole row of its box's source B - o
+//     (zero-filled where the source box is empty or outside the tree) with
+//     16-byte cp.async copies into the no-swizzle K-major core-matrix layout;
+//     multipoles are stored pre-split into a TF32 high part and the residual;
+//   * one thread bulk-copies the pre-split, block-sparse image of K_o (only
+//     the (output band, input prefix) blocks allowed by |n| + |m| <= p) with
+//     cp.async.bulk completing on an mbarrier;
+//   * the same thread issues tcgen05.mma kind::tf32 for the three products
+//     A_hi B_hi + A_hi B_lo + A_lo B_hi (FP32-level accuracy from TF32 inputs),
+//     accumulating into a TMEM accumulator of 128 lanes x NP columns, and
+//     commits them to an mbarrier that every thread waits on before the next
+//     gather overwrites shared memory.
+// At the end each warp reads its 32 TMEM lanes (tcgen05.ld) and writes the
+// partial locals of its boxes; partials of different offset ranges are summed
+// in fixed order by the L2L kernel.  Every wait is bounded: on timeout the CTA
+// raises an error bit, stops issuing and still frees its TMEM.
+#include <math.h>
+#include <string.h>
+
+#include <vector>
+
 #include "internal.cuh"
 
 namespace polfmm {
 
-bool m2l_tensor_enabled(polfmm_ctx*) { return false; }
-void m2l_tensor_launch(polfmm_ctx*) {}
-int m2l_tensor_prepare(polfmm_ctx*) { return POLFMM_OK; }
-void m2l_tensor_release(polfmm_ctx*) {}
+constexpr int kTcRows = 128;
+constexpr int kTcThreads = 128;
+constexpr int kTcMaxEntries = 12;
+constexpr uint64_t kTcWaitNs = 2000000000ull;  // 2 s bound on every wait
+
+struct TcSchedule {
+    int nent;
+    int n0[kTcMaxEntries];    // first output column of the block
+    int nn[kTcMaxEntries];    // block width (multiple of 16)
+    int ks[kTcMaxEntries];    // input steps of 8 (prefix of the inputs)
+    int boff[kTcMaxEntries];  // float offset of the block inside one K_o image part
+    int KP;                   // padded input count (multiple of 8)
+    int NP;                   // padded output count (multiple of 16)
+    int bpart;                // floats per image part (hi or lo) per offset
+    int tmem_cols;            // power of two >= NP
+};
+
+struct TcState {
+    TcSchedule sch;
+    float* Bimg = nullptr;                   // [343][2][bpart]
+    float* Mhi[kMaxDepth + 1] = {nullptr};   // [cap][KP]
+    float* Mlo[kMaxDepth + 1] = {nullptr};
+    size_t smem = 0;
+    bool ready = false;
+};
+
+// ---------------------------------------------------------------------------
+// PTX helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t phase) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(phase)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t phase) {
+    if (mbar_try_wait(bar, phase)) return true;
+    const uint64_t t0 = global_ns();
+    while (global_ns() - t0 < kTcWaitNs)
+        if (mbar_try_wait(bar, phase)) return true;
+    return false;
+}
+
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, uint32_t src_bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(src_bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)), "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int k = 0; k < 16; k++) v[k] = __uint_as_float(r[k]);
+}
+
+// shared-memory matrix descriptor, K-major, no swizzle: core matrices of
+// 8 rows x 16 bytes; lbo = byte step between core matrices along K, sbo =
+// byte step between 8-row groups along M / N.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = 0;
+    d |= (uint64_t)((addr >> 4) & 0x3FFF);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+    d |= (uint64_t)1 << 46;  // descriptor version of this architecture
+    return d;                // base offset 0, layout type 0 (no swizzle)
+}
+
+// instruction descriptor: kind::tf32, FP32 accumulator, both operands K-major
+__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
+    return (1u << 4)                         // D format F32
+           | (2u << 7)                       // A format TF32
+           | (2u << 10)                      // B format TF32
+           | ((uint32_t)(N >> 3) << 17)      // N / 8
+           | ((uint32_t)(M >> 4) << 24);     // M / 16
+}
+
+// ---------------------------------------------------------------------------
+// multipoles -> TF32 high part + residual, padded to KP inputs
+// ---------------------------------------------------------------------------
+__global__ void tc_split_kernel(int nbox, const float* __restrict__ M, int ld, int ncoef, int KP,
+                                float* __restrict__ hi, float* __restrict__ lo) {
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= (int64_t)nbox * KP) return;
+    int64_t b = t / KP;
+    int k = (int)(t - b * KP);
+    float v = k < ncoef ? M[b * ld + k] : 0.f;
+    uint32_t h;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(v));
+    float hv = __uint_as_float(h);
+    hi[t] = hv;
+    lo[t] = v - hv;
+}
+
+// ---------------------------------------------------------------------------
+// the tensor-core M2L kernel
+// ---------------------------------------------------------------------------
+struct TcLevelPtrs {
+    const int* key[kMaxDepth + 1];
+    const int* map[kMaxDepth + 1];
+    const int* by_class[kMaxDepth + 1];
+    const float* Mhi[kMaxDepth + 1];
+    const float* Mlo[kMaxDepth + 1];
+    float* Lp[kMaxDepth + 1];
+    int cap[kMaxDepth + 1];
+};
+
+__global__ void __launch_bounds__(kTcThreads, 1) m2l_tc_kernel(const M2LTile* __restrict__ tiles, TcLevelPtrs lp,
+                                                               const float* __restrict__ Bimg,
+                                                               const int* __restrict__ class_off, TcSchedule sch,
+                                                               int ncoef, int ld, int nchunk,
+                                                               int* __restrict__ err) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    const int KP = sch.KP;
+    // layout: A_hi [KP/4][16][8][4] floats, A_lo (same), B image hi, B image lo
+    float* Ahi = reinterpret_cast<float*>(smem_raw);
+    float* Alo = Ahi + kTcRows * KP;
+    float* Bhi = Alo + kTcRows * KP;
+    float* Blo = Bhi + sch.bpart;
+    __shared__ __align__(8) uint64_t bar_b;
+    __shared__ __align__(8) uint64_t bar_mma;
+    __shared__ uint32_t tmem_base_sh;
+    __shared__ int fail_sh;
+
+    const M2LTile tile = tiles[blockIdx.x];
+    const int chunk = blockIdx.y;
+    const int l = tile.level;
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5;
+    const int nside = 1 << l;
+
+    if (warp == 0) tmem_alloc(&tmem_base_sh, (uint32_t)sch.tmem_cols);
+    if (tid == 0) {
+        mbar_init(&bar_b, 1);
+        mbar_init(&bar_mma, 1);
+        fail_sh = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base_sh;
+
+    // this thread's target box (row `tid` of the tile)
+    int slot = -1, bx = 0, by = 0, bz = 0;
+    if (tid < tile.count) {
+        slot = lp.by_class[l][tile.first + tid];
+        const uint32_t k = (uint32_t)lp.key[l][slot];
+        bx = (int)compact3(k);
+        by = (int)compact3(k >> 1);
+        bz = (int)compact3(k >> 2);
+    }
+    const float* Mhi = lp.Mhi[l];
+    const float* Mlo = lp.Mlo[l];
+    const int* map = lp.map[l];
+
+    const int per = (kNumOffsets + nchunk - 1) / nchunk;
+    const int t0 = chunk * per, t1 = min(kNumOffsets, t0 + per);
+    const uint32_t a_lbo = kTcRows / 8 * 128;  // bytes between K chunks of A
+    const uint32_t bbytes = (uint32_t)sch.bpart * 4u;
+    uint32_t phase_b = 0, phase_m = 0;
+    bool started = false;
+
+    for (int t = t0; t < t1; t++) {
+        const int o = class_off[tile.cls * kNumOffsets + t];
+        const int ox = (o & 15) - 3, oy = ((o >> 4) & 15) - 3, oz = ((o >> 8) & 15) - 3;
+        int src = -1;
+        {
+            const int ax = bx - ox, ay = by - oy, az = bz - oz;
+            if (slot >= 0 && ax >= 0 && ay >= 0 && az >= 0 && ax < nside && ay < nside && az < nside)
+                src = map[morton3(ax, ay, az)];
+        }
+        if (!__syncthreads_or(src >= 0)) continue;  // no source box in this tile for this offset
+        if (fail_sh) break;
+        if (tid == 0) {
+            const int oidx = (ox + 3) + kOffsetGrid * ((oy + 3) + kOffsetGrid * (oz + 3));
+            const float* img = Bimg + (size_t)oidx * 2 * sch.bpart;
+            mbar_arrive_expect_tx(&bar_b, 2 * bbytes);
+            bulk_g2s(Bhi, img, bbytes, &bar_b);
+            bulk_g2s(Blo, img + sch.bpart, bbytes, &bar_b);
+        }
+        // gather this row: chunk c (inputs 4c .. 4c+3) to core matrix (c, row / 8), line row % 8
+        {
+            const uint32_t nbytes = src >= 0 ? 16u : 0u;
+            const int s = src >= 0 ? src : 0;
+            const float* gh = Mhi + (size_t)s * KP;
+            const float* gl = Mlo + (size_t)s * KP;
+            const int row_off = (tid >> 3) * 32 + (tid & 7) * 4;  // floats
+            for (int c = 0; c < KP / 4; c++) {
+                const int off = c * (kTcRows / 8) * 32 + row_off;
+                cp_async16(Ahi + off, gh + 4 * c, nbytes);
+                cp_async16(Alo + off, gl + 4 * c, nbytes);
+            }
+        }
+        cp_async_wait_all();
+        fence_proxy_async();
+        __syncthreads();
+        if (tid == 0) {
+            bool ok = mbar_wait_bounded(&bar_b, phase_b);
+            if (!ok) {
+                atomicOr(err, 4);
+                fail_sh = 1;
+            } else {
+                tc_fence_after();
+                const uint32_t a_hi = smem_u32(Ahi), a_lo = smem_u32(Alo);
+                const uint32_t b_hi = smem_u32(Bhi), b_lo = smem_u32(Blo);
+                for (int e = 0; e < sch.nent; e++) {
+                    const uint32_t idesc = idesc_tf32(kTcRows, sch.nn[e]);
+                    const uint32_t b_lbo = (uint32_t)(sch.nn[e] / 8) * 128u;
+                    const uint32_t d = tmem + (uint32_t)sch.n0[e];
+                    for (int prod = 0; prod < 3; prod++) {
+                        const uint32_t a_base = prod == 2 ? a_lo : a_hi;
+                        const uint32_t b_base = (prod == 1 ? b_lo : b_hi) + (uint32_t)sch.boff[e] * 4u;
+                        for (int k = 0; k < sch.ks[e]; k++) {
+                            const uint64_t ad = smem_desc(a_base + 2u * (uint32_t)k * a_lbo, a_lbo, 128u);
+                            const uint64_t bd = smem_desc(b_base + 2u * (uint32_t)k * b_lbo, b_lbo, 128u);
+                            mma_tf32(d, ad, bd, idesc, (started || prod > 0 || k > 0) ? 1u : 0u);
+                        }
+                    }
+                }
+                mma_commit(&bar_mma);
+            }
+        }
+        phase_b ^= 1;
+        __syncthreads();
+        if (fail_sh) break;
+        if (!mbar_wait_bounded(&bar_mma, phase_m)) {
+            atomicOr(err, 4);
+            fail_sh = 1;
+        }
+        phase_m ^= 1;
+        started = true;
+        tc_fence_after();
+        __syncthreads();
+        if (fail_sh) break;
+    }
+
+    // epilogue: TMEM lanes 32 w .. 32 w + 31 hold the rows of warp w; the loads
+    // are warp-collective, so every lane takes part and only rows with a box
+    // store (fail_sh and started are uniform over the CTA here)
+    tc_fence_after();
+    if (!fail_sh) {
+        float* out = slot >= 0 ? lp.Lp[l] + ((size_t)chunk * lp.cap[l] + slot) * ld : nullptr;
+        for (int c0 = 0; c0 < sch.NP; c0 += 16) {
+            float v[16];
+            if (started) {
+                tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+            } else {
+#pragma unroll
+                for (int k = 0; k < 16; k++) v[k] = 0.f;
+            }
+            if (out)
+                for (int k = 0; k < 16; k++)
+                    if (c0 + k < ncoef) out[c0 + k] = v[k];
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, (uint32_t)sch.tmem_cols);
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+static TcState* state(polfmm_ctx* c) { return reinterpret_cast<TcState*>(c->tc); }
+
+bool m2l_tensor_enabled(polfmm_ctx* c) {
+    TcState* S = state(c);
+    return c->mixed && c->opt.m2l_impl != POLFMM_M2L_SIMT && S && S->ready;
+}
+
+static int degree_of(int idx, int p) {
+    for (int s = 0; s <= p; s++)
+        if (idx < ncoef_of(s)) return s;
+    return p + 1;
+}
+
+// rounding to TF32 (10 explicit mantissa bits), nearest with ties away
+static float tf32_round(float x) {
+    uint32_t u;
+    memcpy(&u, &x, 4);
+    u = (u + 0x1000u) & 0xFFFFE000u;
+    float r;
+    memcpy(&r, &u, 4);
+    return r;
+}
+
+int m2l_tensor_prepare(polfmm_ctx* c) {
+    if (!c->mixed || c->opt.m2l_impl == POLFMM_M2L_SIMT || c->p > 8 || c->depth < 2) return POLFMM_OK;
+    TcState* S = state(c);
+    if (!S) {
+        S = new TcState();
+        c->tc = S;
+        const int p = c->p, nc = c->ncoef;
+        TcSchedule& sch = S->sch;
+        memset(&sch, 0, sizeof(sch));
+        sch.KP = (nc + 7) / 8 * 8;
+        sch.NP = (nc + 15) / 16 * 16;
+        // output bands of 16 columns; each needs the input prefix ncoef(p - min degree)
+        int nbands = sch.NP / 16;
+        std::vector<int> need(nbands, 0);
+        for (int bnd = 0; bnd < nbands; bnd++)
+            for (int n = bnd * 16; n < bnd * 16 + 16 && n < nc; n++)
+                need[bnd] = std::max(need[bnd], ncoef_of(p - degree_of(n, p)));
+        int off = 0;
+        for (int bnd = 0; bnd < nbands;) {
+            int ks = (need[bnd] + 7) / 8;
+            int e = bnd;
+            while (e + 1 < nbands && (need[e + 1] + 7) / 8 == ks && (e + 2 - bnd) * 16 <= 256) e++;
+            if (sch.nent >= kTcMaxEntries) return POLFMM_ERR_INVALID_ARG;
+            int k = sch.nent++;
+            sch.n0[k] = bnd * 16;
+            sch.nn[k] = (e - bnd + 1) * 16;
+            sch.ks[k] = ks;
+            sch.boff[k] = off;
+            off += sch.nn[k] * ks * 8;
+            bnd = e + 1;
+        }
+        sch.bpart = off;
+        sch.tmem_cols = 32;
+        while (sch.tmem_cols < sch.NP) sch.tmem_cols *= 2;
+        S->smem = sizeof(float) * (2 * (size_t)kTcRows * sch.KP + 2 * (size_t)sch.bpart) + 1024;
+        if (S->smem > 227 * 1024) {
+            delete S;
+            c->tc = nullptr;
+            return POLFMM_OK;  // does not fit: the SIMT kernel stays in use
+        }
+        // K_o images: block e holds rows n0..n0+nn, inputs 0..8 ks, core-matrix layout
+        // element (n, k) at (k/4)*(nn/8)*32 + (n/8)*32 + (n%8)*4 + k%4
+        std::vector<double> Dd((size_t)343 * nc);
+        if (cudaMemcpy(Dd.data(), c->tab.D, sizeof(double) * Dd.size(), cudaMemcpyDeviceToHost) != cudaSuccess)
+            return POLFMM_ERR_CUDA;
+        std::vector<int> lut((p + 1) * (p + 1) * (p + 1), -1);
+        std::vector<int> mx(nc), my(nc), mz(nc);
+        for (int k = 0; k < nc; k++) {
+            int v = c->tab.h_mi[k];
+            mx[k] = v & 0xff;
+            my[k] = (v >> 8) & 0xff;
+            mz[k] = (v >> 16) & 0xff;
+            lut[(mx[k] * (p + 1) + my[k]) * (p + 1) + mz[k]] = k;
+        }
+        std::vector<float> img((size_t)343 * 2 * sch.bpart, 0.f);
+        for (int oi = 0; oi < 343; oi++) {
+            float* hi = &img[(size_t)oi * 2 * sch.bpart];
+            float* lo = hi + sch.bpart;
+            for (int e = 0; e < sch.nent; e++) {
+                for (int nl = 0; nl < sch.nn[e]; nl++) {
+                    int n = sch.n0[e] + nl;
+                    for (int k = 0; k < sch.ks[e] * 8; k++) {
+                        float v = 0.f;
+                        if (n < nc && k < nc && degree_of(n, p) + degree_of(k, p) <= p) {
+                            int s = lut[((mx[n] + mx[k]) * (p + 1) + my[n] + my[k]) * (p + 1) + mz[n] + mz[k]];
+                            v = (float)Dd[(size_t)oi * nc + s];
+                        }
+                        size_t pos = sch.boff[e] + (size_t)(k / 4) * (sch.nn[e] / 8) * 32 + (nl / 8) * 32 +
+                                     (nl % 8) * 4 + k % 4;
+                        float h = tf32_round(v);
+                        hi[pos] = h;
+                        lo[pos] = v - h;
+                    }
+                }
+            }
+        }
+        if (cudaMalloc(&S->Bimg, sizeof(float) * img.size()) != cudaSuccess) {
+            cudaGetLastError();
+            return POLFMM_ERR_OUT_OF_MEMORY;
+        }
+        if (cudaMemcpy(S->Bimg, img.data(), sizeof(float) * img.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+            return POLFMM_ERR_CUDA;
+        for (int l = 2; l <= c->depth; l++) {
+            size_t cnt = (size_t)c->lv[l].cap * sch.KP;
+            if (cudaMalloc(&S->Mhi[l], sizeof(float) * cnt) != cudaSuccess ||
+                cudaMalloc(&S->Mlo[l], sizeof(float) * cnt) != cudaSuccess) {
+                cudaGetLastError();
+                return POLFMM_ERR_OUT_OF_MEMORY;
+            }
+        }
+        if (cudaFuncSetAttribute(m2l_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S->smem) !=
+            cudaSuccess) {
+            cudaGetLastError();
+            return POLFMM_ERR_CUDA;
+        }
+        S->ready = true;
+    }
+    // the tensor-core kernel has one CTA per SM: split the offsets further
+    if (c->ntiles > 0) {
+        int want = (2 * c->num_sms + c->ntiles - 1) / c->ntiles;
+        c->m2l_chunks = std::max(1, std::min(want, 27));
+    }
+    return POLFMM_OK;
+}
+
+void m2l_tensor_launch(polfmm_ctx* c) {
+    TcState* S = state(c);
+    const TcSchedule& sch = S->sch;
+    TcLevelPtrs lp{};
+    for (int l = 2; l <= c->depth; l++) {
+        Level& B = c->lv[l];
+        {
+            LaunchScope ls(c, F_M2L);
+            int64_t tot = (int64_t)B.nbox * sch.KP;
+            tc_split_kernel<<<grid_for(tot, 256), 256, 0, c->stream>>>(B.nbox, (const float*)B.M, c->ld, c->ncoef,
+                                                                       sch.KP, S->Mhi[l], S->Mlo[l]);
+        }
+        lp.key[l] = B.key;
+        lp.map[l] = B.map;
+        lp.by_class[l] = B.by_class;
+        lp.Mhi[l] = S->Mhi[l];
+        lp.Mlo[l] = S->Mlo[l];
+        lp.Lp[l] = (float*)B.Lp;
+        lp.cap[l] = B.cap;
+    }
+    LaunchScope ls(c, F_M2L);
+    dim3 grid(c->ntiles, c->m2l_chunks);
+    m2l_tc_kernel<<<grid, kTcThreads, S->smem, c->stream>>>(c->tiles, lp, S->Bimg, c->tab.class_off, sch, c->ncoef,
+                                                            c->ld, c->m2l_chunks, c->err);
+}
+
+void m2l_tensor_release(polfmm_ctx* c) {
+    TcState* S = state(c);
+    if (!S) return;
+    if (S->Bimg) cudaFree(S->Bimg);
+    for (int l = 0; l <= kMaxDepth; l++) {
+        if (S->Mhi[l]) cudaFree(S->Mhi[l]);
+        if (S->Mlo[l]) cudaFree(S->Mlo[l]);
+    }
+    delete S;
+    c->tc = nullptr;
+}
 
 }  // namespace polfmm
