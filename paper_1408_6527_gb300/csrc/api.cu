@@ -341,6 +341,7 @@ int allocate(polfmm_ctx* c) {
     }
     c->lstart = A.get<int>(c->lv[c->depth].cap);
     c->lcount = A.get<int>(c->lv[c->depth].cap);
+    c->leaf_order = A.get<int>(c->lv[c->depth].cap);
     if (!A.ok) return POLFMM_ERR_OUT_OF_MEMORY;
     if (cudaMallocHost(&c->h_scal, sizeof(double) * (S_COUNT + 8)) != cudaSuccess) return POLFMM_ERR_OUT_OF_MEMORY;
     if (cudaMallocHost(&c->h_counts, sizeof(int) * (kMaxDepth + 1) * 9) != cudaSuccess) return POLFMM_ERR_OUT_OF_MEMORY;

@@ -264,11 +264,11 @@ template <typename R>
 struct LeafCap;
 template <>
 struct LeafCap<float> {
-    static constexpr int N = 1024;
+    static constexpr int N = 256;
 };
 template <>
 struct LeafCap<double> {
-    static constexpr int N = 512;
+    static constexpr int N = 128;
 };
 
 template <int MODE>
@@ -310,7 +310,8 @@ __global__ void pack_dipoles_kernel(int64_t n, const double* __restrict__ mu, Q4
 template <typename R, int MODE>
 __global__ void __launch_bounds__(kLeafThreads) leaf_kernel(
     int nleaf, const int* __restrict__ lkey, const int* __restrict__ lstart, const int* __restrict__ lcount,
-    const int* __restrict__ lmap, int depth, const Q4<R>* __restrict__ srcA, const Q4<R>* __restrict__ srcB,
+    const int* __restrict__ lmap, const int* __restrict__ order, int depth, const Q4<R>* __restrict__ srcA,
+    const Q4<R>* __restrict__ srcB,
     const R* __restrict__ Lf, int ld, int ncoef, const int* __restrict__ mi, const double* __restrict__ inv_fact,
     const int* __restrict__ up1, const int* __restrict__ up2, R h, double* __restrict__ out_phi,
     double* __restrict__ out_E, double* __restrict__ out_G, int* __restrict__ err) {
@@ -339,8 +340,8 @@ __global__ void __launch_bounds__(kLeafThreads) leaf_kernel(
     __shared__ R nb_shift[27][3];
     __shared__ R part[NC][kLeafThreads];
 
-    const int b = blockIdx.x;
-    if (b >= nleaf) return;
+    if ((int)blockIdx.x >= nleaf) return;
+    const int b = order[blockIdx.x];
     const int s0 = lstart[b], cnt = lcount[b];
     const int tid = threadIdx.x;
     if (tid < 32) {
@@ -586,7 +587,8 @@ static void launch_leaf(polfmm_ctx* c, int mode, const double* mu_sorted, double
     }
     LaunchScope ls(c, mode == LEAF_DIPOLE_E ? F_LEAF_DIPOLE : (mode == LEAF_CHARGE_PHI_E ? F_LEAF_STATIC : F_LEAF_FULL));
 #define LEAF_ARGS                                                                                                  \
-    L.nbox, L.key, c->lstart, c->lcount, L.map, c->depth, A, B, (const R*)L.L, c->ld, c->ncoef, T.mi, T.inv_fact, \
+    L.nbox, L.key, c->lstart, c->lcount, L.map, c->leaf_order, c->depth, A, B, (const R*)L.L, c->ld, c->ncoef,     \
+        T.mi, T.inv_fact,                                                                                      \
         T.up1, T.up2, h, phi, E, G, c->err
     if (mode == LEAF_DIPOLE_E)
         leaf_kernel<R, LEAF_DIPOLE_E>

@@ -123,6 +123,7 @@ struct polfmm_ctx {
     // leaves
     int* lstart = nullptr;
     int* lcount = nullptr;
+    int* leaf_order = nullptr;    // leaves by descending near-field work
     polfmm::Level lv[polfmm::kMaxDepth + 1];
     polfmm::Tables tab;
     // M2L work list

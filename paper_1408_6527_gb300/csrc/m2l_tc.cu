@@ -49,11 +49,22 @@ struct TcSchedule {
     int tmem_cols;            // power of two >= NP
 };
 
+struct TcTile {
+    int cls;
+    int first;  // into the class-ordered row list
+    int count;  // <= kTcRows
+};
+
 struct TcState {
     TcSchedule sch;
     float* Bimg = nullptr;                   // [343][2][bpart]
     float* Mhi[kMaxDepth + 1] = {nullptr};   // [cap][KP]
     float* Mlo[kMaxDepth + 1] = {nullptr};
+    int2* rows = nullptr;                    // (level, slot) of every box of levels >= 2, by class
+    TcTile* tiles = nullptr;
+    int ntiles = 0, tiles_cap = 0;
+    size_t stage_bytes = 0;
+    int stages = 1;
     size_t smem = 0;
     bool ready = false;
 };
@@ -179,20 +190,45 @@ __host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
 }
 
 // ---------------------------------------------------------------------------
-// multipoles -> TF32 high part + residual, padded to KP inputs
+// multipoles -> TF32 high part + residual, padded to KP inputs (all levels >= 2)
 // ---------------------------------------------------------------------------
-__global__ void tc_split_kernel(int nbox, const float* __restrict__ M, int ld, int ncoef, int KP,
-                                float* __restrict__ hi, float* __restrict__ lo) {
+struct TcSplitArgs {
+    const float* M[kMaxDepth + 1];
+    float* hi[kMaxDepth + 1];
+    float* lo[kMaxDepth + 1];
+    int64_t start[kMaxDepth + 2];  // prefix of nbox * KP over levels
+    int lmin, lmax;
+};
+
+__global__ void tc_split_kernel(TcSplitArgs a, int ld, int ncoef, int KP) {
     int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (t >= (int64_t)nbox * KP) return;
-    int64_t b = t / KP;
-    int k = (int)(t - b * KP);
-    float v = k < ncoef ? M[b * ld + k] : 0.f;
+    if (t >= a.start[a.lmax + 1]) return;
+    int l = a.lmin;
+    while (t >= a.start[l + 1]) l++;
+    const int64_t u = t - a.start[l];
+    const int64_t b = u / KP;
+    const int k = (int)(u - b * KP);
+    const float v = k < ncoef ? a.M[l][b * ld + k] : 0.f;
     uint32_t h;
     asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(v));
-    float hv = __uint_as_float(h);
-    hi[t] = hv;
-    lo[t] = v - hv;
+    const float hv = __uint_as_float(h);
+    a.hi[l][u] = hv;
+    a.lo[l][u] = v - hv;
+}
+
+// (level, slot) rows of every box of one level, placed by octant class
+struct TcRowArgs {
+    int off[8];    // first row of (class, this level) in the class-ordered list
+    int start[8];  // first index of the class in the level's by_class list
+};
+
+__global__ void tc_rows_kernel(int nbox, int level, const int* __restrict__ by_class, const int* __restrict__ key,
+                               TcRowArgs ra, int2* __restrict__ rows) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nbox) return;
+    const int slot = by_class[i];
+    const int c = key[slot] & 7;
+    rows[ra.off[c] + (i - ra.start[c])] = make_int2(level, slot);
 }
 
 // ---------------------------------------------------------------------------
@@ -201,41 +237,41 @@ __global__ void tc_split_kernel(int nbox, const float* __restrict__ M, int ld, i
 struct TcLevelPtrs {
     const int* key[kMaxDepth + 1];
     const int* map[kMaxDepth + 1];
-    const int* by_class[kMaxDepth + 1];
     const float* Mhi[kMaxDepth + 1];
     const float* Mlo[kMaxDepth + 1];
     float* Lp[kMaxDepth + 1];
     int cap[kMaxDepth + 1];
 };
 
-__global__ void __launch_bounds__(kTcThreads, 1) m2l_tc_kernel(const M2LTile* __restrict__ tiles, TcLevelPtrs lp,
+// NST = 1: gather, wait, multiply, wait.  NST = 2: the gather of offset t + 1
+// runs while the MMAs of offset t are in flight (double-buffered stages).
+template <int NST>
+__global__ void __launch_bounds__(kTcThreads, 1) m2l_tc_kernel(const TcTile* __restrict__ tiles,
+                                                               const int2* __restrict__ rows, TcLevelPtrs lp,
                                                                const float* __restrict__ Bimg,
                                                                const int* __restrict__ class_off, TcSchedule sch,
-                                                               int ncoef, int ld, int nchunk,
+                                                               int ncoef, int ld, int nchunk, int stage_floats,
                                                                int* __restrict__ err) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     const int KP = sch.KP;
-    // layout: A_hi [KP/4][16][8][4] floats, A_lo (same), B image hi, B image lo
-    float* Ahi = reinterpret_cast<float*>(smem_raw);
-    float* Alo = Ahi + kTcRows * KP;
-    float* Bhi = Alo + kTcRows * KP;
-    float* Blo = Bhi + sch.bpart;
-    __shared__ __align__(8) uint64_t bar_b;
-    __shared__ __align__(8) uint64_t bar_mma;
+    // stage s: A_hi [KP/4][16][8][4] floats, A_lo (same), B image hi, B image lo
+    float* stage0 = reinterpret_cast<float*>(smem_raw);
+    __shared__ __align__(8) uint64_t bar_b[NST];
+    __shared__ __align__(8) uint64_t bar_m[NST];
     __shared__ uint32_t tmem_base_sh;
     __shared__ int fail_sh;
 
-    const M2LTile tile = tiles[blockIdx.x];
+    const TcTile tile = tiles[blockIdx.x];
     const int chunk = blockIdx.y;
-    const int l = tile.level;
     const int tid = threadIdx.x;
     const int warp = tid >> 5;
-    const int nside = 1 << l;
 
     if (warp == 0) tmem_alloc(&tmem_base_sh, (uint32_t)sch.tmem_cols);
     if (tid == 0) {
-        mbar_init(&bar_b, 1);
-        mbar_init(&bar_mma, 1);
+        for (int s = 0; s < NST; s++) {
+            mbar_init(&bar_b[s], 1);
+            mbar_init(&bar_m[s], 1);
+        }
         fail_sh = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -244,69 +280,95 @@ __global__ void __launch_bounds__(kTcThreads, 1) m2l_tc_kernel(const M2LTile* __
     tc_fence_after();
     const uint32_t tmem = tmem_base_sh;
 
-    // this thread's target box (row `tid` of the tile)
-    int slot = -1, bx = 0, by = 0, bz = 0;
+    // this thread's target box: row `tid` of the tile, any level >= 2
+    int level = 0, slot = -1, bx = 0, by = 0, bz = 0;
     if (tid < tile.count) {
-        slot = lp.by_class[l][tile.first + tid];
-        const uint32_t k = (uint32_t)lp.key[l][slot];
+        const int2 r = rows[tile.first + tid];
+        level = r.x;
+        slot = r.y;
+        const uint32_t k = (uint32_t)lp.key[level][slot];
         bx = (int)compact3(k);
         by = (int)compact3(k >> 1);
         bz = (int)compact3(k >> 2);
     }
-    const float* Mhi = lp.Mhi[l];
-    const float* Mlo = lp.Mlo[l];
-    const int* map = lp.map[l];
+    const int nside = 1 << level;
+    const float* Mhi = slot >= 0 ? lp.Mhi[level] : nullptr;
+    const float* Mlo = slot >= 0 ? lp.Mlo[level] : nullptr;
+    const int* map = slot >= 0 ? lp.map[level] : nullptr;
 
     const int per = (kNumOffsets + nchunk - 1) / nchunk;
-    const int t0 = chunk * per, t1 = min(kNumOffsets, t0 + per);
+    const int t0 = min(kNumOffsets, chunk * per), t1 = min(kNumOffsets, t0 + per);
+    const int nt = t1 - t0;
     const uint32_t a_lbo = kTcRows / 8 * 128;  // bytes between K chunks of A
     const uint32_t bbytes = (uint32_t)sch.bpart * 4u;
-    uint32_t phase_b = 0, phase_m = 0;
-    bool started = false;
+    const int row_off = (tid >> 3) * 32 + (tid & 7) * 4;  // floats: core matrix row of this thread
+    uint32_t pb[NST], pm[NST];
+#pragma unroll
+    for (int s = 0; s < NST; s++) pb[s] = pm[s] = 0;
 
-    for (int t = t0; t < t1; t++) {
+    auto stage_ptr = [&](int s) { return stage0 + (size_t)s * stage_floats; };
+    // gather of offset t into stage s: A rows by this thread, the K_o image by thread 0
+    auto issue = [&](int t, int s) {
+        float* Ahi = stage_ptr(s);
+        float* Alo = Ahi + kTcRows * KP;
+        float* Bhi = Alo + kTcRows * KP;
+        float* Blo = Bhi + sch.bpart;
         const int o = class_off[tile.cls * kNumOffsets + t];
         const int ox = (o & 15) - 3, oy = ((o >> 4) & 15) - 3, oz = ((o >> 8) & 15) - 3;
         int src = -1;
-        {
+        if (slot >= 0) {
             const int ax = bx - ox, ay = by - oy, az = bz - oz;
-            if (slot >= 0 && ax >= 0 && ay >= 0 && az >= 0 && ax < nside && ay < nside && az < nside)
+            if (ax >= 0 && ay >= 0 && az >= 0 && ax < nside && ay < nside && az < nside)
                 src = map[morton3(ax, ay, az)];
         }
-        if (!__syncthreads_or(src >= 0)) continue;  // no source box in this tile for this offset
-        if (fail_sh) break;
         if (tid == 0) {
             const int oidx = (ox + 3) + kOffsetGrid * ((oy + 3) + kOffsetGrid * (oz + 3));
             const float* img = Bimg + (size_t)oidx * 2 * sch.bpart;
-            mbar_arrive_expect_tx(&bar_b, 2 * bbytes);
-            bulk_g2s(Bhi, img, bbytes, &bar_b);
-            bulk_g2s(Blo, img + sch.bpart, bbytes, &bar_b);
+            mbar_arrive_expect_tx(&bar_b[s], 2 * bbytes);
+            bulk_g2s(Bhi, img, bbytes, &bar_b[s]);
+            bulk_g2s(Blo, img + sch.bpart, bbytes, &bar_b[s]);
         }
-        // gather this row: chunk c (inputs 4c .. 4c+3) to core matrix (c, row / 8), line row % 8
-        {
-            const uint32_t nbytes = src >= 0 ? 16u : 0u;
-            const int s = src >= 0 ? src : 0;
-            const float* gh = Mhi + (size_t)s * KP;
-            const float* gl = Mlo + (size_t)s * KP;
-            const int row_off = (tid >> 3) * 32 + (tid & 7) * 4;  // floats
-            for (int c = 0; c < KP / 4; c++) {
-                const int off = c * (kTcRows / 8) * 32 + row_off;
-                cp_async16(Ahi + off, gh + 4 * c, nbytes);
-                cp_async16(Alo + off, gl + 4 * c, nbytes);
+        const uint32_t nbytes = src >= 0 ? 16u : 0u;
+        const size_t so = src >= 0 ? (size_t)src * KP : 0;
+        const float* gh = src >= 0 ? Mhi + so : Bimg;  // any valid address when nothing is read
+        const float* gl = src >= 0 ? Mlo + so : Bimg;
+        for (int c = 0; c < KP / 4; c++) {
+            const int off = c * (kTcRows / 8) * 32 + row_off;
+            cp_async16(Ahi + off, gh + (src >= 0 ? 4 * c : 0), nbytes);
+            cp_async16(Alo + off, gl + (src >= 0 ? 4 * c : 0), nbytes);
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+
+    if (nt > 0) issue(t0, 0);
+    for (int i = 0; i < nt; i++) {
+        const int s = NST == 2 ? (i & 1) : 0;
+        const bool prefetch = NST == 2 && i + 1 < nt;
+        if (prefetch) {
+            const int s1 = (i + 1) & 1;
+            if (i >= 1) {  // the MMAs of offset i - 1 read stage s1: wait for them
+                if (!mbar_wait_bounded(&bar_m[s1], pm[s1])) atomicOr(err, 4), fail_sh = 1;
+                pm[s1] ^= 1;
+                tc_fence_after();
             }
+            issue(t0 + i + 1, s1);
+            asm volatile("cp.async.wait_group 1;" ::: "memory");
+        } else {
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
         }
-        cp_async_wait_all();
         fence_proxy_async();
         __syncthreads();
+        if (fail_sh) break;
         if (tid == 0) {
-            bool ok = mbar_wait_bounded(&bar_b, phase_b);
-            if (!ok) {
+            if (!mbar_wait_bounded(&bar_b[s], pb[s])) {
                 atomicOr(err, 4);
                 fail_sh = 1;
             } else {
                 tc_fence_after();
-                const uint32_t a_hi = smem_u32(Ahi), a_lo = smem_u32(Alo);
-                const uint32_t b_hi = smem_u32(Bhi), b_lo = smem_u32(Blo);
+                const uint32_t a_hi = smem_u32(stage_ptr(s));
+                const uint32_t a_lo = a_hi + (uint32_t)(kTcRows * KP) * 4u;
+                const uint32_t b_hi = a_lo + (uint32_t)(kTcRows * KP) * 4u;
+                const uint32_t b_lo = b_hi + bbytes;
                 for (int e = 0; e < sch.nent; e++) {
                     const uint32_t idesc = idesc_tf32(kTcRows, sch.nn[e]);
                     const uint32_t b_lbo = (uint32_t)(sch.nn[e] / 8) * 128u;
@@ -317,36 +379,37 @@ __global__ void __launch_bounds__(kTcThreads, 1) m2l_tc_kernel(const M2LTile* __
                         for (int k = 0; k < sch.ks[e]; k++) {
                             const uint64_t ad = smem_desc(a_base + 2u * (uint32_t)k * a_lbo, a_lbo, 128u);
                             const uint64_t bd = smem_desc(b_base + 2u * (uint32_t)k * b_lbo, b_lbo, 128u);
-                            mma_tf32(d, ad, bd, idesc, (started || prod > 0 || k > 0) ? 1u : 0u);
+                            mma_tf32(d, ad, bd, idesc, (i > 0 || prod > 0 || k > 0) ? 1u : 0u);
                         }
                     }
                 }
-                mma_commit(&bar_mma);
+                mma_commit(&bar_m[s]);
             }
         }
-        phase_b ^= 1;
-        __syncthreads();
-        if (fail_sh) break;
-        if (!mbar_wait_bounded(&bar_mma, phase_m)) {
-            atomicOr(err, 4);
-            fail_sh = 1;
+        pb[s] ^= 1;
+        if (NST == 1) {
+            __syncthreads();
+            if (fail_sh) break;
+            if (!mbar_wait_bounded(&bar_m[s], pm[s])) atomicOr(err, 4), fail_sh = 1;
+            pm[s] ^= 1;
+            tc_fence_after();
+            __syncthreads();
         }
-        phase_m ^= 1;
-        started = true;
-        tc_fence_after();
-        __syncthreads();
-        if (fail_sh) break;
     }
+    if (NST == 2 && nt > 0 && !fail_sh) {  // last commit: every MMA of this CTA is done
+        const int s = (nt - 1) & 1;
+        if (!mbar_wait_bounded(&bar_m[s], pm[s])) atomicOr(err, 4), fail_sh = 1;
+    }
+    __syncthreads();
 
     // epilogue: TMEM lanes 32 w .. 32 w + 31 hold the rows of warp w; the loads
-    // are warp-collective, so every lane takes part and only rows with a box
-    // store (fail_sh and started are uniform over the CTA here)
+    // are warp-collective, so every lane takes part and only rows with a box store
     tc_fence_after();
     if (!fail_sh) {
-        float* out = slot >= 0 ? lp.Lp[l] + ((size_t)chunk * lp.cap[l] + slot) * ld : nullptr;
+        float* out = slot >= 0 ? lp.Lp[level] + ((size_t)chunk * lp.cap[level] + slot) * ld : nullptr;
         for (int c0 = 0; c0 < sch.NP; c0 += 16) {
             float v[16];
-            if (started) {
+            if (nt > 0) {
                 tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
             } else {
 #pragma unroll
@@ -369,7 +432,7 @@ static TcState* state(polfmm_ctx* c) { return reinterpret_cast<TcState*>(c->tc);
 
 bool m2l_tensor_enabled(polfmm_ctx* c) {
     TcState* S = state(c);
-    return c->mixed && c->opt.m2l_impl != POLFMM_M2L_SIMT && S && S->ready;
+    return c->mixed && c->opt.m2l_impl != POLFMM_M2L_SIMT && S && S->ready && S->ntiles > 0;
 }
 
 static int degree_of(int idx, int p) {
@@ -422,8 +485,11 @@ int m2l_tensor_prepare(polfmm_ctx* c) {
         sch.bpart = off;
         sch.tmem_cols = 32;
         while (sch.tmem_cols < sch.NP) sch.tmem_cols *= 2;
-        S->smem = sizeof(float) * (2 * (size_t)kTcRows * sch.KP + 2 * (size_t)sch.bpart) + 1024;
-        if (S->smem > 227 * 1024) {
+        S->stage_bytes = sizeof(float) * (2 * (size_t)kTcRows * sch.KP + 2 * (size_t)sch.bpart);
+        const size_t limit = 227 * 1024;
+        S->stages = 2 * S->stage_bytes + 1024 <= limit ? 2 : 1;
+        S->smem = S->stages * S->stage_bytes + 1024;
+        if (S->smem > limit) {
             delete S;
             c->tc = nullptr;
             return POLFMM_OK;  // does not fit: the SIMT kernel stays in use
@@ -478,16 +544,67 @@ int m2l_tensor_prepare(polfmm_ctx* c) {
                 return POLFMM_ERR_OUT_OF_MEMORY;
             }
         }
-        if (cudaFuncSetAttribute(m2l_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S->smem) !=
-            cudaSuccess) {
+        size_t rows_cap = 0;
+        for (int l = 2; l <= c->depth; l++) rows_cap += c->lv[l].cap;
+        if (cudaMalloc(&S->rows, sizeof(int2) * std::max<size_t>(rows_cap, 1)) != cudaSuccess) {
+            cudaGetLastError();
+            return POLFMM_ERR_OUT_OF_MEMORY;
+        }
+        cudaError_t e1 = cudaFuncSetAttribute(m2l_tc_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)S->smem);
+        cudaError_t e2 = cudaFuncSetAttribute(m2l_tc_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)S->smem);
+        if (e1 != cudaSuccess || e2 != cudaSuccess) {
             cudaGetLastError();
             return POLFMM_ERR_CUDA;
         }
         S->ready = true;
     }
-    // the tensor-core kernel has one CTA per SM: split the offsets further
-    if (c->ntiles > 0) {
-        int want = (2 * c->num_sms + c->ntiles - 1) / c->ntiles;
+    // rows of all levels >= 2 grouped by octant class, and tiles of 128 rows
+    int total[8] = {0};
+    for (int l = 2; l <= c->depth; l++)
+        for (int k = 0; k < 8; k++) total[k] += c->lv[l].class_count[k];
+    int cls_first[8];
+    int run = 0;
+    for (int k = 0; k < 8; k++) {
+        cls_first[k] = run;
+        run += total[k];
+    }
+    int fill[8];
+    for (int k = 0; k < 8; k++) fill[k] = cls_first[k];
+    for (int l = 2; l <= c->depth; l++) {
+        Level& B = c->lv[l];
+        TcRowArgs ra;
+        for (int k = 0; k < 8; k++) {
+            ra.off[k] = fill[k];
+            ra.start[k] = B.class_start[k];
+            fill[k] += B.class_count[k];
+        }
+        if (B.nbox > 0) {
+            LaunchScope ls(c, F_TREE);
+            tc_rows_kernel<<<grid_for(B.nbox, 256), 256, 0, c->stream>>>(B.nbox, l, B.by_class, B.key, ra, S->rows);
+        }
+    }
+    std::vector<TcTile> tl;
+    for (int k = 0; k < 8; k++)
+        for (int f = 0; f < total[k]; f += kTcRows) tl.push_back(TcTile{k, cls_first[k] + f, std::min(kTcRows, total[k] - f)});
+    S->ntiles = (int)tl.size();
+    if (S->ntiles > S->tiles_cap) {
+        if (S->tiles) cudaFree(S->tiles);
+        S->tiles = nullptr;
+        S->tiles_cap = std::max(S->ntiles, 16);
+        if (cudaMalloc(&S->tiles, sizeof(TcTile) * S->tiles_cap) != cudaSuccess) {
+            cudaGetLastError();
+            return POLFMM_ERR_OUT_OF_MEMORY;
+        }
+    }
+    if (S->ntiles &&
+        cudaMemcpyAsync(S->tiles, tl.data(), sizeof(TcTile) * S->ntiles, cudaMemcpyHostToDevice, c->stream) !=
+            cudaSuccess)
+        return POLFMM_ERR_CUDA;
+    // the tensor-core kernel runs one or two CTAs per SM: split the offsets further
+    if (S->ntiles > 0) {
+        int want = (2 * c->num_sms + S->ntiles - 1) / S->ntiles;
         c->m2l_chunks = std::max(1, std::min(want, 27));
     }
     return POLFMM_OK;
@@ -497,32 +614,48 @@ void m2l_tensor_launch(polfmm_ctx* c) {
     TcState* S = state(c);
     const TcSchedule& sch = S->sch;
     TcLevelPtrs lp{};
+    TcSplitArgs sa{};
+    sa.lmin = 2;
+    sa.lmax = c->depth;
+    int64_t run = 0;
     for (int l = 2; l <= c->depth; l++) {
         Level& B = c->lv[l];
-        {
-            LaunchScope ls(c, F_M2L);
-            int64_t tot = (int64_t)B.nbox * sch.KP;
-            tc_split_kernel<<<grid_for(tot, 256), 256, 0, c->stream>>>(B.nbox, (const float*)B.M, c->ld, c->ncoef,
-                                                                       sch.KP, S->Mhi[l], S->Mlo[l]);
-        }
+        sa.M[l] = (const float*)B.M;
+        sa.hi[l] = S->Mhi[l];
+        sa.lo[l] = S->Mlo[l];
+        sa.start[l] = run;
+        run += (int64_t)B.nbox * sch.KP;
         lp.key[l] = B.key;
         lp.map[l] = B.map;
-        lp.by_class[l] = B.by_class;
         lp.Mhi[l] = S->Mhi[l];
         lp.Mlo[l] = S->Mlo[l];
         lp.Lp[l] = (float*)B.Lp;
         lp.cap[l] = B.cap;
     }
+    sa.start[c->depth + 1] = run;
+    {
+        LaunchScope ls(c, F_P2M);
+        tc_split_kernel<<<grid_for(run, 256), 256, 0, c->stream>>>(sa, c->ld, c->ncoef, sch.KP);
+    }
     LaunchScope ls(c, F_M2L);
-    dim3 grid(c->ntiles, c->m2l_chunks);
-    m2l_tc_kernel<<<grid, kTcThreads, S->smem, c->stream>>>(c->tiles, lp, S->Bimg, c->tab.class_off, sch, c->ncoef,
-                                                            c->ld, c->m2l_chunks, c->err);
+    dim3 grid(S->ntiles, c->m2l_chunks);
+    const int stage_floats = (int)(S->stage_bytes / sizeof(float));
+    if (S->stages == 2)
+        m2l_tc_kernel<2><<<grid, kTcThreads, S->smem, c->stream>>>(S->tiles, S->rows, lp, S->Bimg, c->tab.class_off,
+                                                                   sch, c->ncoef, c->ld, c->m2l_chunks,
+                                                                   stage_floats, c->err);
+    else
+        m2l_tc_kernel<1><<<grid, kTcThreads, S->smem, c->stream>>>(S->tiles, S->rows, lp, S->Bimg, c->tab.class_off,
+                                                                   sch, c->ncoef, c->ld, c->m2l_chunks,
+                                                                   stage_floats, c->err);
 }
 
 void m2l_tensor_release(polfmm_ctx* c) {
     TcState* S = state(c);
     if (!S) return;
     if (S->Bimg) cudaFree(S->Bimg);
+    if (S->rows) cudaFree(S->rows);
+    if (S->tiles) cudaFree(S->tiles);
     for (int l = 0; l <= kMaxDepth; l++) {
         if (S->Mhi[l]) cudaFree(S->Mhi[l]);
         if (S->Mlo[l]) cudaFree(S->Mlo[l]);

@@ -382,6 +382,30 @@ __global__ void class_count_kernel(const int* __restrict__ key, const int* __res
     if (threadIdx.x < 8) atomicAdd(&cnt8[threadIdx.x], h[threadIdx.x]);
 }
 
+// near-field work of each leaf (targets x sources in the 27 adjacent leaves),
+// as an ascending sort key for descending work
+__global__ void leaf_work_kernel(int nleaf, int depth, const int* __restrict__ lkey, const int* __restrict__ lcount,
+                                 const int* __restrict__ lmap, uint32_t* __restrict__ key, int* __restrict__ idx) {
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nleaf) return;
+    const uint32_t k = (uint32_t)lkey[b];
+    const int bx = (int)compact3(k), by = (int)compact3(k >> 1), bz = (int)compact3(k >> 2);
+    const int nside = 1 << depth;
+    long src = 0;
+    for (int dz = -1; dz <= 1; dz++)
+        for (int dy = -1; dy <= 1; dy++)
+            for (int dx = -1; dx <= 1; dx++) {
+                int ax = bx + dx, ay = by + dy, az = bz + dz;
+                if (ax < 0 || ay < 0 || az < 0 || ax >= nside || ay >= nside || az >= nside) continue;
+                int s = lmap[morton3(ax, ay, az)];
+                if (s >= 0) src += lcount[s];
+            }
+    long w = (long)lcount[b] * src;
+    long q = w >> 4;
+    key[b] = 0xFFFFu - (uint32_t)(q > 0xFFFF ? 0xFFFF : q);
+    idx[b] = b;
+}
+
 int tree_build(polfmm_ctx* c, const double* x_in) {
     const int64_t n = c->n;
     const int d = c->depth;
@@ -493,6 +517,19 @@ int tree_tables(polfmm_ctx* c, const double* x_in, const double* q_in, const dou
     }
     cudaMemcpyAsync(c->h_counts, nbox_dev, sizeof(int) * (kMaxDepth + 1) * 9, cudaMemcpyDeviceToHost, st);
     if (cudaStreamSynchronize(st) != cudaSuccess) return POLFMM_ERR_CUDA;
+    // leaves in descending order of near-field work, so that the heaviest
+    // leaf blocks start first and the lighter ones fill in behind them
+    {
+        const int nl = c->h_counts[d];
+        {
+            LaunchScope ls(c, F_TREE);
+            leaf_work_kernel<<<grid_for(nl, 256), 256, 0, st>>>(nl, d, L.key, c->lcount, L.map, c->key_tmp,
+                                                                c->val_tmp);
+        }
+        uint32_t* kb = reinterpret_cast<uint32_t*>(c->flags);
+        radix_pass<8>(c, c->key_tmp, c->val_tmp, kb, c->val_a, nullptr, nl, 0);
+        radix_pass<8>(c, kb, c->val_a, c->key_tmp, c->leaf_order, nullptr, nl, 8);
+    }
     for (int l = 0; l <= d; l++) {
         Level& B = c->lv[l];
         B.nbox = c->h_counts[l];
