@@ -80,6 +80,8 @@ typedef struct {
     int m2l_impl;        /* POLFMM_M2L_* */
     int profile;         /* 1: time kernels with CUDA events (see fmm_profile_get) */
     void* cuda_stream;   /* cudaStream_t for all work; NULL = the legacy default stream */
+    int no_graphs;       /* 1: launch every solver iteration kernel by kernel instead of replaying a
+                            CUDA graph of one iteration (graphs are also off while profiling) */
 } polfmm_options;
 
 /* Fill *opt with the defaults: FP64, PCG, max_iter 100, coulomb_k 1, bounding

@@ -40,6 +40,7 @@ class Options(ctypes.Structure):
         ("m2l_impl", ctypes.c_int),
         ("profile", ctypes.c_int),
         ("cuda_stream", ctypes.c_void_p),
+        ("no_graphs", ctypes.c_int),
     ]
 
 

@@ -436,7 +436,63 @@ int rebuild(polfmm_ctx* c) {
     if ((rc = ensure_lp(c)) != POLFMM_OK) return rc;
     pack_positions(c);
     fmm_pass(c, LEAF_CHARGE_PHI_E, true, nullptr, c->phiq, c->Eq, nullptr);
+    c->pcg_graph_dirty = true;  // launch sizes of the solver iteration changed
     return read_err(c);
+}
+
+// Capture one PCG iteration (FMM dipole-field pass + vector updates) as a CUDA
+// graph on a private stream; later trees update the executable in place.
+int capture_pcg_graph(polfmm_ctx* c) {
+    if (!c->cap_stream &&
+        cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+        return POLFMM_ERR_CUDA;
+    cudaStream_t orig = c->stream;
+    const int64_t l0 = c->launches;
+    c->stream = c->cap_stream;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        solver_pcg_step(c);
+        e = cudaStreamEndCapture(c->cap_stream, &g);
+    }
+    c->stream = orig;
+    c->pcg_graph_launches = c->launches - l0;
+    c->launches = l0;
+    if (e != cudaSuccess || !g) {
+        cudaGetLastError();
+        return POLFMM_ERR_CUDA;
+    }
+    if (c->pcg_graph) {
+        cudaGraphExecUpdateResultInfo info;
+        if (cudaGraphExecUpdate(c->pcg_graph, g, &info) != cudaSuccess) {
+            cudaGetLastError();
+            cudaGraphExecDestroy(c->pcg_graph);
+            c->pcg_graph = nullptr;
+        }
+    }
+    if (!c->pcg_graph && cudaGraphInstantiate(&c->pcg_graph, g, 0) != cudaSuccess) {
+        cudaGetLastError();
+        c->pcg_graph = nullptr;
+        cudaGraphDestroy(g);
+        return POLFMM_ERR_CUDA;
+    }
+    cudaGraphDestroy(g);
+    c->pcg_graph_dirty = false;
+    return POLFMM_OK;
+}
+
+int pcg_iteration(polfmm_ctx* c) {
+    if (c->opt.no_graphs || c->opt.profile) {
+        solver_pcg_step(c);
+        return POLFMM_OK;
+    }
+    if (c->pcg_graph_dirty || !c->pcg_graph) {
+        int rc = capture_pcg_graph(c);
+        if (rc != POLFMM_OK) return rc;
+    }
+    if (cudaGraphLaunch(c->pcg_graph, c->stream) != cudaSuccess) return POLFMM_ERR_CUDA;
+    c->launches += c->pcg_graph_launches;
+    return POLFMM_OK;
 }
 
 void destroy_impl(polfmm_ctx* c) {
@@ -455,6 +511,8 @@ void destroy_impl(polfmm_ctx* c) {
     if (c->h_bbox) cudaFreeHost(c->h_bbox);
     if (c->ev_created)
         for (int i = 0; i < 2 * 4096; i++) cudaEventDestroy(c->ev_pool[i]);
+    if (c->pcg_graph) cudaGraphExecDestroy(c->pcg_graph);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     delete X;
     delete c;
 }
@@ -574,7 +632,7 @@ int fmm_solve_induced_dipoles(polfmm_ctx* c, double tol, int* iters_out, double*
     if (!jacobi) {
         res = sqrt(c->h_scal[S_RR] / bb);
         while (res > tol && it < c->opt.max_iter) {
-            solver_pcg_step(c);
+            if ((rc = pcg_iteration(c)) != POLFMM_OK) return rc;
             it++;
             if ((rc = fetch()) != POLFMM_OK) return rc;
             if (!(c->h_scal[S_DAD] > 0.0)) {  // operator not positive definite (polarization catastrophe)

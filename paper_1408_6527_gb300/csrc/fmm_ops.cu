@@ -253,7 +253,7 @@ __global__ void __launch_bounds__(256) m2l_simt_kernel(const M2LTile* __restrict
 // target t and every slices-th source, and the slices are added in a fixed
 // order at the end.  The self pair has r = 0 exactly and is masked.
 // ---------------------------------------------------------------------------
-constexpr int kLeafThreads = 128;
+constexpr int kLeafThreads = 256;
 
 template <typename R>
 struct alignas(sizeof(R) == 4 ? 16 : 16) Q4 {

@@ -162,6 +162,10 @@ struct polfmm_ctx {
     bool have_mu = false;
     int64_t launches = 0;
     void* extra = nullptr;        // host-side bookkeeping of device allocations
+    cudaStream_t cap_stream = nullptr;     // private stream for graph capture
+    cudaGraphExec_t pcg_graph = nullptr;   // one PCG iteration of the current tree
+    bool pcg_graph_dirty = true;
+    int64_t pcg_graph_launches = 0;
     void* tc = nullptr;           // tensor-core M2L state
     // profiling
     cudaEvent_t ev_pool[2 * 4096];

@@ -305,3 +305,19 @@ def test_tensor_core_m2l_forces_within_gate(w2):
             f.solve(1e-8 if mode == "fp64" else 1e-7)
             outs[mode] = host(f.energy_forces()["F"])
     assert oracle.rel_rms(outs["mixed"], outs["fp64"]) < MIXED_FORCE_TOL
+
+
+def test_graph_replay_matches_direct_launches(w1):
+    res = {}
+    for graphs in (True, False):
+        with PolFMM(dev(w1.pos), dev(w1.q), dev(w1.alpha), p=4, depth=3, mode="mixed", graphs=graphs) as f:
+            info = f.solve(1e-7)
+            res[graphs] = (info["iterations"], host(f.dipoles()), host(f.energy_forces()["F"]))
+            # a new tree re-captures (or updates) the graph
+            f.update_positions(dev(w1.pos * 1.01))
+            f.reset_dipoles()
+            f.solve(1e-7)
+            res[graphs] += (host(f.dipoles()),)
+    assert res[True][0] == res[False][0]
+    for k in (1, 2, 3):
+        np.testing.assert_array_equal(res[True][k], res[False][k])
