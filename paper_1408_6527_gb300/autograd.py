@@ -15,11 +15,11 @@ import torch
 
 class _PolarizableEnergy(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, pos, q, alpha, p, depth, mode, tol, max_iter, coulomb_k, recompute_tree):
+    def forward(ctx, pos, q, alpha, p, depth, mode, tol, max_iter, coulomb_k, root_box):
         from . import PolFMM
 
         fmm = PolFMM(pos.detach(), q.detach(), alpha.detach(), p=p, depth=depth, mode=mode, max_iter=max_iter,
-                     coulomb_k=coulomb_k)
+                     coulomb_k=coulomb_k, root_box=root_box)
         info = fmm.solve(tol)
         out = fmm.energy_forces(forces=True, dq=True, dalpha=True)
         ctx.info = info
@@ -38,11 +38,11 @@ class _PolarizableEnergyTwoPass(torch.autograd.Function):
     force pass on it, so the gradient pass happens only when asked for."""
 
     @staticmethod
-    def forward(ctx, pos, q, alpha, p, depth, mode, tol, max_iter, coulomb_k):
+    def forward(ctx, pos, q, alpha, p, depth, mode, tol, max_iter, coulomb_k, root_box):
         from . import PolFMM
 
         fmm = PolFMM(pos.detach(), q.detach(), alpha.detach(), p=p, depth=depth, mode=mode, max_iter=max_iter,
-                     coulomb_k=coulomb_k)
+                     coulomb_k=coulomb_k, root_box=root_box)
         info = fmm.solve(tol)
         st = fmm.static_field()
         mu = fmm.dipoles()
@@ -57,16 +57,18 @@ class _PolarizableEnergyTwoPass(torch.autograd.Function):
         out = ctx.fmm.energy_forces(forces=True, dq=True, dalpha=True)
         ctx.fmm.close()
         ctx.fmm = None
-        return gU * (-out["F"]), gU * out["dUdq"], gU * out["dUdalpha"], None, None, None, None, None, None
+        return gU * (-out["F"]), gU * out["dUdq"], gU * out["dUdalpha"], None, None, None, None, None, None, None
 
 
 def polarizable_energy(pos, q, alpha, p=6, depth=4, mode="fp64", tol=1e-8, max_iter=200, coulomb_k=1.0,
-                       keep_context=True):
+                       keep_context=True, root_box=None):
     """U(pos, q, alpha) for CUDA float64 tensors; differentiable in all three.
 
     keep_context=True keeps the tree, static pass and dipoles from the forward
     pass and runs the force pass in backward; False computes the gradients in
-    forward and frees the device state at once."""
+    forward and frees the device state at once.  root_box = (lo[3], side)
+    fixes the root cube (e.g. for finite differences, so that no site changes
+    leaf); None uses the bounding cube of the positions."""
     if keep_context:
-        return _PolarizableEnergyTwoPass.apply(pos, q, alpha, p, depth, mode, tol, max_iter, coulomb_k)
-    return _PolarizableEnergy.apply(pos, q, alpha, p, depth, mode, tol, max_iter, coulomb_k, False)
+        return _PolarizableEnergyTwoPass.apply(pos, q, alpha, p, depth, mode, tol, max_iter, coulomb_k, root_box)
+    return _PolarizableEnergy.apply(pos, q, alpha, p, depth, mode, tol, max_iter, coulomb_k, root_box)
