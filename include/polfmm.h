@@ -235,6 +235,11 @@ POLFMM_API int fmm_sort_sites_noalloc(int64_t n, const double* positions, int tr
 /* Release every device buffer of the context; NULL is a no-op. */
 POLFMM_API void fmm_destroy(polfmm_ctx* ctx);
 
+/* Description of the CUDA failure behind the last POLFMM_ERR_CUDA returned on
+ * the calling thread ("" if none): the CUDA error name and string, or which
+ * bounded device wait timed out. */
+POLFMM_API const char* fmm_last_error(void);
+
 /* Static description of a status code. */
 POLFMM_API const char* fmm_status_string(int status);
 

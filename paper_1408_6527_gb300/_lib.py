@@ -73,6 +73,7 @@ SIGNATURES = {
     "fmm_destroy": (None, [P]),
     "fmm_sort_sites_noalloc": (I, [I64, P, I, P, P, P, P, P, P]),
     "fmm_status_string": (ctypes.c_char_p, [I]),
+    "fmm_last_error": (ctypes.c_char_p, []),
 }
 
 
@@ -109,6 +110,8 @@ class PolFMMError(RuntimeError):
         self.status = status
         try:
             msg = load().fmm_status_string(status).decode()
+            if status == ERR_CUDA:
+                msg += ": " + load().fmm_last_error().decode()
         except Exception:  # pragma: no cover
             msg = f"status {status}"
         super().__init__(f"{where}: {msg} ({status})")

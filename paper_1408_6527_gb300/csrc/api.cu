@@ -3,6 +3,7 @@
 // pass in fmm_build, iterative dipoles in fmm_solve_induced_dipoles, energy
 // and forces in fmm_energy_forces), and the index / derivative tables.
 #include <math.h>
+#include <stdio.h>
 #include <string.h>
 
 #include <algorithm>
@@ -372,15 +373,25 @@ int ensure_lp(polfmm_ctx* c) {
     return POLFMM_OK;
 }
 
+thread_local char g_last_error[256] = "";
+
+int cuda_fail(cudaError_t e, const char* where) {
+    snprintf(g_last_error, sizeof(g_last_error), "%s: %s (%s)", where, cudaGetErrorName(e), cudaGetErrorString(e));
+    return POLFMM_ERR_CUDA;
+}
+
 int read_err(polfmm_ctx* c) {
     int h[4] = {0, 0, 0, 0};
-    if (cudaMemcpyAsync(h, c->err, sizeof(int) * 4, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
-        return POLFMM_ERR_CUDA;
-    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return POLFMM_ERR_CUDA;
-    if (cudaGetLastError() != cudaSuccess) return POLFMM_ERR_CUDA;
+    cudaError_t e = cudaMemcpyAsync(h, c->err, sizeof(int) * 4, cudaMemcpyDeviceToHost, c->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "copy of the error word");
+    if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return cuda_fail(e, "stream synchronize");
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "kernel launch");
     if (h[0] & 1) return POLFMM_ERR_INVALID_ARG;
     if (h[0] & 2) return POLFMM_ERR_COINCIDENT;
-    if (h[0] & 4) return POLFMM_ERR_CUDA;  // a bounded device wait timed out
+    if (h[0] & 4) {
+        snprintf(g_last_error, sizeof(g_last_error), "a bounded wait of the tensor-core M2L kernel timed out");
+        return POLFMM_ERR_CUDA;
+    }
     return POLFMM_OK;
 }
 
@@ -432,7 +443,10 @@ int rebuild(polfmm_ctx* c) {
     if ((rc = tree_tables(c, x_in, q_in, a_in)) != POLFMM_OK) return rc;
     if ((rc = read_err(c)) != POLFMM_OK) return rc;
     if ((rc = m2l_setup(c)) != POLFMM_OK) return rc;
-    if ((rc = m2l_tensor_prepare(c)) != POLFMM_OK) return rc;  // may raise the offset-chunk count
+    if ((rc = m2l_tensor_prepare(c)) != POLFMM_OK) {  // may raise the offset-chunk count
+        if (rc == POLFMM_ERR_CUDA) cuda_fail(cudaGetLastError(), "tensor-core M2L set-up");
+        return rc;
+    }
     if ((rc = ensure_lp(c)) != POLFMM_OK) return rc;
     pack_positions(c);
     fmm_pass(c, LEAF_CHARGE_PHI_E, true, nullptr, c->phiq, c->Eq, nullptr);
@@ -591,6 +605,7 @@ int fmm_build(polfmm_ctx** out, int64_t n, const double* positions, const double
     }
     if ((rc = allocate(c)) != POLFMM_OK || (rc = build_tables(c)) != POLFMM_OK ||
         (rc = fmm_ops_init_attributes(c)) != POLFMM_OK) {
+        if (rc == POLFMM_ERR_CUDA) cuda_fail(cudaGetLastError(), "set-up (tables or kernel attributes)");
         destroy_impl(c);
         return rc;
     }
@@ -830,6 +845,8 @@ int fmm_profile_reset(polfmm_ctx* c) {
 int64_t fmm_launch_count(polfmm_ctx* c) { return c ? c->launches : 0; }
 
 void fmm_destroy(polfmm_ctx* c) { destroy_impl(c); }
+
+const char* fmm_last_error(void) { return g_last_error; }
 
 const char* fmm_status_string(int s) {
     switch (s) {

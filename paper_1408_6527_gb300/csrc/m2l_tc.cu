@@ -394,6 +394,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) m2l_tc_kernel(const TcTile* __r
             pm[s] ^= 1;
             tc_fence_after();
             __syncthreads();
+            if (fail_sh) break;
+            if (i + 1 < nt) issue(t0 + i + 1, 0);  // the single stage is free again
         }
     }
     if (NST == 2 && nt > 0 && !fail_sh) {  // last commit: every MMA of this CTA is done
