@@ -168,6 +168,19 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
     for (int k = 0; k < 16; k++) v[k] = __uint_as_float(r[k]);
 }
 
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const float* v) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16};" ::"r"(taddr),
+        "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])), "r"(__float_as_uint(v[3])),
+        "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])), "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])),
+        "r"(__float_as_uint(v[8])), "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])),
+        "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])), "r"(__float_as_uint(v[15]))
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
 // shared-memory matrix descriptor, K-major, no swizzle: core matrices of
 // 8 rows x 16 bytes; lbo = byte step between core matrices along K, sbo =
 // byte step between 8-row groups along M / N.
@@ -345,12 +358,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) m2l_tc_kernel(const TcTile* __r
         const int s = NST == 2 ? (i & 1) : 0;
         const bool prefetch = NST == 2 && i + 1 < nt;
         if (prefetch) {
-            const int s1 = (i + 1) & 1;
-            if (i >= 1) {  // the MMAs of offset i - 1 read stage s1: wait for them
-                if (!mbar_wait_bounded(&bar_m[s1], pm[s1])) atomicOr(err, 4), fail_sh = 1;
-                pm[s1] ^= 1;
-                tc_fence_after();
-            }
+            const int s1 = (i + 1) & 1;  // the MMAs of offset i - 1 (stage s1) finished last iteration
             issue(t0 + i + 1, s1);
             asm volatile("cp.async.wait_group 1;" ::: "memory");
         } else {
@@ -369,17 +377,23 @@ __global__ void __launch_bounds__(kTcThreads, 1) m2l_tc_kernel(const TcTile* __r
                 const uint32_t a_lo = a_hi + (uint32_t)(kTcRows * KP) * 4u;
                 const uint32_t b_hi = a_lo + (uint32_t)(kTcRows * KP) * 4u;
                 const uint32_t b_lo = b_hi + bbytes;
+                // this offset alone into the accumulator: the two small correction
+                // products first, the main product last; the first MMA of each band
+                // overwrites
                 for (int e = 0; e < sch.nent; e++) {
                     const uint32_t idesc = idesc_tf32(kTcRows, sch.nn[e]);
                     const uint32_t b_lbo = (uint32_t)(sch.nn[e] / 8) * 128u;
                     const uint32_t d = tmem + (uint32_t)sch.n0[e];
-                    for (int prod = 0; prod < 3; prod++) {
+                    int first = 1;
+                    for (int pi = 0; pi < 3; pi++) {
+                        const int prod = pi == 0 ? 1 : (pi == 1 ? 2 : 0);  // hi*lo, lo*hi, hi*hi
                         const uint32_t a_base = prod == 2 ? a_lo : a_hi;
                         const uint32_t b_base = (prod == 1 ? b_lo : b_hi) + (uint32_t)sch.boff[e] * 4u;
                         for (int k = 0; k < sch.ks[e]; k++) {
                             const uint64_t ad = smem_desc(a_base + 2u * (uint32_t)k * a_lbo, a_lbo, 128u);
                             const uint64_t bd = smem_desc(b_base + 2u * (uint32_t)k * b_lbo, b_lbo, 128u);
-                            mma_tf32(d, ad, bd, idesc, (i > 0 || prod > 0 || k > 0) ? 1u : 0u);
+                            mma_tf32(d, ad, bd, idesc, first ? 0u : 1u);
+                            first = 0;
                         }
                     }
                 }
@@ -387,20 +401,31 @@ __global__ void __launch_bounds__(kTcThreads, 1) m2l_tc_kernel(const TcTile* __r
             }
         }
         pb[s] ^= 1;
-        if (NST == 1) {
-            __syncthreads();
-            if (fail_sh) break;
-            if (!mbar_wait_bounded(&bar_m[s], pm[s])) atomicOr(err, 4), fail_sh = 1;
-            pm[s] ^= 1;
-            tc_fence_after();
-            __syncthreads();
-            if (fail_sh) break;
-            if (i + 1 < nt) issue(t0 + i + 1, 0);  // the single stage is free again
-        }
-    }
-    if (NST == 2 && nt > 0 && !fail_sh) {  // last commit: every MMA of this CTA is done
-        const int s = (nt - 1) & 1;
+        // wait for this offset's MMAs, then fold the accumulator into the running
+        // sum with round-to-nearest FP32 additions (warp w: TMEM lanes 32 w ..)
+        __syncthreads();
+        if (fail_sh) break;
         if (!mbar_wait_bounded(&bar_m[s], pm[s])) atomicOr(err, 4), fail_sh = 1;
+        pm[s] ^= 1;
+        tc_fence_after();
+        {
+            const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+            for (int c0 = 0; c0 < sch.NP; c0 += 16) {
+                float a[16], b[16];
+                tmem_ld16(lane_base + (uint32_t)c0, a);
+                if (i > 0) {
+                    tmem_ld16(lane_base + (uint32_t)(sch.NP + c0), b);
+#pragma unroll
+                    for (int k = 0; k < 16; k++) a[k] += b[k];
+                }
+                tmem_st16(lane_base + (uint32_t)(sch.NP + c0), a);
+            }
+            tmem_wait_st();
+        }
+        tc_fence_before();
+        __syncthreads();
+        if (fail_sh) break;
+        if (NST == 1 && i + 1 < nt) issue(t0 + i + 1, 0);  // the single stage is free again
     }
     __syncthreads();
 
@@ -412,7 +437,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) m2l_tc_kernel(const TcTile* __r
         for (int c0 = 0; c0 < sch.NP; c0 += 16) {
             float v[16];
             if (nt > 0) {
-                tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+                tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(sch.NP + c0), v);
             } else {
 #pragma unroll
                 for (int k = 0; k < 16; k++) v[k] = 0.f;
@@ -485,8 +510,10 @@ int m2l_tensor_prepare(polfmm_ctx* c) {
             bnd = e + 1;
         }
         sch.bpart = off;
+        // TMEM: one accumulator for the current offset and one running sum (NP columns each)
         sch.tmem_cols = 32;
-        while (sch.tmem_cols < sch.NP) sch.tmem_cols *= 2;
+        while (sch.tmem_cols < 2 * sch.NP) sch.tmem_cols *= 2;
+        if (sch.tmem_cols > 512) return POLFMM_OK;  // the SIMT kernel stays in use
         S->stage_bytes = sizeof(float) * (2 * (size_t)kTcRows * sch.KP + 2 * (size_t)sch.bpart);
         const size_t limit = 227 * 1024;
         S->stages = 2 * S->stage_bytes + 1024 <= limit ? 2 : 1;
