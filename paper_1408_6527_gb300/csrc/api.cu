@@ -237,6 +237,9 @@ int build_tables(polfmm_ctx* c) {
     UP(m2m_src, T.m2m_src);
     UP(m2m_par, T.m2m_par);
     UP(m2m_w, T.m2m_w);
+    std::vector<float> m2m_wf(m2m_w.begin(), m2m_w.end()), l2l_wf(l2l_w.begin(), l2l_w.end());
+    UP(m2m_wf, T.m2m_wf);
+    UP(l2l_wf, T.l2l_wf);
     UP(l2l_ptr, T.l2l_ptr);
     UP(l2l_src, T.l2l_src);
     UP(l2l_par, T.l2l_par);
@@ -253,7 +256,7 @@ int build_tables(polfmm_ctx* c) {
 
 void free_tables(Tables& T) {
     void* ptrs[] = {T.mi, T.inv_fact, T.inv_fact_f, T.up1, T.up2, T.pre, T.add, T.m2m_ptr, T.m2m_src, T.m2m_par,
-                    T.m2m_w, T.l2l_ptr, T.l2l_src, T.l2l_par, T.l2l_w, T.D, T.Df, T.class_off, T.warp_out_ptr,
+                    T.m2m_w, T.m2m_wf, T.l2l_wf, T.l2l_ptr, T.l2l_src, T.l2l_par, T.l2l_w, T.D, T.Df, T.class_off, T.warp_out_ptr,
                     T.warp_out};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -318,6 +321,7 @@ int allocate(polfmm_ctx* c) {
     c->partial = A.get<double>((size_t)kRedSlots * kRedBlocks);
     c->scal = A.get<double>(S_COUNT + 8);
     c->err = A.get<int>(4);
+    c->ticket = A.get<int>(4);
     c->key_tmp = A.get<uint32_t>(n);
     c->val_tmp = A.get<int>(n);
     c->val_a = A.get<int>(n);
@@ -348,6 +352,7 @@ int allocate(polfmm_ctx* c) {
     if (cudaMallocHost(&c->h_counts, sizeof(int) * (kMaxDepth + 1) * 9) != cudaSuccess) return POLFMM_ERR_OUT_OF_MEMORY;
     if (cudaMallocHost(&c->h_bbox, sizeof(double) * 8) != cudaSuccess) return POLFMM_ERR_OUT_OF_MEMORY;
     cudaMemsetAsync(c->err, 0, sizeof(int) * 4, c->stream);
+    cudaMemsetAsync(c->ticket, 0, sizeof(int) * 4, c->stream);
     cudaMemsetAsync(c->scal, 0, sizeof(double) * (S_COUNT + 8), c->stream);
     return POLFMM_OK;
 }
@@ -527,6 +532,9 @@ void destroy_impl(polfmm_ctx* c) {
         for (int i = 0; i < 2 * 4096; i++) cudaEventDestroy(c->ev_pool[i]);
     if (c->pcg_graph) cudaGraphExecDestroy(c->pcg_graph);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    if (c->side_stream) cudaStreamDestroy(c->side_stream);
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
     delete X;
     delete c;
 }
@@ -602,6 +610,12 @@ int fmm_build(polfmm_ctx** out, int64_t n, const double* positions, const double
     if (o.profile) {
         for (int i = 0; i < 2 * 4096; i++) cudaEventCreate(&c->ev_pool[i]);
         c->ev_created = true;
+    }
+    if (cudaStreamCreateWithFlags(&c->side_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        c->side_stream = nullptr;
     }
     if ((rc = allocate(c)) != POLFMM_OK || (rc = build_tables(c)) != POLFMM_OK ||
         (rc = fmm_ops_init_attributes(c)) != POLFMM_OK) {

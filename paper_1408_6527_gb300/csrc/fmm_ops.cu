@@ -101,7 +101,7 @@ __global__ void __launch_bounds__(128) m2m_kernel(int npar, const int* __restric
                                                   const int* __restrict__ nchild, const int* __restrict__ ckey,
                                                   const R* __restrict__ Mc, R* __restrict__ Mp, int ld, int ncoef,
                                                   const int* __restrict__ ptr, const int* __restrict__ src,
-                                                  const int* __restrict__ par, const double* __restrict__ w) {
+                                                  const int* __restrict__ par, const R* __restrict__ w) {
     extern __shared__ unsigned char smem_raw[];
     R* S = reinterpret_cast<R*>(smem_raw);  // [8][ld]
     __shared__ int oct[8];
@@ -118,7 +118,7 @@ __global__ void __launch_bounds__(128) m2m_kernel(int npar, const int* __restric
         R acc = R(0);
         for (int e = ptr[cc]; e < ptr[cc + 1]; e++) {
             int s = src[e], pb = par[e];
-            R ww = R(w[e]);
+            R ww = w[e];
             for (int j = 0; j < nc; j++) {
                 R v = ww * S[j * ld + s];
                 acc += (__popc(pb & oct[j]) & 1) ? -v : v;
@@ -137,7 +137,7 @@ __global__ void __launch_bounds__(128) l2l_kernel(int nbox, int cap, int nchunk,
                                                   const int* __restrict__ parent, const R* __restrict__ Lp,
                                                   const R* __restrict__ Lpar, R* __restrict__ L, int ld, int ncoef,
                                                   const int* __restrict__ ptr, const int* __restrict__ src,
-                                                  const int* __restrict__ par, const double* __restrict__ w) {
+                                                  const int* __restrict__ par, const R* __restrict__ w) {
     extern __shared__ unsigned char smem_raw[];
     R* F = reinterpret_cast<R*>(smem_raw);  // parent locals [ld]
     const int b = blockIdx.x;
@@ -155,7 +155,7 @@ __global__ void __launch_bounds__(128) l2l_kernel(int nbox, int cap, int nchunk,
         for (int k = 0; k < nchunk; k++) acc += Lp[((int64_t)k * cap + b) * ld + cc];
         if (shift) {
             for (int e = ptr[cc]; e < ptr[cc + 1]; e++) {
-                R v = R(w[e]) * F[src[e]];
+                R v = w[e] * F[src[e]];
                 acc += (__popc(par[e] & noct) & 1) ? -v : v;
             }
         }
@@ -314,7 +314,7 @@ __global__ void __launch_bounds__(kLeafThreads) leaf_kernel(
     const Q4<R>* __restrict__ srcB,
     const R* __restrict__ Lf, int ld, int ncoef, const int* __restrict__ mi, const double* __restrict__ inv_fact,
     const int* __restrict__ up1, const int* __restrict__ up2, R h, double* __restrict__ out_phi,
-    double* __restrict__ out_E, double* __restrict__ out_G, int* __restrict__ err) {
+    double* __restrict__ out_E, double* __restrict__ out_G, int* __restrict__ err, int far) {
     constexpr int NC = LeafOut<MODE>::NC;
     constexpr int CAP = LeafCap<R>::N;
     constexpr bool HAS_PHI = MODE != LEAF_DIPOLE_E;
@@ -368,7 +368,7 @@ __global__ void __launch_bounds__(kLeafThreads) leaf_kernel(
         if (tid == 0) nb_pre[0] = 0;
     }
     for (int cc = tid; cc < ncoef; cc += blockDim.x) {
-        f[cc] = Lf[(int64_t)b * ld + cc];
+        f[cc] = far ? Lf[(int64_t)b * ld + cc] : R(0);
         ifact[cc] = R(inv_fact[cc]);
         cinfo[4 * cc] = mi[cc];
         cinfo[4 * cc + 1] = up1[3 * cc];
@@ -400,7 +400,7 @@ __global__ void __launch_bounds__(kLeafThreads) leaf_kernel(
             const R ux = xi * inv_h, uy = yi * inv_h, uz = zi * inv_h;
             R phi = R(0), d0 = R(0), d1 = R(0), d2 = R(0);
             R dd[6] = {R(0), R(0), R(0), R(0), R(0), R(0)};
-            for (int cc = s; cc < ncoef; cc += slices) {
+            for (int cc = far ? s : ncoef; cc < ncoef; cc += slices) {
                 const int pk = cinfo[4 * cc];
                 R wgt = ifact[cc];
                 for (int k = pk & 0xff; k > 0; k--) wgt *= ux;
@@ -528,6 +528,57 @@ __global__ void __launch_bounds__(kLeafThreads) leaf_kernel(
     }
 }
 
+// far field of the solver pass, added to the near field already in out_E:
+// E += -(1/h^2) sum_{|n| <= p-1} u^n/n! f_{n+e_d}, u = (x - z) / h (Sec. II.B)
+template <typename R>
+__global__ void __launch_bounds__(128) l2p_field_add_kernel(int nleaf, const int* __restrict__ lstart,
+                                                            const int* __restrict__ lcount,
+                                                            const Q4<R>* __restrict__ srcA, const R* __restrict__ Lf,
+                                                            int ld, int ncoef, const int* __restrict__ mi,
+                                                            const double* __restrict__ inv_fact,
+                                                            const int* __restrict__ up1, R h,
+                                                            double* __restrict__ out_E) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    R* f = reinterpret_cast<R*>(smem_raw);
+    R* ifact = f + ncoef;
+    int* cinfo = reinterpret_cast<int*>(ifact + ncoef);  // [ncoef][4]
+    const int b = blockIdx.x;
+    if (b >= nleaf) return;
+    for (int cc = threadIdx.x; cc < ncoef; cc += blockDim.x) {
+        f[cc] = Lf[(int64_t)b * ld + cc];
+        ifact[cc] = R(inv_fact[cc]);
+        cinfo[4 * cc] = mi[cc];
+        cinfo[4 * cc + 1] = up1[3 * cc];
+        cinfo[4 * cc + 2] = up1[3 * cc + 1];
+        cinfo[4 * cc + 3] = up1[3 * cc + 2];
+    }
+    __syncthreads();
+    const int s0 = lstart[b], cnt = lcount[b];
+    const R inv_h = R(1) / h;
+    for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
+        const int i = s0 + t;
+        const Q4<R> me = srcA[i];
+        const R ux = me.x * inv_h, uy = me.y * inv_h, uz = me.z * inv_h;
+        R d0 = R(0), d1 = R(0), d2 = R(0);
+        for (int cc = 0; cc < ncoef; cc++) {
+            const int u0 = cinfo[4 * cc + 1];
+            if (u0 < 0) continue;
+            const int pk = cinfo[4 * cc];
+            R wgt = ifact[cc];
+            for (int k = pk & 0xff; k > 0; k--) wgt *= ux;
+            for (int k = (pk >> 8) & 0xff; k > 0; k--) wgt *= uy;
+            for (int k = (pk >> 16) & 0xff; k > 0; k--) wgt *= uz;
+            d0 += wgt * f[u0];
+            d1 += wgt * f[cinfo[4 * cc + 2]];
+            d2 += wgt * f[cinfo[4 * cc + 3]];
+        }
+        const R s2 = -inv_h * inv_h;
+        out_E[3 * (int64_t)i] += (double)(d0 * s2);
+        out_E[3 * (int64_t)i + 1] += (double)(d1 * s2);
+        out_E[3 * (int64_t)i + 2] += (double)(d2 * s2);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
@@ -575,29 +626,30 @@ int m2l_setup(polfmm_ctx* c) {
 }
 
 template <typename R>
-static void launch_leaf(polfmm_ctx* c, int mode, const double* mu_sorted, double* phi, double* E, double* G) {
+static void launch_leaf(polfmm_ctx* c, int mode, const double* mu_sorted, double* phi, double* E, double* G,
+                        bool mu_packed, cudaStream_t st, int far) {
     Level& L = c->lv[c->depth];
     const R h = R(c->side / (double)(1 << c->depth));
     const Tables& T = c->tab;
     Q4<R>* A = reinterpret_cast<Q4<R>*>(c->srcA);
     Q4<R>* B = reinterpret_cast<Q4<R>*>(c->srcB);
-    if (mode != LEAF_CHARGE_PHI_E) {
+    if (mode != LEAF_CHARGE_PHI_E && !mu_packed) {
         LaunchScope ls(c, F_P2M);
-        pack_dipoles_kernel<R><<<grid_for(c->n, 256), 256, 0, c->stream>>>(c->n, mu_sorted, B);
+        pack_dipoles_kernel<R><<<grid_for(c->n, 256), 256, 0, st>>>(c->n, mu_sorted, B);
     }
     LaunchScope ls(c, mode == LEAF_DIPOLE_E ? F_LEAF_DIPOLE : (mode == LEAF_CHARGE_PHI_E ? F_LEAF_STATIC : F_LEAF_FULL));
 #define LEAF_ARGS                                                                                                  \
     L.nbox, L.key, c->lstart, c->lcount, L.map, c->leaf_order, c->depth, A, B, (const R*)L.L, c->ld, c->ncoef,     \
         T.mi, T.inv_fact,                                                                                      \
-        T.up1, T.up2, h, phi, E, G, c->err
+        T.up1, T.up2, h, phi, E, G, c->err, far
     if (mode == LEAF_DIPOLE_E)
         leaf_kernel<R, LEAF_DIPOLE_E>
-            <<<L.nbox, kLeafThreads, leaf_smem_bytes<R, LEAF_DIPOLE_E>(c->ncoef), c->stream>>>(LEAF_ARGS);
+            <<<L.nbox, kLeafThreads, leaf_smem_bytes<R, LEAF_DIPOLE_E>(c->ncoef), st>>>(LEAF_ARGS);
     else if (mode == LEAF_CHARGE_PHI_E)
         leaf_kernel<R, LEAF_CHARGE_PHI_E>
-            <<<L.nbox, kLeafThreads, leaf_smem_bytes<R, LEAF_CHARGE_PHI_E>(c->ncoef), c->stream>>>(LEAF_ARGS);
+            <<<L.nbox, kLeafThreads, leaf_smem_bytes<R, LEAF_CHARGE_PHI_E>(c->ncoef), st>>>(LEAF_ARGS);
     else
-        leaf_kernel<R, LEAF_FULL><<<L.nbox, kLeafThreads, leaf_smem_bytes<R, LEAF_FULL>(c->ncoef), c->stream>>>(
+        leaf_kernel<R, LEAF_FULL><<<L.nbox, kLeafThreads, leaf_smem_bytes<R, LEAF_FULL>(c->ncoef), st>>>(
             LEAF_ARGS);
 #undef LEAF_ARGS
 }
@@ -619,11 +671,31 @@ void m2l_tensor_launch(polfmm_ctx* c);  // m2l_tc.cu
 bool m2l_tensor_enabled(polfmm_ctx* c);
 
 template <typename R>
+static const R* weights(const double* wd, const float* wf);
+template <>
+const double* weights<double>(const double* wd, const float*) {
+    return wd;
+}
+template <>
+const float* weights<float>(const double*, const float* wf) {
+    return wf;
+}
+
+template <typename R>
 static void pass_impl(polfmm_ctx* c, int mode, bool use_q, const double* mu_sorted, double* phi, double* E,
-                      double* G) {
+                      double* G, bool mu_packed) {
     const int d = c->depth;
     const Tables& T = c->tab;
     Level& Lf = c->lv[d];
+    // solver passes: the near-field pair sums run on a second stream while the
+    // far-field chain (P2M .. L2L) runs here; the far field is added after the join
+    const bool overlap = mode == LEAF_DIPOLE_E && d >= 2 && c->side_stream && !c->opt.profile;
+    if (overlap) {
+        cudaEventRecord(c->ev_fork, c->stream);
+        cudaStreamWaitEvent(c->side_stream, c->ev_fork, 0);
+        launch_leaf<R>(c, mode, mu_sorted, phi, E, G, mu_packed, c->side_stream, 0);
+        cudaEventRecord(c->ev_join, c->side_stream);
+    }
     // P2M
     {
         LaunchScope ls(c, F_P2M);
@@ -640,7 +712,7 @@ static void pass_impl(polfmm_ctx* c, int mode, bool use_q, const double* mu_sort
             Level& C = c->lv[l + 1];
             m2m_kernel<R><<<P.nbox, 128, sizeof(R) * 8 * c->ld, c->stream>>>(
                 P.nbox, P.child0, P.nchild, C.key, (const R*)C.M, (R*)P.M, c->ld, c->ncoef, T.m2m_ptr, T.m2m_src,
-                T.m2m_par, T.m2m_w);
+                T.m2m_par, weights<R>(T.m2m_w, T.m2m_wf));
         }
         // M2L
         if (c->ntiles > 0) {
@@ -662,19 +734,31 @@ static void pass_impl(polfmm_ctx* c, int mode, bool use_q, const double* mu_sort
             const R* Lpar = l >= 3 ? (const R*)c->lv[l - 1].L : nullptr;
             l2l_kernel<R><<<B.nbox, 128, sizeof(R) * c->ld, c->stream>>>(
                 B.nbox, B.cap, c->m2l_chunks, B.key, B.parent, (const R*)B.Lp, Lpar, (R*)B.L, c->ld, c->ncoef,
-                T.l2l_ptr, T.l2l_src, T.l2l_par, T.l2l_w);
+                T.l2l_ptr, T.l2l_src, T.l2l_par, weights<R>(T.l2l_w, T.l2l_wf));
         }
     } else {
         cudaMemsetAsync(Lf.L, 0, sizeof(R) * (size_t)Lf.cap * c->ld, c->stream);
     }
-    launch_leaf<R>(c, mode, mu_sorted, phi, E, G);
+    if (overlap) {
+        cudaStreamWaitEvent(c->stream, c->ev_join, 0);
+        LaunchScope ls(c, F_LEAF_DIPOLE);
+        const R h = R(c->side / (double)(1 << d));
+        size_t smem = (2 * sizeof(R) + 4 * sizeof(int)) * (size_t)c->ncoef;
+        l2p_field_add_kernel<R><<<Lf.nbox, 128, smem, c->stream>>>(Lf.nbox, c->lstart, c->lcount,
+                                                                   reinterpret_cast<const Q4<R>*>(c->srcA),
+                                                                   (const R*)Lf.L, c->ld, c->ncoef, T.mi, T.inv_fact,
+                                                                   T.up1, h, E);
+        return;
+    }
+    launch_leaf<R>(c, mode, mu_sorted, phi, E, G, mu_packed, c->stream, 1);
 }
 
-void fmm_pass(polfmm_ctx* c, int mode, bool use_q, const double* mu_sorted, double* phi, double* E, double* G) {
+void fmm_pass(polfmm_ctx* c, int mode, bool use_q, const double* mu_sorted, double* phi, double* E, double* G,
+              bool mu_packed) {
     if (c->mixed)
-        pass_impl<float>(c, mode, use_q, mu_sorted, phi, E, G);
+        pass_impl<float>(c, mode, use_q, mu_sorted, phi, E, G, mu_packed);
     else
-        pass_impl<double>(c, mode, use_q, mu_sorted, phi, E, G);
+        pass_impl<double>(c, mode, use_q, mu_sorted, phi, E, G, mu_packed);
 }
 
 int fmm_ops_init_attributes(polfmm_ctx*) {

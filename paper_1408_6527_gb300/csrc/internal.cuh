@@ -49,10 +49,12 @@ struct Tables {
     int* m2m_src = nullptr;           // index of n - k
     int* m2m_par = nullptr;           // parity bits of k (kx&1 | (ky&1)<<1 | (kz&1)<<2)
     double* m2m_w = nullptr;          // 2^-(|n|+|k|) / k!
+    float* m2m_wf = nullptr;
     int* l2l_ptr = nullptr;
     int* l2l_src = nullptr;           // index of n + k
     int* l2l_par = nullptr;
     double* l2l_w = nullptr;          // 2^-(|n|+1+2|k|) / k!
+    float* l2l_wf = nullptr;
     double* D = nullptr;              // [343][ncoef] normalised derivatives of 1/r at integer offsets
     float* Df = nullptr;
     int* class_off = nullptr;         // [8][189] packed offsets (ox+3) | (oy+3)<<4 | (oz+3)<<8
@@ -147,6 +149,7 @@ struct polfmm_ctx {
     double* scal = nullptr;       // device scalars
     double* h_scal = nullptr;     // pinned host mirror
     int* err = nullptr;           // device error word
+    int* ticket = nullptr;        // last-block counter of the fused reductions (0 between kernels)
     // sort / scan scratch
     uint32_t* key_tmp = nullptr;
     int* val_tmp = nullptr;
@@ -163,6 +166,8 @@ struct polfmm_ctx {
     int64_t launches = 0;
     void* extra = nullptr;        // host-side bookkeeping of device allocations
     cudaStream_t cap_stream = nullptr;     // private stream for graph capture
+    cudaStream_t side_stream = nullptr;    // near-field pairs concurrent with the far-field chain
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     cudaGraphExec_t pcg_graph = nullptr;   // one PCG iteration of the current tree
     bool pcg_graph_dirty = true;
     int64_t pcg_graph_launches = 0;
@@ -198,7 +203,7 @@ int scan_exclusive(polfmm_ctx* c, const int* in, int* out, int n, int* total_dev
 
 // fmm_ops.cu
 void fmm_pass(polfmm_ctx* c, int mode, bool use_q, const double* mu_sorted, double* phi, double* E,
-              double* G);
+              double* G, bool mu_packed = false);
 int m2l_setup(polfmm_ctx* c);
 void pack_positions(polfmm_ctx* c);
 size_t source_record_bytes(bool mixed);

@@ -516,7 +516,9 @@ int m2l_tensor_prepare(polfmm_ctx* c) {
         if (sch.tmem_cols > 512) return POLFMM_OK;  // the SIMT kernel stays in use
         S->stage_bytes = sizeof(float) * (2 * (size_t)kTcRows * sch.KP + 2 * (size_t)sch.bpart);
         const size_t limit = 227 * 1024;
-        S->stages = 2 * S->stage_bytes + 1024 <= limit ? 2 : 1;
+        // one stage per CTA: two CTAs (or a CTA and near-field blocks) per SM hide
+        // the gather latency better than double buffering inside one CTA
+        S->stages = 1;
         S->smem = S->stages * S->stage_bytes + 1024;
         if (S->smem > limit) {
             delete S;
@@ -581,9 +583,7 @@ int m2l_tensor_prepare(polfmm_ctx* c) {
         }
         cudaError_t e1 = cudaFuncSetAttribute(m2l_tc_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                               (int)S->smem);
-        cudaError_t e2 = cudaFuncSetAttribute(m2l_tc_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              (int)S->smem);
-        if (e1 != cudaSuccess || e2 != cudaSuccess) {
+        if (e1 != cudaSuccess) {
             cudaGetLastError();
             return POLFMM_ERR_CUDA;
         }
@@ -669,14 +669,8 @@ void m2l_tensor_launch(polfmm_ctx* c) {
     LaunchScope ls(c, F_M2L);
     dim3 grid(S->ntiles, c->m2l_chunks);
     const int stage_floats = (int)(S->stage_bytes / sizeof(float));
-    if (S->stages == 2)
-        m2l_tc_kernel<2><<<grid, kTcThreads, S->smem, c->stream>>>(S->tiles, S->rows, lp, S->Bimg, c->tab.class_off,
-                                                                   sch, c->ncoef, c->ld, c->m2l_chunks,
-                                                                   stage_floats, c->err);
-    else
-        m2l_tc_kernel<1><<<grid, kTcThreads, S->smem, c->stream>>>(S->tiles, S->rows, lp, S->Bimg, c->tab.class_off,
-                                                                   sch, c->ncoef, c->ld, c->m2l_chunks,
-                                                                   stage_floats, c->err);
+    m2l_tc_kernel<1><<<grid, kTcThreads, S->smem, c->stream>>>(S->tiles, S->rows, lp, S->Bimg, c->tab.class_off, sch,
+                                                               c->ncoef, c->ld, c->m2l_chunks, stage_floats, c->err);
 }
 
 void m2l_tensor_release(polfmm_ctx* c) {

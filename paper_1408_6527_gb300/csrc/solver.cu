@@ -29,6 +29,34 @@ __device__ inline double block_sum(double v, double* sh) {
     return r;
 }
 
+// true in exactly one block: the last to finish.  Its caller then adds the
+// per-block partials in fixed order (deterministic) and re-arms the ticket.
+__device__ inline bool last_block(int* ticket) {
+    __shared__ bool last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(ticket, 1) == (int)gridDim.x - 1;
+    __syncthreads();
+    if (last) __threadfence();
+    return last;
+}
+
+__device__ inline double sum_partials(const double* __restrict__ partial, int row, double* sh) {
+    double v = 0.0;
+    for (int b = threadIdx.x; b < kRedBlocks; b += kRedThreads) v += *((volatile const double*)&partial[row * kRedBlocks + b]);
+    return block_sum(v, sh);
+}
+
+// packed (mu_x, mu_y, mu_z, 0) record of site i for the near-field kernels
+template <typename R>
+__device__ inline void store_packed(void* base, int64_t i, double x, double y, double z) {
+    R* p = reinterpret_cast<R*>(base) + 4 * i;
+    p[0] = R(x);
+    p[1] = R(y);
+    p[2] = R(z);
+    p[3] = R(0);
+}
+
 // single-block final reduction of nslot partial rows
 // post: 0 = store sums into scal[dst[k]]; 1 = PCG direction update
 // (scal[S_BETA] = sum0 / scal[S_RZ], scal[S_RZ] = sum0, scal[S_RR] = sum1)
@@ -103,9 +131,10 @@ __global__ void pcg_init_kernel(int64_t n, const double* __restrict__ alpha, con
     }
 }
 
-// Ad = d/alpha - T d; partial d.Ad
+// Ad = d/alpha - T d; d.Ad (partials, then the last block stores the sum)
 __global__ void pcg_ad_kernel(int64_t n, const double* __restrict__ alpha, const double* __restrict__ d,
-                              const double* __restrict__ Td, double* __restrict__ Ad, double* __restrict__ partial) {
+                              const double* __restrict__ Td, double* __restrict__ Ad, double* __restrict__ partial,
+                              double* __restrict__ scal, int* __restrict__ ticket) {
     __shared__ double sh[kRedThreads];
     double s = 0;
     RED_LOOP(i, 3 * n) {
@@ -116,12 +145,21 @@ __global__ void pcg_ad_kernel(int64_t n, const double* __restrict__ alpha, const
     }
     s = block_sum(s, sh);
     if (threadIdx.x == 0) partial[blockIdx.x] = s;
+    if (last_block(ticket)) {
+        double t = sum_partials(partial, 0, sh);
+        if (threadIdx.x == 0) {
+            scal[S_DAD] = t;
+            *ticket = 0;
+        }
+    }
 }
 
-// step = rz / dAd; mu += step d; r -= step Ad; z = alpha r; partials r.z, r.r
-__global__ void pcg_update_kernel(int64_t n, const double* __restrict__ alpha, const double* __restrict__ scal,
+// step = rz / dAd; mu += step d; r -= step Ad; z = alpha r; r.z and r.r; the
+// last block stores beta = (r.z)_new / (r.z)_old, (r.z)_new and r.r
+__global__ void pcg_update_kernel(int64_t n, const double* __restrict__ alpha, double* __restrict__ scal,
                                   const double* __restrict__ d, const double* __restrict__ Ad, double* __restrict__ mu,
-                                  double* __restrict__ r, double* __restrict__ z, double* __restrict__ partial) {
+                                  double* __restrict__ r, double* __restrict__ z, double* __restrict__ partial,
+                                  int* __restrict__ ticket) {
     __shared__ double sh[kRedThreads];
     const double step = scal[S_RZ] / scal[S_DAD];
     double rz = 0, rr = 0;
@@ -143,14 +181,39 @@ __global__ void pcg_update_kernel(int64_t n, const double* __restrict__ alpha, c
         partial[0 * kRedBlocks + blockIdx.x] = rz;
         partial[1 * kRedBlocks + blockIdx.x] = rr;
     }
+    if (last_block(ticket)) {
+        double rz_new = sum_partials(partial, 0, sh);
+        double rr_all = sum_partials(partial, 1, sh);
+        if (threadIdx.x == 0) {
+            scal[S_BETA] = rz_new / scal[S_RZ];
+            scal[S_RZ] = rz_new;
+            scal[S_RR] = rr_all;
+            *ticket = 0;
+        }
+    }
 }
 
-// d = z + beta d
+// d = z + beta d, and its packed copy for the next near-field pass
+template <typename R>
 __global__ void pcg_direction_kernel(int64_t n, const double* __restrict__ scal, const double* __restrict__ z,
-                                     double* __restrict__ d) {
+                                     double* __restrict__ d, void* __restrict__ packed) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= 3 * n) return;
-    d[i] = z[i] + scal[S_BETA] * d[i];
+    if (i >= n) return;
+    const double beta = scal[S_BETA];
+    double v[3];
+    for (int k = 0; k < 3; k++) {
+        v[k] = z[3 * i + k] + beta * d[3 * i + k];
+        d[3 * i + k] = v[k];
+    }
+    store_packed<R>(packed, i, v[0], v[1], v[2]);
+}
+
+// packed copy of d after the PCG start (d = z)
+template <typename R>
+__global__ void pack_vec_kernel(int64_t n, const double* __restrict__ v, void* __restrict__ packed) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    store_packed<R>(packed, i, v[3 * i], v[3 * i + 1], v[3 * i + 2]);
 }
 
 // Jacobi fixed point: r = E^q + T mu - mu/alpha (residual at the current mu),
@@ -291,24 +354,35 @@ void solver_init(polfmm_ctx* c, bool warm) {
                                                                     c->z, c->d, c->partial);
     }
     reduce(c, 3, S_RZ, S_RR, S_BB, 0, 0, F_SOLVER);
+    LaunchScope ls(c, F_SOLVER);
+    if (c->mixed)
+        pack_vec_kernel<float><<<grid_for(c->n, 256), 256, 0, c->stream>>>(c->n, c->d, c->srcB);
+    else
+        pack_vec_kernel<double><<<grid_for(c->n, 256), 256, 0, c->stream>>>(c->n, c->d, c->srcB);
 }
 
+// one PCG iteration: T d by the FMM (d already packed for the near field),
+// then three fused vector kernels
 void solver_pcg_step(polfmm_ctx* c) {
-    fmm_pass(c, LEAF_DIPOLE_E, false, c->d, nullptr, c->Td, nullptr);
+    fmm_pass(c, LEAF_DIPOLE_E, false, c->d, nullptr, c->Td, nullptr, true);
     {
         LaunchScope ls(c, F_SOLVER);
-        pcg_ad_kernel<<<kRedBlocks, kRedThreads, 0, c->stream>>>(c->n, c->alpha_s, c->d, c->Td, c->Ad, c->partial);
+        pcg_ad_kernel<<<kRedBlocks, kRedThreads, 0, c->stream>>>(c->n, c->alpha_s, c->d, c->Td, c->Ad, c->partial,
+                                                                  c->scal, c->ticket);
     }
-    reduce(c, 1, S_DAD, 0, 0, 0, 0, F_SOLVER);
     {
         LaunchScope ls(c, F_SOLVER);
         pcg_update_kernel<<<kRedBlocks, kRedThreads, 0, c->stream>>>(c->n, c->alpha_s, c->scal, c->d, c->Ad, c->mu,
-                                                                      c->r, c->z, c->partial);
+                                                                      c->r, c->z, c->partial, c->ticket);
     }
-    reduce(c, 2, 0, 0, 0, 0, 1, F_SOLVER);
     {
         LaunchScope ls(c, F_SOLVER);
-        pcg_direction_kernel<<<grid_for(3 * c->n, 256), 256, 0, c->stream>>>(c->n, c->scal, c->z, c->d);
+        if (c->mixed)
+            pcg_direction_kernel<float><<<grid_for(c->n, 256), 256, 0, c->stream>>>(c->n, c->scal, c->z, c->d,
+                                                                                    c->srcB);
+        else
+            pcg_direction_kernel<double><<<grid_for(c->n, 256), 256, 0, c->stream>>>(c->n, c->scal, c->z, c->d,
+                                                                                     c->srcB);
     }
 }
 
