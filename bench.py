@@ -39,6 +39,9 @@ METRIC = "atoms/s polarizable FMM energy+forces, mixed vs FP64, at ≤1e-5 RMS f
 WORKLOAD_INDEX = 2
 TOL = {"mixed": 1e-6, "fp64": 1e-8}
 FP32_LANES_PER_SM = 128
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
+# current kernels from one ncu capture (profiles/); None where not captured
+TRAFFIC = {("m2l", "mixed"): 7629824, ("leaf_dipole", "mixed"): 1021696}
 NUM_SMS = 152
 SM_MAX_MHZ = 2070.0
 
@@ -46,12 +49,15 @@ SM_MAX_MHZ = 2070.0
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--mode", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
     ap.add_argument("--m2l", default="auto", choices=["auto", "simt", "tensor"])
+    ap.add_argument("--workload", default="globule30k",
+                    choices=["globule30k", "cube1k", "ring300k", "globule100k", "shell250k", "shell1M", "shell4M"],
+                    help="workload (the default is the one the headline metric is quoted on)")
     ap.add_argument("--only-main", action="store_true",
                     help="time the headline mode only (no FP64 leg, profiling, e2e or CPU leg): for ncu captures")
     return ap.parse_args()
@@ -70,6 +76,26 @@ def m2l_flops_per_box_pair(p):
     return 2 * sum((s + 1) * (s + 2) // 2 * ncoef(p - s) for s in range(p + 1))
 
 
+def tc_issued_macs_per_row(p):
+    """MACs per tile row and offset issued by the tensor-core M2L: output bands
+    of 16 columns, each over the input prefix its lowest degree needs."""
+    nc = ncoef(p)
+    deg = [next(s for s in range(p + 1) if i < ncoef(s)) for i in range(nc)]
+    NP = (nc + 15) // 16 * 16
+    need = [max((ncoef(p - deg[n]) for n in range(b * 16, min(b * 16 + 16, nc))), default=0)
+            for b in range(NP // 16)]
+    return sum(16 * ((k + 7) // 8) * 8 for k in need)
+
+
+def load_peaks():
+    try:
+        j = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        return float(j["hbm_gbs"]), float(j["bf16_tflops"]), float(j.get("bf16_tflops_sustained", j["bf16_tflops"])), \
+            "measured"
+    except (OSError, ValueError, KeyError):
+        return 6800.0, 1900.0, 1700.0, "fallback"
+
+
 def tree_work(pos, depth, lo, side):
     """Near-field pairs (ordered, i != j, adjacent leaves) and far-field box
     pairs (the 189-offset interaction lists, occupied sources only)."""
@@ -86,12 +112,14 @@ def tree_work(pos, depth, lo, side):
                 nb += pad[1 + dx:1 + dx + ns, 1 + dy:1 + dy + ns, 1 + dz:1 + dz + ns]
     near_pairs = int(np.sum(cnt * nb) - pos.shape[0])
     box_pairs = 0
+    class_rows = np.zeros(8, dtype=np.int64)
     for l in range(2, depth + 1):
         m = 1 << l
         occ = np.zeros((m, m, m), dtype=bool)
         c = cell >> (depth - l)
         occ[c[:, 0], c[:, 1], c[:, 2]] = True
         tx, ty, tz = np.nonzero(occ)
+        class_rows += np.bincount((tx & 1) + 2 * (ty & 1) + 4 * (tz & 1), minlength=8)
         for ox in range(-3, 4):
             for oy in range(-3, 4):
                 for oz in range(-3, 4):
@@ -105,7 +133,8 @@ def tree_work(pos, depth, lo, side):
                     ok &= (sx >= 0) & (sy >= 0) & (sz >= 0) & (sx < m) & (sy < m) & (sz < m)
                     ok[ok] &= occ[sx[ok], sy[ok], sz[ok]]
                     box_pairs += int(ok.sum())
-    return near_pairs, box_pairs
+    tc_tiles = int(sum((r + 127) // 128 for r in class_rows))
+    return near_pairs, box_pairs, tc_tiles
 
 
 # ---------------------------------------------------------------------------
@@ -123,7 +152,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
         except (OSError, FileNotFoundError):
@@ -185,6 +214,17 @@ def main():
         tdist.destroy_process_group()
 
 
+WORKLOADS = {"globule30k": (2, None), "cube1k": (1, None), "ring300k": (3, None), "globule100k": (4, None),
+             "shell250k": (5, 250000), "shell1M": (5, 1000000), "shell4M": (5, 4000000)}
+
+
+def make_workload(name):
+    import synth
+
+    idx, n = WORKLOADS[name]
+    return synth.workload(idx, n=n)
+
+
 def run_gpu(args, rank, world, local_rank):
     import torch
 
@@ -195,7 +235,7 @@ def run_gpu(args, rank, world, local_rank):
     dist = world > 1
     if dist:
         import torch.distributed as tdist
-    w = synth.workload(WORKLOAD_INDEX)
+    w = make_workload(args.workload)
     n = w.n
     dev = lambda a: torch.as_tensor(a, dtype=torch.float64, device="cuda")
     pos_d, q_d, a_d = dev(w.pos), dev(w.q), dev(w.alpha)
@@ -282,28 +322,41 @@ def run_gpu(args, rank, world, local_rank):
     ctxp.close()
     prof_total = sum(v[0] for v in prof.values())
 
-    # roofline of the dominant kernel family (FP32 ALU in MIXED mode)
-    near_pairs, box_pairs = tree_work(w.pos, w.depth, lo, side)
-    dom = max(prof, key=lambda f: prof[f][0])
+    # roofline of the dominant kernel families: the near-field pass (FP32 ALU in
+    # MIXED, FP64 ALU in FP64) and the multipole-to-local pass (TF32 tensor
+    # cores in MIXED; FP64 ALU otherwise), each against its own peak
+    near_pairs, box_pairs, tc_tiles = tree_work(w.pos, w.depth, lo, side)
+    hbm_peak, bf16_burst, bf16_sust, peak_src = load_peaks()
     p = w.p
-    flops = {
-        # dipole -> field pair: 34 flops (FMA = 2, rsqrt = 1); L2P field: 6 per coefficient of order <= p-1
-        "leaf_dipole": near_pairs * 34 + n * 6 * ncoef(p - 1),
-        "m2l": box_pairs * m2l_flops_per_box_pair(p),
+    mixed = args.mode == "mixed"
+    fp32_peak = NUM_SMS * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    tf32_peak = bf16_sust * 1.1 / 2.25
+    fams = {
+        "leaf_dipole": dict(flops=near_pairs * 34 + n * 6 * ncoef(p - 1), bound="alu",
+                            peak=fp32_peak if mixed else 1.25,
+                            peak_note="FP32 FMA nominal: 152 SMs x 128 lanes x 2 x 2070 MHz" if mixed
+                            else "FP64 nominal 1.25 TFLOP/s"),
+        "m2l": dict(flops=box_pairs * m2l_flops_per_box_pair(p), bound="tensor" if mixed else "alu",
+                    peak=tf32_peak if mixed else 1.25,
+                    peak_note=(f"TF32 dense = {peak_src} sustained bf16 {bf16_sust} x nominal TF32/BF16 1.1/2.25")
+                    if mixed else "FP64 nominal 1.25 TFLOP/s"),
     }
-    roof = None
-    if dom in flops and prof[dom][1] > 0:
-        dur_s = prof[dom][0] / prof[dom][1] / 1e3
-        achieved = flops[dom] / dur_s / 1e12
-        sm_mhz = SM_MAX_MHZ
-        peak = NUM_SMS * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12 if args.mode == "mixed" else None
-        if args.mode == "fp64":
-            peak = 1.25  # nominal FP64 TFLOP/s of GB300 (no measured FP64 peak on this machine)
-        roof = {"kernel": dom, "bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 2),
-                "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": None,
-                "peak_note": "FP32 FMA: 152 SMs x 128 lanes x 2 flops x 2070 MHz (nominal)" if args.mode == "mixed"
-                else "FP64 nominal", "avg_launch_ms": round(prof[dom][0] / prof[dom][1], 4),
-                "algorithmic_flops_per_launch": int(flops[dom])}
+    roofs = {}
+    for fam, info in fams.items():
+        if prof[fam][1] == 0:
+            continue
+        dur_s = prof[fam][0] / prof[fam][1] / 1e3
+        achieved = info["flops"] / dur_s / 1e12
+        r = {"kernel": fam, "bound": info["bound"], "achieved": round(achieved, 3), "peak": round(info["peak"], 2),
+             "unit": "TFLOP/s", "frac": round(achieved / info["peak"], 5), "traffic": TRAFFIC.get((fam, args.mode)),
+             "peak_note": info["peak_note"], "avg_launch_ms": round(prof[fam][0] / prof[fam][1], 4),
+             "algorithmic_flops_per_launch": int(info["flops"]), "share_of_step": round(prof[fam][0] / prof_total, 4)}
+        if fam == "m2l" and mixed:
+            issued = 3 * 2 * 128 * tc_issued_macs_per_row(p) * tc_tiles * 189
+            r["issued_tensor_tflops"] = round(issued / dur_s / 1e12, 3)
+        roofs[fam] = r
+    dom = max(roofs, key=lambda f: prof[f][0]) if roofs else None
+    roof = roofs.get(dom)
 
     # e2e: the same step through the public API with pinned host buffers
     pos_h = torch.from_numpy(w.pos.copy()).pin_memory()
@@ -325,7 +378,7 @@ def run_gpu(args, rank, world, local_rank):
         "metric": METRIC, "value": round(value, 1), "unit": "atoms/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64" if args.mode == "mixed" else "f64", "data": "synthetic",
-        "config": {"workload": f"globule {n} sites p={w.p} depth={w.depth} {args.mode}", "n_sites": n, "p": w.p,
+        "config": {"workload": f"{w.name} {n} sites p={w.p} depth={w.depth} {args.mode}", "n_sites": n, "p": w.p,
                    "depth": w.depth, "mode": args.mode, "tol": TOL[args.mode], "m2l": args.m2l,
                    "parallelism": "replicas" if world > 1 else "single",
                    "l2": "flushed before every step (256 MB write, outside the step interval)"},
@@ -335,8 +388,8 @@ def run_gpu(args, rank, world, local_rank):
         "gpu_launches": int(launches),
         "kernel_ms_per_step": {f: round(v[0] / 3, 4) for f, v in prof.items()},
         "kernel_share": {f: round(v[0] / prof_total, 4) for f, v in prof.items()} if prof_total > 0 else None,
-        "roofline": roof, "clocks": clocks, "e2e": e2e,
-        "tree": {"near_pairs": near_pairs, "m2l_box_pairs": box_pairs},
+        "roofline": roof, "roofline_kernels": roofs, "clocks": clocks, "e2e": e2e,
+        "tree": {"near_pairs": near_pairs, "m2l_box_pairs": box_pairs, "tc_tiles": tc_tiles},
     }
     if world == 1 and not args.no_cpu:
         result["cpu_baseline"] = cpu_baseline(w, lo, side)
@@ -363,7 +416,7 @@ def run_reference(args):
     import synth
     import oracle
 
-    w = synth.workload(WORKLOAD_INDEX)
+    w = make_workload(args.workload)
     lo, side = oracle.root_box(w.pos)
     for _ in range(args.warmup):
         cpu_baseline(w, lo, side, TOL[args.mode])
@@ -379,7 +432,7 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": round(value, 2), "unit": "atoms/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * total / args.steps, 2),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"globule {w.n} sites p={w.p} depth={w.depth} {args.mode}", "n_sites": w.n,
+        "config": {"workload": f"{w.name} {w.n} sites p={w.p} depth={w.depth} {args.mode}", "n_sites": w.n,
                    "p": w.p, "depth": w.depth, "mode": args.mode, "tol": TOL[args.mode]},
         "cpu_baseline": {"value": round(value, 2), "unit": "atoms/s", "cores": cores, "kind": "oracle",
                          "sample": "each step one complete oracle step of the full workload"},
