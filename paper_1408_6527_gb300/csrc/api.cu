@@ -136,7 +136,7 @@ int build_tables(polfmm_ctx* c) {
     T.ncoef = t.nc;
     T.ld = c->ld;
     const int nc = t.nc;
-    std::vector<int> mi(nc), pre(nc), up1(3 * nc), up2(6 * nc);
+    std::vector<int> mi(nc), pre(nc), up1(3 * nc), dn1(3 * nc), up2(6 * nc);
     std::vector<double> inv_fact(nc);
     std::vector<float> inv_fact_f(nc);
     std::vector<short> add((size_t)nc * nc, (short)-1);
@@ -150,6 +150,8 @@ int build_tables(polfmm_ctx* c) {
             int m[3] = {t.nx[k], t.ny[k], t.nz[k]};
             m[d]++;
             up1[3 * k + d] = t.at(m[0], m[1], m[2]);
+            m[d] -= 2;
+            dn1[3 * k + d] = m[d] >= 0 ? t.at(m[0], m[1], m[2]) : -1;
         }
         for (int e = 0; e < 6; e++) {
             int m[3] = {t.nx[k], t.ny[k], t.nz[k]};
@@ -158,28 +160,6 @@ int build_tables(polfmm_ctx* c) {
             up2[6 * k + e] = t.at(m[0], m[1], m[2]);
         }
         for (int j = 0; j < pre[k]; j++) add[(size_t)k * nc + j] = (short)t.at(t.nx[k] + t.nx[j], t.ny[k] + t.ny[j], t.nz[k] + t.nz[j]);
-    }
-    // shift operators
-    std::vector<int> m2m_ptr(nc + 1, 0), m2m_src, m2m_par, l2l_ptr(nc + 1, 0), l2l_src, l2l_par;
-    std::vector<double> m2m_w, l2l_w;
-    for (int k = 0; k < nc; k++) {
-        for (int kx = 0; kx <= t.nx[k]; kx++)
-            for (int ky = 0; ky <= t.ny[k]; ky++)
-                for (int kz = 0; kz <= t.nz[k]; kz++) {
-                    m2m_src.push_back(t.at(t.nx[k] - kx, t.ny[k] - ky, t.nz[k] - kz));
-                    m2m_par.push_back((kx & 1) | ((ky & 1) << 1) | ((kz & 1) << 2));
-                    int ks = kx + ky + kz;
-                    m2m_w.push_back(ldexp(1.0, -(t.s[k] + ks)) / (factorial(kx) * factorial(ky) * factorial(kz)));
-                }
-        m2m_ptr[k + 1] = (int)m2m_src.size();
-        for (int j = 0; j < nc; j++) {
-            if (t.s[j] > p - t.s[k]) continue;
-            l2l_src.push_back(t.at(t.nx[k] + t.nx[j], t.ny[k] + t.ny[j], t.nz[k] + t.nz[j]));
-            l2l_par.push_back((t.nx[j] & 1) | ((t.ny[j] & 1) << 1) | ((t.nz[j] & 1) << 2));
-            l2l_w.push_back(ldexp(1.0, -(t.s[k] + 1 + 2 * t.s[j])) /
-                            (factorial(t.nx[j]) * factorial(t.ny[j]) * factorial(t.nz[j])));
-        }
-        l2l_ptr[k + 1] = (int)l2l_src.size();
     }
     // derivative tables at the integer offsets of [-3, 3]^3
     std::vector<double> D((size_t)343 * nc, 0.0);
@@ -233,17 +213,7 @@ int build_tables(polfmm_ctx* c) {
     UP(up2, T.up2);
     UP(pre, T.pre);
     UP(add, T.add);
-    UP(m2m_ptr, T.m2m_ptr);
-    UP(m2m_src, T.m2m_src);
-    UP(m2m_par, T.m2m_par);
-    UP(m2m_w, T.m2m_w);
-    std::vector<float> m2m_wf(m2m_w.begin(), m2m_w.end()), l2l_wf(l2l_w.begin(), l2l_w.end());
-    UP(m2m_wf, T.m2m_wf);
-    UP(l2l_wf, T.l2l_wf);
-    UP(l2l_ptr, T.l2l_ptr);
-    UP(l2l_src, T.l2l_src);
-    UP(l2l_par, T.l2l_par);
-    UP(l2l_w, T.l2l_w);
+    UP(dn1, T.dn1);
     UP(D, T.D);
     UP(Df, T.Df);
     UP(class_off, T.class_off);
@@ -255,9 +225,8 @@ int build_tables(polfmm_ctx* c) {
 }
 
 void free_tables(Tables& T) {
-    void* ptrs[] = {T.mi, T.inv_fact, T.inv_fact_f, T.up1, T.up2, T.pre, T.add, T.m2m_ptr, T.m2m_src, T.m2m_par,
-                    T.m2m_w, T.m2m_wf, T.l2l_wf, T.l2l_ptr, T.l2l_src, T.l2l_par, T.l2l_w, T.D, T.Df, T.class_off, T.warp_out_ptr,
-                    T.warp_out};
+    void* ptrs[] = {T.mi, T.inv_fact, T.inv_fact_f, T.up1, T.dn1, T.up2, T.pre, T.add, T.D, T.Df, T.class_off,
+                    T.warp_out_ptr, T.warp_out};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     T = Tables();
@@ -342,9 +311,10 @@ int allocate(polfmm_ctx* c) {
         B.nchild = A.get<int>(B.cap);
         B.by_class = A.get<int>(B.cap);
         B.M = A.get<unsigned char>((size_t)B.cap * c->ld * rsz);
-        B.L = A.get<unsigned char>((size_t)B.cap * c->ld * rsz);
+        B.arrive = A.get<int>(B.cap);
     }
     c->lstart = A.get<int>(c->lv[c->depth].cap);
+    c->leaf_partial = A.get<double>(c->lv[c->depth].cap);
     c->lcount = A.get<int>(c->lv[c->depth].cap);
     c->leaf_order = A.get<int>(c->lv[c->depth].cap);
     if (!A.ok) return POLFMM_ERR_OUT_OF_MEMORY;
@@ -354,6 +324,7 @@ int allocate(polfmm_ctx* c) {
     cudaMemsetAsync(c->err, 0, sizeof(int) * 4, c->stream);
     cudaMemsetAsync(c->ticket, 0, sizeof(int) * 4, c->stream);
     cudaMemsetAsync(c->scal, 0, sizeof(double) * (S_COUNT + 8), c->stream);
+    for (int l = 0; l <= c->depth; l++) cudaMemsetAsync(c->lv[l].arrive, 0, sizeof(int) * c->lv[l].cap, c->stream);
     return POLFMM_OK;
 }
 
@@ -456,6 +427,7 @@ int rebuild(polfmm_ctx* c) {
     pack_positions(c);
     fmm_pass(c, LEAF_CHARGE_PHI_E, true, nullptr, c->phiq, c->Eq, nullptr);
     c->pcg_graph_dirty = true;  // launch sizes of the solver iteration changed
+    c->loop_dirty = true;
     return read_err(c);
 }
 
@@ -500,6 +472,74 @@ int capture_pcg_graph(polfmm_ctx* c) {
     return POLFMM_OK;
 }
 
+// The solve loop as one graph: a while node whose body is one PCG iteration.
+// Graph and condition handle live as long as the context; after a new tree the
+// body is emptied, captured again and the executable graph updated.  The body
+// clears the condition in its first solver kernel and only the update kernel
+// sets it again, so a body that fails to finish ends the loop.
+int prepare_loop_graph(polfmm_ctx* c) {
+    auto fail = [&](void) {
+        cudaGetLastError();
+        if (c->loop_exec) cudaGraphExecDestroy(c->loop_exec);
+        if (c->loop_g) cudaGraphDestroy(c->loop_g);
+        c->loop_exec = nullptr;
+        c->loop_g = nullptr;
+        c->loop_body = nullptr;
+        c->loop_cond = 0;
+        c->loop_failed = true;
+        return POLFMM_ERR_CUDA;
+    };
+    if (!c->cap_stream && cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+        return fail();
+    if (!c->loop_g) {
+        if (cudaGraphCreate(&c->loop_g, 0) != cudaSuccess) return fail();
+        if (cudaGraphConditionalHandleCreate(&c->loop_cond, c->loop_g, 1, cudaGraphCondAssignDefault) != cudaSuccess)
+            return fail();
+        cudaGraphNodeParams np = {};
+        np.type = cudaGraphNodeTypeConditional;
+        np.conditional.handle = c->loop_cond;
+        np.conditional.type = cudaGraphCondTypeWhile;
+        np.conditional.size = 1;
+        cudaGraphNode_t node;
+        if (cudaGraphAddNode(&node, c->loop_g, nullptr, nullptr, 0, &np) != cudaSuccess) return fail();
+        c->loop_body = np.conditional.phGraph_out[0];
+    } else {
+        size_t nn = 0;
+        if (cudaGraphGetNodes(c->loop_body, nullptr, &nn) != cudaSuccess) return fail();
+        std::vector<cudaGraphNode_t> nodes(nn);
+        if (nn && cudaGraphGetNodes(c->loop_body, nodes.data(), &nn) != cudaSuccess) return fail();
+        for (cudaGraphNode_t nd : nodes)
+            if (cudaGraphDestroyNode(nd) != cudaSuccess) return fail();
+    }
+    cudaStream_t orig = c->stream;
+    const int64_t l0 = c->launches;
+    c->stream = c->cap_stream;
+    c->capturing_loop = true;
+    cudaError_t e = cudaStreamBeginCaptureToGraph(c->cap_stream, c->loop_body, nullptr, nullptr, 0,
+                                                  cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        solver_pcg_step(c);
+        cudaGraph_t out = nullptr;
+        e = cudaStreamEndCapture(c->cap_stream, &out);
+    }
+    c->capturing_loop = false;
+    c->stream = orig;
+    c->loop_launches = c->launches - l0;
+    c->launches = l0;
+    if (e != cudaSuccess) return fail();
+    if (c->loop_exec) {
+        cudaGraphExecUpdateResultInfo info;
+        if (cudaGraphExecUpdate(c->loop_exec, c->loop_g, &info) != cudaSuccess) {
+            cudaGetLastError();
+            cudaGraphExecDestroy(c->loop_exec);
+            c->loop_exec = nullptr;
+        }
+    }
+    if (!c->loop_exec && cudaGraphInstantiate(&c->loop_exec, c->loop_g, 0) != cudaSuccess) return fail();
+    c->loop_dirty = false;
+    return POLFMM_OK;
+}
+
 int pcg_iteration(polfmm_ctx* c) {
     if (c->opt.no_graphs || c->opt.profile) {
         solver_pcg_step(c);
@@ -531,6 +571,8 @@ void destroy_impl(polfmm_ctx* c) {
     if (c->ev_created)
         for (int i = 0; i < 2 * 4096; i++) cudaEventDestroy(c->ev_pool[i]);
     if (c->pcg_graph) cudaGraphExecDestroy(c->pcg_graph);
+    if (c->loop_exec) cudaGraphExecDestroy(c->loop_exec);
+    if (c->loop_g) cudaGraphDestroy(c->loop_g);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     if (c->side_stream) cudaStreamDestroy(c->side_stream);
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
@@ -658,7 +700,24 @@ int fmm_solve_induced_dipoles(polfmm_ctx* c, double tol, int* iters_out, double*
         if (res_out) *res_out = 0.0;
         return read_err(c);
     }
-    if (!jacobi) {
+    const bool use_loop = !jacobi && !c->opt.no_graphs && !c->opt.profile && !c->loop_failed;
+    if (use_loop && (res = sqrt(c->h_scal[S_RR] / bb)) > tol && c->opt.max_iter > 0 &&
+        ((!c->loop_dirty && c->loop_exec) || prepare_loop_graph(c) == POLFMM_OK)) {
+        // all iterations in one graph launch; the device decides when to stop
+        solver_loop_setup(c, tol, c->opt.max_iter);
+        cudaError_t e = cudaGraphLaunch(c->loop_exec, c->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "solve graph launch");
+        if ((rc = fetch()) != POLFMM_OK) return rc;
+        it = (int)c->h_scal[S_ITER];
+        c->launches += c->loop_launches * it;
+        if (!(c->h_scal[S_DAD] > 0.0)) {  // operator not positive definite (polarization catastrophe)
+            res = sqrt(fabs(c->h_scal[S_RR] / bb));
+            status = POLFMM_ERR_NOT_CONVERGED;
+        } else {
+            res = sqrt(c->h_scal[S_RR] / bb);
+            if (!isfinite(res)) status = POLFMM_ERR_NOT_CONVERGED;
+        }
+    } else if (!jacobi) {
         res = sqrt(c->h_scal[S_RR] / bb);
         while (res > tol && it < c->opt.max_iter) {
             if ((rc = pcg_iteration(c)) != POLFMM_OK) return rc;

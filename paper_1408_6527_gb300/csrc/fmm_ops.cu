@@ -28,56 +28,151 @@ __device__ inline void decode_mi(int packed, int& nx, int& ny, int& nz) {
 }
 
 // ---------------------------------------------------------------------------
-// P2M
+// shared helpers of the upward and downward passes
+// ---------------------------------------------------------------------------
+// 2^-s for 0 <= s <= 2 kMaxP + 2, exact
+template <typename R>
+__device__ inline R pow2neg(int s);
+template <>
+__device__ inline float pow2neg<float>(int s) {
+    return __int_as_float((127 - s) << 23);
+}
+template <>
+__device__ inline double pow2neg<double>(int s) {
+    return __longlong_as_double((long long)(1023 - s) << 52);
+}
+
+// W[k] = 4^-k / k!, the 1-D weights of a shift by a quarter of the parent side
+template <typename R>
+__device__ inline void shift_weights(R* W, int p) {
+    if ((int)threadIdx.x <= p) {
+        double w = 1.0;
+        for (int k = 1; k <= (int)threadIdx.x; k++) w *= 0.25 / k;
+        W[threadIdx.x] = R(w);
+    }
+}
+
+// TF32 high part (round to nearest, ties away) and residual of v
+__device__ inline void tf32_split(float v, float& hi, float& lo) {
+    uint32_t h;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(v));
+    hi = __uint_as_float(h);
+    lo = v - hi;
+}
+__device__ inline void tf32_split(double, float& hi, float& lo) { hi = lo = 0.f; }
+
+// ---------------------------------------------------------------------------
+// upward pass: P2M of every leaf, then M2M up to level 2 inside the same
+// launch.  The block that completes the last child of a parent (counted with
+// one atomic per parent) forms that parent; the parent's sum runs over its
+// children in Morton order whichever block does it, so the result does not
+// depend on the schedule.
+//
+// P2M (Eq. multipole, normalised): m_n = sum_i q_i v_i^n/n! - sum_d
+// (mu_i,d/h) v_i^(n-e_d)/(n-e_d)!, v_i = -(x_i - z)/h; a point dipole is the
+// dl -> 0 limit of the +-q pair of Sec. II.C.
+// M2M (Sec. II.B, shift of a multipole expansion): with child centre
+// z_C = z_P + (b - 1/2) h_P / 2 per axis,
+//   m^P_n = sum_{k <= n} prod_d (s_d/4)^k_d / k_d!  2^-|n-k| m^C_{n-k},
+// s_d = -1 where the child bit b_d is 1.  The kernel applies it as three
+// one-axis convolutions (exact: the truncation k <= n is a box).
+// With `hi` set (tensor-core M2L), every multipole row of levels >= 2 is also
+// stored as a TF32 high part plus residual.
 // ---------------------------------------------------------------------------
 constexpr int kP2MChunk = 64;
-constexpr int kP2MThreads = 128;
+constexpr int kUpThreads = 128;
+
+struct UpPtrs {
+    void* M[kMaxDepth + 1];
+    const int* parent[kMaxDepth + 1];
+    const int* child0[kMaxDepth + 1];
+    const int* nchild[kMaxDepth + 1];
+    const int* key[kMaxDepth + 1];
+    int* arrive[kMaxDepth + 1];
+    float* hi[kMaxDepth + 1];
+    float* lo[kMaxDepth + 1];
+    int KP;
+};
 
 template <typename R>
-__global__ void __launch_bounds__(kP2MThreads) p2m_kernel(
-    int nleaf, const int* __restrict__ lstart, const int* __restrict__ lcount, const R* __restrict__ ploc,
-    const double* __restrict__ q, const double* __restrict__ mu, R* __restrict__ M, int ld, int ncoef, int p,
-    const int* __restrict__ mi, R inv_h) {
-    const int b = blockIdx.x;
-    if (b >= nleaf) return;
-    const int s0 = lstart[b], cnt = lcount[b];
+__host__ __device__ inline size_t upward_smem_bytes(int ncoef) {
+    return sizeof(R) * 16 * (size_t)ncoef + sizeof(int) * 4 * (size_t)ncoef;
+}
+
+template <typename R>
+__device__ inline void store_multipole(const UpPtrs& up, int l, int box, int cc, R v, int ld) {
+    reinterpret_cast<R*>(up.M[l])[(int64_t)box * ld + cc] = v;
+    if (up.hi[l]) {
+        float h, lo;
+        tf32_split(v, h, lo);
+        up.hi[l][(int64_t)box * up.KP + cc] = h;
+        up.lo[l][(int64_t)box * up.KP + cc] = lo;
+    }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kUpThreads) upward_kernel(
+    int nleaf, int depth, const int* __restrict__ lstart, const int* __restrict__ lcount,
+    const R* __restrict__ ploc, const double* __restrict__ q, const double* __restrict__ mu, UpPtrs up, int ld,
+    int ncoef, int p, const int* __restrict__ mi, const int* __restrict__ dn1, R inv_h) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    R* S = reinterpret_cast<R*>(smem_raw);         // [8][ncoef] children, then ping-pong
+    R* T = S + 8 * ncoef;                           // [8][ncoef]
+    int* sdn = reinterpret_cast<int*>(T + 8 * ncoef);  // [ncoef][3] index of n - e_d
+    int* sdeg = sdn + 3 * ncoef;                    // [ncoef] |n|
     // P[site][axis][k + 1] = v^k / k!, v = -(x - z) / h, P[.][.][0] = 0
     __shared__ R P[kP2MChunk][3][kMaxP + 2];
     __shared__ R sq[kP2MChunk];
     __shared__ R sm[kP2MChunk][3];
-    constexpr int CPT = (286 + kP2MThreads - 1) / kP2MThreads;  // coefficients per thread (p <= 10)
+    __shared__ R W[kMaxP + 1];
+    __shared__ int s_oct[8];
+    __shared__ int s_next;
+    const int b = blockIdx.x;
+    if (b >= nleaf) return;
+    const int tid = threadIdx.x;
+    for (int cc = tid; cc < ncoef; cc += kUpThreads) {
+        sdn[3 * cc] = dn1[3 * cc];
+        sdn[3 * cc + 1] = dn1[3 * cc + 1];
+        sdn[3 * cc + 2] = dn1[3 * cc + 2];
+        sdeg[cc] = mi[cc] >> 24;
+    }
+    shift_weights(W, p);
+
+    // P2M of leaf b
+    const int s0 = lstart[b], cnt = lcount[b];
+    constexpr int CPT = (286 + kUpThreads - 1) / kUpThreads;  // coefficients per thread (p <= 10)
     R acc[CPT];
 #pragma unroll
     for (int k = 0; k < CPT; k++) acc[k] = R(0);
+    int pk[CPT];
+#pragma unroll
+    for (int k = 0; k < CPT; k++) pk[k] = tid + k * kUpThreads < ncoef ? mi[tid + k * kUpThreads] : 0;
     for (int k0 = 0; k0 < cnt; k0 += kP2MChunk) {
-        int m = min(kP2MChunk, cnt - k0);
+        const int m = min(kP2MChunk, cnt - k0);
         __syncthreads();
-        if (threadIdx.x < m) {
-            int i = s0 + k0 + threadIdx.x;
+        if (tid < m) {
+            const int i = s0 + k0 + tid;
             for (int a = 0; a < 3; a++) {
-                R v = -ploc[3 * i + a] * inv_h;
+                const R v = -ploc[3 * i + a] * inv_h;
                 R t = R(1);
-                P[threadIdx.x][a][0] = R(0);
-                P[threadIdx.x][a][1] = t;
+                P[tid][a][0] = R(0);
+                P[tid][a][1] = t;
                 for (int k = 1; k <= p; k++) {
                     t = t * v / R(k);
-                    P[threadIdx.x][a][k + 1] = t;
+                    P[tid][a][k + 1] = t;
                 }
-                sm[threadIdx.x][a] = mu ? R(mu[3 * i + a]) * inv_h : R(0);
+                sm[tid][a] = mu ? R(mu[3 * i + a]) * inv_h : R(0);
             }
-            sq[threadIdx.x] = q ? R(q[i]) : R(0);
+            sq[tid] = q ? R(q[i]) : R(0);
         }
         __syncthreads();
 #pragma unroll
         for (int k = 0; k < CPT; k++) {
-            int cidx = threadIdx.x + k * kP2MThreads;
-            if (cidx >= ncoef) continue;
-            int nx, ny, nz;
-            decode_mi(mi[cidx], nx, ny, nz);
+            if (tid + k * kUpThreads >= ncoef) continue;
+            const int nx = pk[k] & 0xff, ny = (pk[k] >> 8) & 0xff, nz = (pk[k] >> 16) & 0xff;
             R a = acc[k];
             for (int s = 0; s < m; s++) {
-                R px = P[s][0][nx + 1], py = P[s][1][ny + 1], pz = P[s][2][nz + 1];
-                // m_n = q v^n/n! - sum_d (mu_d/h) v^(n-e_d)/(n-e_d)!
+                const R px = P[s][0][nx + 1], py = P[s][1][ny + 1], pz = P[s][2][nz + 1];
                 a += sq[s] * px * py * pz;
                 a -= sm[s][0] * P[s][0][nx] * py * pz + sm[s][1] * px * P[s][1][ny] * pz +
                      sm[s][2] * px * py * P[s][2][nz];
@@ -87,79 +182,148 @@ __global__ void __launch_bounds__(kP2MThreads) p2m_kernel(
     }
 #pragma unroll
     for (int k = 0; k < CPT; k++) {
-        int cidx = threadIdx.x + k * kP2MThreads;
-        if (cidx < ncoef) M[(int64_t)b * ld + cidx] = acc[k];
+        const int cc = tid + k * kUpThreads;
+        if (cc < ncoef) store_multipole(up, depth, b, cc, acc[k], ld);
+    }
+
+    // M2M: climb while this block completes the last child of the parent
+    int box = b;
+    for (int l = depth; l > 2; l--) {
+        __threadfence();  // this block's multipoles are visible before the count
+        __syncthreads();
+        if (tid == 0) {
+            const int par = up.parent[l][box];
+            const int old = atomicAdd(&up.arrive[l - 1][par], 1);
+            int nxt = -1;
+            if (old == up.nchild[l - 1][par] - 1) {
+                up.arrive[l - 1][par] = 0;  // re-armed for the next pass
+                nxt = par;
+            }
+            s_next = nxt;
+        }
+        __syncthreads();
+        const int par = s_next;
+        if (par < 0) return;
+        __threadfence();
+        const int c0 = up.child0[l - 1][par], nc = up.nchild[l - 1][par];
+        if (tid < nc) s_oct[tid] = up.key[l][c0 + tid] & 7;
+        const R* Mc = reinterpret_cast<const R*>(up.M[l]);
+        for (int idx = tid; idx < nc * ncoef; idx += kUpThreads) {
+            const int j = idx / ncoef, cc = idx - j * ncoef;
+            S[j * ncoef + cc] = __ldcg(Mc + (int64_t)(c0 + j) * ld + cc) * pow2neg<R>(sdeg[cc]);
+        }
+        __syncthreads();
+        // g_n = sum_k (s/4)^k/k! m_{n - k e_d}, along x (S -> T), y (T -> S), z (S -> T)
+        for (int ax = 0; ax < 3; ax++) {
+            const R* src = ax == 1 ? T : S;
+            R* dst = ax == 1 ? S : T;
+            for (int idx = tid; idx < nc * ncoef; idx += kUpThreads) {
+                const int j = idx / ncoef, cc = idx - j * ncoef;
+                const bool neg = (s_oct[j] >> ax) & 1;
+                const R* row = src + j * ncoef;
+                R a = row[cc];
+                int i = cc;
+                for (int k = 1; k <= kMaxP; k++) {
+                    i = sdn[3 * i + ax];
+                    if (i < 0) break;
+                    const R v = W[k] * row[i];
+                    a += (neg && (k & 1)) ? -v : v;
+                }
+                dst[j * ncoef + cc] = a;
+            }
+            __syncthreads();
+        }
+        for (int cc = tid; cc < ncoef; cc += kUpThreads) {
+            R a = R(0);
+            for (int j = 0; j < nc; j++) a += T[j * ncoef + cc];
+            store_multipole(up, l - 1, par, cc, a, ld);
+        }
+        box = par;
     }
 }
 
 // ---------------------------------------------------------------------------
-// M2M: m^P_n = sum_children sum_{k <= n} (-1)^(b.k) 2^-(|n|+|k|)/k! m^C_{n-k}
-// (child centre offset from the parent centre is (b - 1/2) h_P / 2 per axis)
+// downward pass, inside the kernels that evaluate the leaves: the block of
+// leaf b forms the locals of b's ancestors from level 2 down to b itself,
+//   f^l = sum over offset chunks of the M2L partials of level l
+//         + 2^-(|n|+1) sum_{|k| <= p-|n|} prod_d (t_d)^k_d / k_d!  f^(l-1)_{n+k},
+// t_d = +1/4 where the child bit is 1, -1/4 where it is 0 (L2L, Sec. II.B,
+// shift of a local expansion to the child centre z_P + (b - 1/2) h_P / 2).
+// The shift runs as three one-axis passes (exact: |n + k| <= p is kept by each).
+// cinfo[4 c .. 4 c + 3] = packed n, index of n + e_x, n + e_y, n + e_z.
 // ---------------------------------------------------------------------------
+struct DownPtrs {
+    const void* Lp[kMaxDepth + 1];
+    const int* parent[kMaxDepth + 1];
+    const int* key[kMaxDepth + 1];
+    int cap[kMaxDepth + 1];
+    int depth, nchunk;
+};
+
 template <typename R>
-__global__ void __launch_bounds__(128) m2m_kernel(int npar, const int* __restrict__ child0,
-                                                  const int* __restrict__ nchild, const int* __restrict__ ckey,
-                                                  const R* __restrict__ Mc, R* __restrict__ Mp, int ld, int ncoef,
-                                                  const int* __restrict__ ptr, const int* __restrict__ src,
-                                                  const int* __restrict__ par, const R* __restrict__ w) {
-    extern __shared__ unsigned char smem_raw[];
-    R* S = reinterpret_cast<R*>(smem_raw);  // [8][ld]
-    __shared__ int oct[8];
-    const int b = blockIdx.x;
-    if (b >= npar) return;
-    const int c0 = child0[b], nc = nchild[b];
-    if (threadIdx.x < nc) oct[threadIdx.x] = ckey[c0 + threadIdx.x] & 7;
-    for (int idx = threadIdx.x; idx < nc * ncoef; idx += blockDim.x) {
-        int j = idx / ncoef, cc = idx - j * ncoef;
-        S[j * ld + cc] = Mc[(int64_t)(c0 + j) * ld + cc];
+__device__ inline R shift_up_axis(const R* src, int cc, int ax, bool neg, const int* cinfo, const R* W) {
+    R a = src[cc];
+    int i = cc;
+    for (int k = 1; k <= kMaxP; k++) {
+        i = cinfo[4 * i + 1 + ax];
+        if (i < 0) break;
+        const R v = W[k] * src[i];
+        a += (neg && (k & 1)) ? -v : v;
     }
-    __syncthreads();
-    for (int cc = threadIdx.x; cc < ncoef; cc += blockDim.x) {
-        R acc = R(0);
-        for (int e = ptr[cc]; e < ptr[cc + 1]; e++) {
-            int s = src[e], pb = par[e];
-            R ww = w[e];
-            for (int j = 0; j < nc; j++) {
-                R v = ww * S[j * ld + s];
-                acc += (__popc(pb & oct[j]) & 1) ? -v : v;
-            }
-        }
-        Mp[(int64_t)b * ld + cc] = acc;
-    }
+    return a;
 }
 
-// ---------------------------------------------------------------------------
-// L2L: f^C_n = sum_chunks M2L partial + 2^-(|n|+1) sum_k (x/h_P)^k/k! f^P_{n+k},
-// x/h_P = +-1/4 per axis (+ where the child bit is 1)
-// ---------------------------------------------------------------------------
-template <typename R>
-__global__ void __launch_bounds__(128) l2l_kernel(int nbox, int cap, int nchunk, const int* __restrict__ key,
-                                                  const int* __restrict__ parent, const R* __restrict__ Lp,
-                                                  const R* __restrict__ Lpar, R* __restrict__ L, int ld, int ncoef,
-                                                  const int* __restrict__ ptr, const int* __restrict__ src,
-                                                  const int* __restrict__ par, const R* __restrict__ w) {
-    extern __shared__ unsigned char smem_raw[];
-    R* F = reinterpret_cast<R*>(smem_raw);  // parent locals [ld]
-    const int b = blockIdx.x;
-    if (b >= nbox) return;
-    const bool shift = Lpar != nullptr;
-    int noct = 0;
-    if (shift) {
-        int ps = parent[b];
-        noct = (~key[b]) & 7;
-        for (int cc = threadIdx.x; cc < ncoef; cc += blockDim.x) F[cc] = Lpar[(int64_t)ps * ld + cc];
+// all threads of the block call it; f, t0, t1: ncoef each in shared memory
+template <typename R, int NT>
+__device__ void far_locals(const DownPtrs& dp, int b, R* f, R* t0, R* t1, const int* cinfo, const R* W, int ncoef,
+                           int ld) {
+    __shared__ int chain[kMaxDepth + 1];
+    __shared__ int coct[kMaxDepth + 1];
+    const int tid = threadIdx.x;
+    const int d = dp.depth;
+    if (tid == 0) {
+        int s = b;
+        for (int l = d; l >= 2; l--) {
+            chain[l] = s;
+            coct[l] = dp.key[l][s] & 7;
+            if (l > 2) s = dp.parent[l][s];
+        }
     }
     __syncthreads();
-    for (int cc = threadIdx.x; cc < ncoef; cc += blockDim.x) {
-        R acc = R(0);
-        for (int k = 0; k < nchunk; k++) acc += Lp[((int64_t)k * cap + b) * ld + cc];
-        if (shift) {
-            for (int e = ptr[cc]; e < ptr[cc + 1]; e++) {
-                R v = w[e] * F[src[e]];
-                acc += (__popc(par[e] & noct) & 1) ? -v : v;
+    constexpr int CPT = (286 + NT - 1) / NT;
+    for (int l = 2; l <= d; l++) {
+        const R* lp = reinterpret_cast<const R*>(dp.Lp[l]) + (int64_t)chain[l] * ld;
+        const int64_t cs = (int64_t)dp.cap[l] * ld;
+        R ps[CPT];
+#pragma unroll
+        for (int k = 0; k < CPT; k++) {
+            const int cc = tid + k * NT;
+            R a = R(0);
+            if (cc < ncoef) {
+#pragma unroll 4
+                for (int ch = 0; ch < dp.nchunk; ch++) a += lp[ch * cs + cc];
+            }
+            ps[k] = a;
+        }
+        if (l > 2) {
+            const int oct = coct[l];
+            for (int cc = tid; cc < ncoef; cc += NT) t0[cc] = shift_up_axis(f, cc, 0, !(oct & 1), cinfo, W);
+            __syncthreads();
+            for (int cc = tid; cc < ncoef; cc += NT) t1[cc] = shift_up_axis(t0, cc, 1, !(oct & 2), cinfo, W);
+            __syncthreads();
+#pragma unroll
+            for (int k = 0; k < CPT; k++) {
+                const int cc = tid + k * NT;
+                if (cc < ncoef)
+                    ps[k] += pow2neg<R>((cinfo[4 * cc] >> 24) + 1) * shift_up_axis(t1, cc, 2, !(oct & 4), cinfo, W);
             }
         }
-        L[(int64_t)b * ld + cc] = acc;
+#pragma unroll
+        for (int k = 0; k < CPT; k++) {
+            const int cc = tid + k * NT;
+            if (cc < ncoef) f[cc] = ps[k];
+        }
+        __syncthreads();
     }
 }
 
@@ -167,7 +331,8 @@ __global__ void __launch_bounds__(128) l2l_kernel(int nbox, int cap, int nchunk,
 // M2L (SIMT): tiles of up to 32 same-level, same-octant-class target boxes;
 // lane = target box, each warp owns a balanced set of output coefficients;
 // the offsets of the class are split into `nchunk` ranges over blockIdx.y,
-// each writing its own partial output (summed in fixed order by l2l_kernel).
+// each writing its own partial output (summed in fixed order by the downward
+// pass in the leaf kernels).
 // ---------------------------------------------------------------------------
 template <typename R>
 __global__ void __launch_bounds__(256) m2l_simt_kernel(const M2LTile* __restrict__ tiles, LevelPtrs lp,
@@ -286,7 +451,7 @@ __host__ __device__ inline size_t leaf_smem_bytes(int ncoef) {
     size_t b = sizeof(Q4<R>) * CAP;                          // positions + charge
     if (MODE != LEAF_CHARGE_PHI_E) b += sizeof(Q4<R>) * CAP;  // dipoles
     if (MODE == LEAF_CHARGE_PHI_E) b += sizeof(int) * CAP;    // source index (coincidence check)
-    b += sizeof(R) * 2 * (size_t)ncoef;                      // locals, 1/n!
+    b += sizeof(R) * 4 * (size_t)ncoef;                      // locals, two shift buffers, 1/n!
     b += sizeof(int) * 4 * (size_t)ncoef;                     // packed n, n + e_d
     if (MODE == LEAF_FULL) b += sizeof(int) * 6 * (size_t)ncoef;
     return b;
@@ -311,10 +476,10 @@ template <typename R, int MODE>
 __global__ void __launch_bounds__(kLeafThreads) leaf_kernel(
     int nleaf, const int* __restrict__ lkey, const int* __restrict__ lstart, const int* __restrict__ lcount,
     const int* __restrict__ lmap, const int* __restrict__ order, int depth, const Q4<R>* __restrict__ srcA,
-    const Q4<R>* __restrict__ srcB,
-    const R* __restrict__ Lf, int ld, int ncoef, const int* __restrict__ mi, const double* __restrict__ inv_fact,
-    const int* __restrict__ up1, const int* __restrict__ up2, R h, double* __restrict__ out_phi,
-    double* __restrict__ out_E, double* __restrict__ out_G, int* __restrict__ err, int far) {
+    const Q4<R>* __restrict__ srcB, DownPtrs dp, int ld, int ncoef, int p, const int* __restrict__ mi,
+    const double* __restrict__ inv_fact, const int* __restrict__ up1, const int* __restrict__ up2, R h,
+    double* __restrict__ out_phi, double* __restrict__ out_E, double* __restrict__ out_G, int* __restrict__ err,
+    int far) {
     constexpr int NC = LeafOut<MODE>::NC;
     constexpr int CAP = LeafCap<R>::N;
     constexpr bool HAS_PHI = MODE != LEAF_DIPOLE_E;
@@ -332,9 +497,12 @@ __global__ void __launch_bounds__(kLeafThreads) leaf_kernel(
     int* sidx = reinterpret_cast<int*>(tail);
     if (CHECK) tail += sizeof(int) * CAP;
     R* f = reinterpret_cast<R*>(tail);
-    R* ifact = f + ncoef;
+    R* t0 = f + ncoef;
+    R* t1 = t0 + ncoef;
+    R* ifact = t1 + ncoef;
     int* cinfo = reinterpret_cast<int*>(ifact + ncoef);  // [ncoef][4]: packed n, n+e_x, n+e_y, n+e_z
     int* cup2 = cinfo + 4 * ncoef;                       // [ncoef][6] (FULL only)
+    __shared__ R W[kMaxP + 1];
     __shared__ int nb_start[27];
     __shared__ int nb_pre[28];
     __shared__ R nb_shift[27][3];
@@ -368,7 +536,6 @@ __global__ void __launch_bounds__(kLeafThreads) leaf_kernel(
         if (tid == 0) nb_pre[0] = 0;
     }
     for (int cc = tid; cc < ncoef; cc += blockDim.x) {
-        f[cc] = far ? Lf[(int64_t)b * ld + cc] : R(0);
         ifact[cc] = R(inv_fact[cc]);
         cinfo[4 * cc] = mi[cc];
         cinfo[4 * cc + 1] = up1[3 * cc];
@@ -377,7 +544,9 @@ __global__ void __launch_bounds__(kLeafThreads) leaf_kernel(
         if (HAS_G)
             for (int k = 0; k < 6; k++) cup2[6 * cc + k] = up2[6 * cc + k];
     }
+    shift_weights(W, p);
     __syncthreads();
+    if (far) far_locals<R, kLeafThreads>(dp, b, f, t0, t1, cinfo, W, ncoef, ld);
     const int total = nb_pre[27];
     const R inv_h = R(1) / h;
 
@@ -529,33 +698,54 @@ __global__ void __launch_bounds__(kLeafThreads) leaf_kernel(
 }
 
 // far field of the solver pass, added to the near field already in out_E:
-// E += -(1/h^2) sum_{|n| <= p-1} u^n/n! f_{n+e_d}, u = (x - z) / h (Sec. II.B)
+// E += -(1/h^2) sum_{|n| <= p-1} u^n/n! f_{n+e_d}, u = (x - z) / h (Sec. II.B).
+// With pf.Ad set (PCG), the kernel also forms Ad = d/alpha - E of its sites
+// and the leaf's partial of d.Ad; the last block to finish adds the partials
+// of all leaves in leaf order into scal[S_DAD] (deterministic).
+constexpr int kL2PThreads = 128;
+
+struct PcgFuse {
+    const double* alpha;
+    const double* d;
+    double* Ad;
+    double* partial;  // [nleaf]
+    double* scal;
+    int* ticket;
+    cudaGraphConditionalHandle cond;  // inside the solve graph: cleared here, set by the update kernel
+};
+
 template <typename R>
-__global__ void __launch_bounds__(128) l2p_field_add_kernel(int nleaf, const int* __restrict__ lstart,
-                                                            const int* __restrict__ lcount,
-                                                            const Q4<R>* __restrict__ srcA, const R* __restrict__ Lf,
-                                                            int ld, int ncoef, const int* __restrict__ mi,
-                                                            const double* __restrict__ inv_fact,
-                                                            const int* __restrict__ up1, R h,
-                                                            double* __restrict__ out_E) {
+__global__ void __launch_bounds__(kL2PThreads) l2p_field_add_kernel(
+    int nleaf, const int* __restrict__ lstart, const int* __restrict__ lcount, const Q4<R>* __restrict__ srcA,
+    DownPtrs dp, int ld, int ncoef, int p, const int* __restrict__ mi, const double* __restrict__ inv_fact,
+    const int* __restrict__ up1, R h, double* __restrict__ out_E, PcgFuse pf) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     R* f = reinterpret_cast<R*>(smem_raw);
-    R* ifact = f + ncoef;
+    R* t0 = f + ncoef;
+    R* t1 = t0 + ncoef;
+    R* ifact = t1 + ncoef;
     int* cinfo = reinterpret_cast<int*>(ifact + ncoef);  // [ncoef][4]
+    __shared__ R W[kMaxP + 1];
+    __shared__ double red[kL2PThreads / 32];
+    __shared__ bool last;
     const int b = blockIdx.x;
     if (b >= nleaf) return;
-    for (int cc = threadIdx.x; cc < ncoef; cc += blockDim.x) {
-        f[cc] = Lf[(int64_t)b * ld + cc];
+    const int tid = threadIdx.x;
+    if (pf.cond && b == 0 && tid == 0) cudaGraphSetConditional(pf.cond, 0u);
+    for (int cc = tid; cc < ncoef; cc += kL2PThreads) {
         ifact[cc] = R(inv_fact[cc]);
         cinfo[4 * cc] = mi[cc];
         cinfo[4 * cc + 1] = up1[3 * cc];
         cinfo[4 * cc + 2] = up1[3 * cc + 1];
         cinfo[4 * cc + 3] = up1[3 * cc + 2];
     }
+    shift_weights(W, p);
     __syncthreads();
+    far_locals<R, kL2PThreads>(dp, b, f, t0, t1, cinfo, W, ncoef, ld);
     const int s0 = lstart[b], cnt = lcount[b];
     const R inv_h = R(1) / h;
-    for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
+    double dot = 0.0;
+    for (int t = tid; t < cnt; t += kL2PThreads) {
         const int i = s0 + t;
         const Q4<R> me = srcA[i];
         const R ux = me.x * inv_h, uy = me.y * inv_h, uz = me.z * inv_h;
@@ -573,9 +763,47 @@ __global__ void __launch_bounds__(128) l2p_field_add_kernel(int nleaf, const int
             d2 += wgt * f[cinfo[4 * cc + 3]];
         }
         const R s2 = -inv_h * inv_h;
-        out_E[3 * (int64_t)i] += (double)(d0 * s2);
-        out_E[3 * (int64_t)i + 1] += (double)(d1 * s2);
-        out_E[3 * (int64_t)i + 2] += (double)(d2 * s2);
+        double e[3];
+        e[0] = out_E[3 * (int64_t)i] + (double)(d0 * s2);
+        e[1] = out_E[3 * (int64_t)i + 1] + (double)(d1 * s2);
+        e[2] = out_E[3 * (int64_t)i + 2] + (double)(d2 * s2);
+        for (int k = 0; k < 3; k++) out_E[3 * (int64_t)i + k] = e[k];
+        if (pf.Ad) {
+            const double a = pf.alpha[i];
+            for (int k = 0; k < 3; k++) {
+                const double dk = pf.d[3 * (int64_t)i + k];
+                const double v = a > 0.0 ? dk / a - e[k] : 0.0;
+                pf.Ad[3 * (int64_t)i + k] = v;
+                dot += dk * v;
+            }
+        }
+    }
+    if (!pf.Ad) return;
+    // leaf partial, then the last block adds all leaves in order
+    for (int o = 16; o > 0; o >>= 1) dot += __shfl_down_sync(0xffffffffu, dot, o);
+    if ((tid & 31) == 0) red[tid >> 5] = dot;
+    __syncthreads();
+    if (tid == 0) {
+        double v = 0.0;
+        for (int w = 0; w < kL2PThreads / 32; w++) v += red[w];
+        pf.partial[b] = v;
+        __threadfence();
+        last = atomicAdd(pf.ticket, 1) == (int)gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    double v = 0.0;
+    for (int k = tid; k < nleaf; k += kL2PThreads) v += __ldcg(pf.partial + k);
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    __syncthreads();
+    if ((tid & 31) == 0) red[tid >> 5] = v;
+    __syncthreads();
+    if (tid == 0) {
+        double t = 0.0;
+        for (int w = 0; w < kL2PThreads / 32; w++) t += red[w];
+        pf.scal[S_DAD] = t;
+        *pf.ticket = 0;
     }
 }
 
@@ -625,6 +853,19 @@ int m2l_setup(polfmm_ctx* c) {
     return POLFMM_OK;
 }
 
+static DownPtrs down_ptrs(polfmm_ctx* c) {
+    DownPtrs dp{};
+    for (int l = 0; l <= c->depth; l++) {
+        dp.Lp[l] = c->lv[l].Lp;
+        dp.parent[l] = c->lv[l].parent;
+        dp.key[l] = c->lv[l].key;
+        dp.cap[l] = c->lv[l].cap;
+    }
+    dp.depth = c->depth;
+    dp.nchunk = c->m2l_chunks;
+    return dp;
+}
+
 template <typename R>
 static void launch_leaf(polfmm_ctx* c, int mode, const double* mu_sorted, double* phi, double* E, double* G,
                         bool mu_packed, cudaStream_t st, int far) {
@@ -638,10 +879,10 @@ static void launch_leaf(polfmm_ctx* c, int mode, const double* mu_sorted, double
         pack_dipoles_kernel<R><<<grid_for(c->n, 256), 256, 0, st>>>(c->n, mu_sorted, B);
     }
     LaunchScope ls(c, mode == LEAF_DIPOLE_E ? F_LEAF_DIPOLE : (mode == LEAF_CHARGE_PHI_E ? F_LEAF_STATIC : F_LEAF_FULL));
-#define LEAF_ARGS                                                                                                  \
-    L.nbox, L.key, c->lstart, c->lcount, L.map, c->leaf_order, c->depth, A, B, (const R*)L.L, c->ld, c->ncoef,     \
-        T.mi, T.inv_fact,                                                                                      \
-        T.up1, T.up2, h, phi, E, G, c->err, far
+    const DownPtrs dp = down_ptrs(c);
+#define LEAF_ARGS                                                                                                \
+    L.nbox, L.key, c->lstart, c->lcount, L.map, c->leaf_order, c->depth, A, B, dp, c->ld, c->ncoef, c->p, T.mi, \
+        T.inv_fact, T.up1, T.up2, h, phi, E, G, c->err, far
     if (mode == LEAF_DIPOLE_E)
         leaf_kernel<R, LEAF_DIPOLE_E>
             <<<L.nbox, kLeafThreads, leaf_smem_bytes<R, LEAF_DIPOLE_E>(c->ncoef), st>>>(LEAF_ARGS);
@@ -670,25 +911,39 @@ size_t source_record_bytes(bool mixed) { return mixed ? sizeof(Q4<float>) : size
 void m2l_tensor_launch(polfmm_ctx* c);  // m2l_tc.cu
 bool m2l_tensor_enabled(polfmm_ctx* c);
 
-template <typename R>
-static const R* weights(const double* wd, const float* wf);
-template <>
-const double* weights<double>(const double* wd, const float*) {
-    return wd;
-}
-template <>
-const float* weights<float>(const double*, const float* wf) {
-    return wf;
+bool m2l_tensor_split_targets(polfmm_ctx* c, float** hi, float** lo, int* KP);  // m2l_tc.cu
+
+static UpPtrs up_ptrs(polfmm_ctx* c) {
+    UpPtrs up{};
+    for (int l = 0; l <= c->depth; l++) {
+        up.M[l] = c->lv[l].M;
+        up.parent[l] = c->lv[l].parent;
+        up.child0[l] = c->lv[l].child0;
+        up.nchild[l] = c->lv[l].nchild;
+        up.key[l] = c->lv[l].key;
+        up.arrive[l] = c->lv[l].arrive;
+    }
+    float* hi[kMaxDepth + 1] = {nullptr};
+    float* lo[kMaxDepth + 1] = {nullptr};
+    int KP = 0;
+    if (m2l_tensor_split_targets(c, hi, lo, &KP)) {
+        for (int l = 2; l <= c->depth; l++) {
+            up.hi[l] = hi[l];
+            up.lo[l] = lo[l];
+        }
+        up.KP = KP;
+    }
+    return up;
 }
 
 template <typename R>
-static void pass_impl(polfmm_ctx* c, int mode, bool use_q, const double* mu_sorted, double* phi, double* E,
-                      double* G, bool mu_packed) {
+static bool pass_impl(polfmm_ctx* c, int mode, bool use_q, const double* mu_sorted, double* phi, double* E,
+                      double* G, bool mu_packed, bool pcg) {
     const int d = c->depth;
     const Tables& T = c->tab;
     Level& Lf = c->lv[d];
     // solver passes: the near-field pair sums run on a second stream while the
-    // far-field chain (P2M .. L2L) runs here; the far field is added after the join
+    // far-field chain (upward pass, M2L) runs here; the far field is added after the join
     const bool overlap = mode == LEAF_DIPOLE_E && d >= 2 && c->side_stream && !c->opt.profile;
     if (overlap) {
         cudaEventRecord(c->ev_fork, c->stream);
@@ -696,69 +951,50 @@ static void pass_impl(polfmm_ctx* c, int mode, bool use_q, const double* mu_sort
         launch_leaf<R>(c, mode, mu_sorted, phi, E, G, mu_packed, c->side_stream, 0);
         cudaEventRecord(c->ev_join, c->side_stream);
     }
-    // P2M
-    {
-        LaunchScope ls(c, F_P2M);
-        R inv_h = R((double)(1 << d) / c->side);
-        p2m_kernel<R><<<Lf.nbox, kP2MThreads, 0, c->stream>>>(Lf.nbox, c->lstart, c->lcount, (const R*)c->ploc,
-                                                              use_q ? c->q_s : nullptr, mu_sorted, (R*)Lf.M, c->ld,
-                                                              c->ncoef, c->p, T.mi, inv_h);
-    }
     if (d >= 2) {
-        // M2M up to level 2
-        for (int l = d - 1; l >= 2; l--) {
-            LaunchScope ls(c, F_M2M);
-            Level& P = c->lv[l];
-            Level& C = c->lv[l + 1];
-            m2m_kernel<R><<<P.nbox, 128, sizeof(R) * 8 * c->ld, c->stream>>>(
-                P.nbox, P.child0, P.nchild, C.key, (const R*)C.M, (R*)P.M, c->ld, c->ncoef, T.m2m_ptr, T.m2m_src,
-                T.m2m_par, weights<R>(T.m2m_w, T.m2m_wf));
+        // P2M and M2M up to level 2 (one launch)
+        {
+            LaunchScope ls(c, F_P2M);
+            R inv_h = R((double)(1 << d) / c->side);
+            upward_kernel<R><<<Lf.nbox, kUpThreads, upward_smem_bytes<R>(c->ncoef), c->stream>>>(
+                Lf.nbox, d, c->lstart, c->lcount, (const R*)c->ploc, use_q ? c->q_s : nullptr, mu_sorted,
+                up_ptrs(c), c->ld, c->ncoef, c->p, T.mi, T.dn1, inv_h);
         }
-        // M2L
-        if (c->ntiles > 0) {
-            if (m2l_tensor_enabled(c)) {
-                m2l_tensor_launch(c);
-            } else {
-                LaunchScope ls(c, F_M2L);
-                dim3 grid(c->ntiles, c->m2l_chunks);
-                size_t smem = m2l_simt_smem(c->ncoef, sizeof(R));
-                m2l_simt_kernel<R><<<grid, 256, smem, c->stream>>>(
-                    c->tiles, level_ptrs(c), c->mixed ? (const R*)T.Df : (const R*)T.D, T.class_off, T.add, T.pre,
-                    T.warp_out_ptr, T.warp_out, c->ncoef, c->ld, c->m2l_chunks);
-            }
+        // M2L, all levels >= 2 in one launch
+        if (m2l_tensor_enabled(c)) {
+            m2l_tensor_launch(c);
+        } else {
+            LaunchScope ls(c, F_M2L);
+            dim3 grid(c->ntiles, c->m2l_chunks);
+            size_t smem = m2l_simt_smem(c->ncoef, sizeof(R));
+            m2l_simt_kernel<R><<<grid, 256, smem, c->stream>>>(
+                c->tiles, level_ptrs(c), c->mixed ? (const R*)T.Df : (const R*)T.D, T.class_off, T.add, T.pre,
+                T.warp_out_ptr, T.warp_out, c->ncoef, c->ld, c->m2l_chunks);
         }
-        // L2L (level 2: partial sums only)
-        for (int l = 2; l <= d; l++) {
-            LaunchScope ls(c, F_L2L);
-            Level& B = c->lv[l];
-            const R* Lpar = l >= 3 ? (const R*)c->lv[l - 1].L : nullptr;
-            l2l_kernel<R><<<B.nbox, 128, sizeof(R) * c->ld, c->stream>>>(
-                B.nbox, B.cap, c->m2l_chunks, B.key, B.parent, (const R*)B.Lp, Lpar, (R*)B.L, c->ld, c->ncoef,
-                T.l2l_ptr, T.l2l_src, T.l2l_par, weights<R>(T.l2l_w, T.l2l_wf));
-        }
-    } else {
-        cudaMemsetAsync(Lf.L, 0, sizeof(R) * (size_t)Lf.cap * c->ld, c->stream);
     }
+    // L2L runs inside the leaf kernels below
     if (overlap) {
         cudaStreamWaitEvent(c->stream, c->ev_join, 0);
         LaunchScope ls(c, F_LEAF_DIPOLE);
         const R h = R(c->side / (double)(1 << d));
-        size_t smem = (2 * sizeof(R) + 4 * sizeof(int)) * (size_t)c->ncoef;
-        l2p_field_add_kernel<R><<<Lf.nbox, 128, smem, c->stream>>>(Lf.nbox, c->lstart, c->lcount,
-                                                                   reinterpret_cast<const Q4<R>*>(c->srcA),
-                                                                   (const R*)Lf.L, c->ld, c->ncoef, T.mi, T.inv_fact,
-                                                                   T.up1, h, E);
-        return;
+        size_t smem = (4 * sizeof(R) + 4 * sizeof(int)) * (size_t)c->ncoef;
+        PcgFuse pf{};
+        if (pcg)
+            pf = PcgFuse{c->alpha_s, c->d,      c->Ad, c->leaf_partial,
+                         c->scal,    c->ticket, c->capturing_loop ? c->loop_cond : 0};
+        l2p_field_add_kernel<R><<<Lf.nbox, kL2PThreads, smem, c->stream>>>(
+            Lf.nbox, c->lstart, c->lcount, reinterpret_cast<const Q4<R>*>(c->srcA), down_ptrs(c), c->ld, c->ncoef,
+            c->p, T.mi, T.inv_fact, T.up1, h, E, pf);
+        return pcg;
     }
-    launch_leaf<R>(c, mode, mu_sorted, phi, E, G, mu_packed, c->stream, 1);
+    launch_leaf<R>(c, mode, mu_sorted, phi, E, G, mu_packed, c->stream, d >= 2 ? 1 : 0);
+    return false;
 }
 
-void fmm_pass(polfmm_ctx* c, int mode, bool use_q, const double* mu_sorted, double* phi, double* E, double* G,
-              bool mu_packed) {
-    if (c->mixed)
-        pass_impl<float>(c, mode, use_q, mu_sorted, phi, E, G, mu_packed);
-    else
-        pass_impl<double>(c, mode, use_q, mu_sorted, phi, E, G, mu_packed);
+bool fmm_pass(polfmm_ctx* c, int mode, bool use_q, const double* mu_sorted, double* phi, double* E, double* G,
+              bool mu_packed, bool pcg) {
+    if (c->mixed) return pass_impl<float>(c, mode, use_q, mu_sorted, phi, E, G, mu_packed, pcg);
+    return pass_impl<double>(c, mode, use_q, mu_sorted, phi, E, G, mu_packed, pcg);
 }
 
 int fmm_ops_init_attributes(polfmm_ctx*) {
@@ -771,6 +1007,11 @@ int fmm_ops_init_attributes(polfmm_ctx*) {
         return POLFMM_ERR_CUDA;
     if (cudaFuncSetAttribute(m2l_simt_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need_f) !=
         cudaSuccess)
+        return POLFMM_ERR_CUDA;
+    if (cudaFuncSetAttribute(upward_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)upward_smem_bytes<double>(nc_max)) != cudaSuccess ||
+        cudaFuncSetAttribute(upward_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)upward_smem_bytes<float>(nc_max)) != cudaSuccess)
         return POLFMM_ERR_CUDA;
 #define LEAF_ATTR(R, M)                                                                                 \
     if (cudaFuncSetAttribute(leaf_kernel<R, M>, cudaFuncAttributeMaxDynamicSharedMemorySize,            \

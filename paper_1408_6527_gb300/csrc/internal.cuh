@@ -44,17 +44,7 @@ struct Tables {
     int* up2 = nullptr;               // [ncoef][6]: index of n + e_d + e_e (xx xy xz yy yz zz) or -1
     int* pre = nullptr;               // [ncoef]: number of m with |m| <= p - |n| (a prefix)
     short* add = nullptr;             // [ncoef][ncoef]: index of n + m (valid for m < pre[n])
-    // shift operators as CSR lists over output coefficient c
-    int* m2m_ptr = nullptr;           // [ncoef + 1]
-    int* m2m_src = nullptr;           // index of n - k
-    int* m2m_par = nullptr;           // parity bits of k (kx&1 | (ky&1)<<1 | (kz&1)<<2)
-    double* m2m_w = nullptr;          // 2^-(|n|+|k|) / k!
-    float* m2m_wf = nullptr;
-    int* l2l_ptr = nullptr;
-    int* l2l_src = nullptr;           // index of n + k
-    int* l2l_par = nullptr;
-    double* l2l_w = nullptr;          // 2^-(|n|+1+2|k|) / k!
-    float* l2l_wf = nullptr;
+    int* dn1 = nullptr;               // [ncoef][3]: index of n - e_d or -1
     double* D = nullptr;              // [343][ncoef] normalised derivatives of 1/r at integer offsets
     float* Df = nullptr;
     int* class_off = nullptr;         // [8][189] packed offsets (ox+3) | (oy+3)<<4 | (oz+3)<<8
@@ -91,8 +81,8 @@ struct Level {
     int class_count[8] = {0};
     int class_start[8] = {0};
     void* M = nullptr;    // [cap][ld]
-    void* L = nullptr;    // [cap][ld]
-    void* Lp = nullptr;   // [m2l_chunks][cap][ld]
+    void* Lp = nullptr;   // [m2l_chunks][cap][ld] M2L partial locals
+    int* arrive = nullptr;  // [cap] children whose multipoles are done (0 between passes)
 };
 
 // profiling families
@@ -150,6 +140,7 @@ struct polfmm_ctx {
     double* h_scal = nullptr;     // pinned host mirror
     int* err = nullptr;           // device error word
     int* ticket = nullptr;        // last-block counter of the fused reductions (0 between kernels)
+    double* leaf_partial = nullptr;  // [leaves] per-leaf partial sums of the fused d.Ad reduction
     // sort / scan scratch
     uint32_t* key_tmp = nullptr;
     int* val_tmp = nullptr;
@@ -171,6 +162,16 @@ struct polfmm_ctx {
     cudaGraphExec_t pcg_graph = nullptr;   // one PCG iteration of the current tree
     bool pcg_graph_dirty = true;
     int64_t pcg_graph_launches = 0;
+    // PCG iterations until convergence as one graph: a while node whose body is
+    // one iteration; the last kernel of the body sets the loop condition
+    cudaGraph_t loop_g = nullptr;
+    cudaGraph_t loop_body = nullptr;
+    cudaGraphExec_t loop_exec = nullptr;
+    cudaGraphConditionalHandle loop_cond = 0;
+    bool loop_dirty = true;
+    bool loop_failed = false;              // set-up refused: per-iteration graphs instead
+    bool capturing_loop = false;           // kernels captured now take loop_cond
+    int64_t loop_launches = 0;             // kernel launches per iteration of the body
     void* tc = nullptr;           // tensor-core M2L state
     // profiling
     cudaEvent_t ev_pool[2 * 4096];
@@ -202,8 +203,11 @@ size_t tree_count_scratch(int64_t n);
 int scan_exclusive(polfmm_ctx* c, const int* in, int* out, int n, int* total_dev);
 
 // fmm_ops.cu
-void fmm_pass(polfmm_ctx* c, int mode, bool use_q, const double* mu_sorted, double* phi, double* E,
-              double* G, bool mu_packed = false);
+// pcg: when non-null in a solver pass, the kernel that completes the field
+// also forms Ad = d/alpha - T d and the sum d.Ad (scal[S_DAD]); returns true
+// if it did (false: the caller runs the separate kernel)
+bool fmm_pass(polfmm_ctx* c, int mode, bool use_q, const double* mu_sorted, double* phi, double* E,
+              double* G, bool mu_packed = false, bool pcg = false);
 int m2l_setup(polfmm_ctx* c);
 void pack_positions(polfmm_ctx* c);
 size_t source_record_bytes(bool mixed);
@@ -213,6 +217,7 @@ void gather_sites(polfmm_ctx* c, const double* src_caller, double* dst_sorted, i
 void scatter_sites(polfmm_ctx* c, const double* src_sorted, double* dst_caller, int comps);
 void solver_init(polfmm_ctx* c, bool warm);
 void solver_pcg_step(polfmm_ctx* c);
+void solver_loop_setup(polfmm_ctx* c, double tol, int max_iter);
 void solver_jacobi_step(polfmm_ctx* c);
 void energy_and_gradients(polfmm_ctx* c, double* forces_caller, double* dq_caller,
                           double* dalpha_caller, bool want_f, bool want_dq, bool want_da);
@@ -220,7 +225,7 @@ void mask_dipoles(polfmm_ctx* c, double* v);
 
 // device scalar slots
 enum Scal {
-    S_RZ = 0, S_RZ_NEW, S_DAD, S_RR, S_BB, S_UQQ, S_MUEQ, S_MUEMU, S_AMU, S_BETA, S_COUNT
+    S_RZ = 0, S_RZ_NEW, S_DAD, S_RR, S_BB, S_UQQ, S_MUEQ, S_MUEMU, S_AMU, S_BETA, S_TOL, S_MAXIT, S_ITER, S_COUNT
 };
 constexpr int kRedBlocks = 256;
 constexpr int kRedSlots = 8;

@@ -10,7 +10,8 @@
 //   * every thread gathers the multipole row of its box's source B - o
 //     (zero-filled where the source box is empty or outside the tree) with
 //     16-byte cp.async copies into the no-swizzle K-major core-matrix layout;
-//     multipoles are stored pre-split into a TF32 high part and the residual;
+//     the upward pass stores every multipole row of levels >= 2 pre-split into
+//     a TF32 high part and the residual, zero-padded to KP inputs;
 //   * one thread bulk-copies the pre-split, block-sparse image of K_o (only
 //     the (output band, input prefix) blocks allowed by |n| + |m| <= p) with
 //     cp.async.bulk completing on an mbarrier;
@@ -21,7 +22,7 @@
 //     gather overwrites shared memory.
 // At the end each warp reads its 32 TMEM lanes (tcgen05.ld) and writes the
 // partial locals of its boxes; partials of different offset ranges are summed
-// in fixed order by the L2L kernel.  Every wait is bounded: on timeout the CTA
+// in fixed order by the downward pass of the leaf kernels.  Every wait is bounded: on timeout the CTA
 // raises an error bit, stops issuing and still frees its TMEM.
 #include <math.h>
 #include <string.h>
@@ -200,33 +201,6 @@ __host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
            | (2u << 10)                      // B format TF32
            | ((uint32_t)(N >> 3) << 17)      // N / 8
            | ((uint32_t)(M >> 4) << 24);     // M / 16
-}
-
-// ---------------------------------------------------------------------------
-// multipoles -> TF32 high part + residual, padded to KP inputs (all levels >= 2)
-// ---------------------------------------------------------------------------
-struct TcSplitArgs {
-    const float* M[kMaxDepth + 1];
-    float* hi[kMaxDepth + 1];
-    float* lo[kMaxDepth + 1];
-    int64_t start[kMaxDepth + 2];  // prefix of nbox * KP over levels
-    int lmin, lmax;
-};
-
-__global__ void tc_split_kernel(TcSplitArgs a, int ld, int ncoef, int KP) {
-    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (t >= a.start[a.lmax + 1]) return;
-    int l = a.lmin;
-    while (t >= a.start[l + 1]) l++;
-    const int64_t u = t - a.start[l];
-    const int64_t b = u / KP;
-    const int k = (int)(u - b * KP);
-    const float v = k < ncoef ? a.M[l][b * ld + k] : 0.f;
-    uint32_t h;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(v));
-    const float hv = __uint_as_float(h);
-    a.hi[l][u] = hv;
-    a.lo[l][u] = v - hv;
 }
 
 // (level, slot) rows of every box of one level, placed by octant class
@@ -574,6 +548,10 @@ int m2l_tensor_prepare(polfmm_ctx* c) {
                 cudaGetLastError();
                 return POLFMM_ERR_OUT_OF_MEMORY;
             }
+            // the padding inputs ncoef .. KP - 1 stay zero; the upward pass writes the rest
+            if (cudaMemset(S->Mhi[l], 0, sizeof(float) * cnt) != cudaSuccess ||
+                cudaMemset(S->Mlo[l], 0, sizeof(float) * cnt) != cudaSuccess)
+                return POLFMM_ERR_CUDA;
         }
         size_t rows_cap = 0;
         for (int l = 2; l <= c->depth; l++) rows_cap += c->lv[l].cap;
@@ -639,32 +617,29 @@ int m2l_tensor_prepare(polfmm_ctx* c) {
     return POLFMM_OK;
 }
 
+bool m2l_tensor_split_targets(polfmm_ctx* c, float** hi, float** lo, int* KP) {
+    if (!m2l_tensor_enabled(c)) return false;
+    TcState* S = state(c);
+    for (int l = 2; l <= c->depth; l++) {
+        hi[l] = S->Mhi[l];
+        lo[l] = S->Mlo[l];
+    }
+    *KP = S->sch.KP;
+    return true;
+}
+
 void m2l_tensor_launch(polfmm_ctx* c) {
     TcState* S = state(c);
     const TcSchedule& sch = S->sch;
     TcLevelPtrs lp{};
-    TcSplitArgs sa{};
-    sa.lmin = 2;
-    sa.lmax = c->depth;
-    int64_t run = 0;
     for (int l = 2; l <= c->depth; l++) {
         Level& B = c->lv[l];
-        sa.M[l] = (const float*)B.M;
-        sa.hi[l] = S->Mhi[l];
-        sa.lo[l] = S->Mlo[l];
-        sa.start[l] = run;
-        run += (int64_t)B.nbox * sch.KP;
         lp.key[l] = B.key;
         lp.map[l] = B.map;
         lp.Mhi[l] = S->Mhi[l];
         lp.Mlo[l] = S->Mlo[l];
         lp.Lp[l] = (float*)B.Lp;
         lp.cap[l] = B.cap;
-    }
-    sa.start[c->depth + 1] = run;
-    {
-        LaunchScope ls(c, F_P2M);
-        tc_split_kernel<<<grid_for(run, 256), 256, 0, c->stream>>>(sa, c->ld, c->ncoef, sch.KP);
     }
     LaunchScope ls(c, F_M2L);
     dim3 grid(S->ntiles, c->m2l_chunks);

@@ -131,11 +131,14 @@ __global__ void pcg_init_kernel(int64_t n, const double* __restrict__ alpha, con
     }
 }
 
-// Ad = d/alpha - T d; d.Ad (partials, then the last block stores the sum)
+// Ad = d/alpha - T d; d.Ad (partials, then the last block stores the sum).
+// Inside the solve graph (cond != 0) it also clears the loop condition, which
+// only the last kernel of the iteration sets again.
 __global__ void pcg_ad_kernel(int64_t n, const double* __restrict__ alpha, const double* __restrict__ d,
                               const double* __restrict__ Td, double* __restrict__ Ad, double* __restrict__ partial,
-                              double* __restrict__ scal, int* __restrict__ ticket) {
+                              double* __restrict__ scal, int* __restrict__ ticket, cudaGraphConditionalHandle cond) {
     __shared__ double sh[kRedThreads];
+    if (cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(cond, 0u);
     double s = 0;
     RED_LOOP(i, 3 * n) {
         double a = alpha[i / 3];
@@ -155,11 +158,14 @@ __global__ void pcg_ad_kernel(int64_t n, const double* __restrict__ alpha, const
 }
 
 // step = rz / dAd; mu += step d; r -= step Ad; z = alpha r; r.z and r.r; the
-// last block stores beta = (r.z)_new / (r.z)_old, (r.z)_new and r.r
+// last block stores beta = (r.z)_new / (r.z)_old, (r.z)_new and r.r.  Inside
+// the solve graph (cond != 0) it counts the iteration and keeps the loop going
+// while d.Ad > 0, the relative residual is finite and above tol, and fewer than
+// max_iter iterations are done.
 __global__ void pcg_update_kernel(int64_t n, const double* __restrict__ alpha, double* __restrict__ scal,
                                   const double* __restrict__ d, const double* __restrict__ Ad, double* __restrict__ mu,
                                   double* __restrict__ r, double* __restrict__ z, double* __restrict__ partial,
-                                  int* __restrict__ ticket) {
+                                  int* __restrict__ ticket, cudaGraphConditionalHandle cond) {
     __shared__ double sh[kRedThreads];
     const double step = scal[S_RZ] / scal[S_DAD];
     double rz = 0, rr = 0;
@@ -189,8 +195,22 @@ __global__ void pcg_update_kernel(int64_t n, const double* __restrict__ alpha, d
             scal[S_RZ] = rz_new;
             scal[S_RR] = rr_all;
             *ticket = 0;
+            if (cond) {
+                const double it = scal[S_ITER] + 1.0;
+                scal[S_ITER] = it;
+                const double res = sqrt(rr_all / scal[S_BB]);
+                const bool go = scal[S_DAD] > 0.0 && isfinite(res) && res > scal[S_TOL] && it < scal[S_MAXIT];
+                cudaGraphSetConditional(cond, go ? 1u : 0u);
+            }
         }
     }
+}
+
+// solve-graph start: tolerance, iteration limit, iteration count
+__global__ void loop_setup_kernel(double* __restrict__ scal, double tol, double max_iter) {
+    scal[S_TOL] = tol;
+    scal[S_MAXIT] = max_iter;
+    scal[S_ITER] = 0.0;
 }
 
 // d = z + beta d, and its packed copy for the next near-field pass
@@ -361,19 +381,20 @@ void solver_init(polfmm_ctx* c, bool warm) {
         pack_vec_kernel<double><<<grid_for(c->n, 256), 256, 0, c->stream>>>(c->n, c->d, c->srcB);
 }
 
-// one PCG iteration: T d by the FMM (d already packed for the near field),
-// then three fused vector kernels
+// one PCG iteration: T d by the FMM (d already packed for the near field;
+// the kernel completing the field also forms Ad and d.Ad when it can), then
+// the fused update and direction kernels
 void solver_pcg_step(polfmm_ctx* c) {
-    fmm_pass(c, LEAF_DIPOLE_E, false, c->d, nullptr, c->Td, nullptr, true);
-    {
+    const cudaGraphConditionalHandle cond = c->capturing_loop ? c->loop_cond : 0;
+    if (!fmm_pass(c, LEAF_DIPOLE_E, false, c->d, nullptr, c->Td, nullptr, true, true)) {
         LaunchScope ls(c, F_SOLVER);
         pcg_ad_kernel<<<kRedBlocks, kRedThreads, 0, c->stream>>>(c->n, c->alpha_s, c->d, c->Td, c->Ad, c->partial,
-                                                                  c->scal, c->ticket);
+                                                                  c->scal, c->ticket, cond);
     }
     {
         LaunchScope ls(c, F_SOLVER);
         pcg_update_kernel<<<kRedBlocks, kRedThreads, 0, c->stream>>>(c->n, c->alpha_s, c->scal, c->d, c->Ad, c->mu,
-                                                                      c->r, c->z, c->partial, c->ticket);
+                                                                      c->r, c->z, c->partial, c->ticket, cond);
     }
     {
         LaunchScope ls(c, F_SOLVER);
@@ -384,6 +405,11 @@ void solver_pcg_step(polfmm_ctx* c) {
             pcg_direction_kernel<double><<<grid_for(c->n, 256), 256, 0, c->stream>>>(c->n, c->scal, c->z, c->d,
                                                                                      c->srcB);
     }
+}
+
+void solver_loop_setup(polfmm_ctx* c, double tol, int max_iter) {
+    LaunchScope ls(c, F_SOLVER);
+    loop_setup_kernel<<<1, 1, 0, c->stream>>>(c->scal, tol, (double)max_iter);
 }
 
 void solver_jacobi_step(polfmm_ctx* c) {
