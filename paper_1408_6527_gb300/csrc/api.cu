@@ -161,6 +161,15 @@ int build_tables(polfmm_ctx* c) {
         }
         for (int j = 0; j < pre[k]; j++) add[(size_t)k * nc + j] = (short)t.at(t.nx[k] + t.nx[j], t.ny[k] + t.ny[j], t.nz[k] + t.nz[j]);
     }
+    // the device code locates multi-indices by formula; the order must agree
+    for (int k = 0; k < nc; k++)
+        if (mi_index(t.nx[k], t.ny[k], t.nz[k]) != k) return POLFMM_ERR_INVALID_ARG;
+    std::vector<double> w4(kMaxP + 1), rinv(kMaxP + 1, 0.0);
+    for (int k = 0; k <= kMaxP; k++) {
+        w4[k] = ldexp(1.0, -2 * k) / factorial(k);
+        if (k > 0) rinv[k] = 1.0 / k;
+    }
+    std::vector<float> w4f(w4.begin(), w4.end()), rinvf(rinv.begin(), rinv.end());
     // derivative tables at the integer offsets of [-3, 3]^3
     std::vector<double> D((size_t)343 * nc, 0.0);
     std::vector<float> Df((size_t)343 * nc, 0.f);
@@ -214,6 +223,10 @@ int build_tables(polfmm_ctx* c) {
     UP(pre, T.pre);
     UP(add, T.add);
     UP(dn1, T.dn1);
+    UP(w4, T.w4);
+    UP(w4f, T.w4f);
+    UP(rinv, T.rinv);
+    UP(rinvf, T.rinvf);
     UP(D, T.D);
     UP(Df, T.Df);
     UP(class_off, T.class_off);
@@ -225,8 +238,9 @@ int build_tables(polfmm_ctx* c) {
 }
 
 void free_tables(Tables& T) {
-    void* ptrs[] = {T.mi, T.inv_fact, T.inv_fact_f, T.up1, T.dn1, T.up2, T.pre, T.add, T.D, T.Df, T.class_off,
-                    T.warp_out_ptr, T.warp_out};
+    void* ptrs[] = {T.mi,   T.inv_fact, T.inv_fact_f, T.up1,  T.dn1, T.w4,        T.w4f,        T.rinv,
+                    T.rinvf, T.up2,     T.pre,        T.add,  T.D,   T.Df,        T.class_off,  T.warp_out_ptr,
+                    T.warp_out};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     T = Tables();
@@ -317,6 +331,9 @@ int allocate(polfmm_ctx* c) {
     c->leaf_partial = A.get<double>(c->lv[c->depth].cap);
     c->lcount = A.get<int>(c->lv[c->depth].cap);
     c->leaf_order = A.get<int>(c->lv[c->depth].cap);
+    c->leaf_items_cap = (int)std::min<int64_t>((int64_t)c->lv[c->depth].cap + n / kLeafTargets + 1, 2 * n + 1);
+    c->leaf_items = A.get<int2>(c->leaf_items_cap);
+    c->leaf_nitems = A.get<int>(4);
     if (!A.ok) return POLFMM_ERR_OUT_OF_MEMORY;
     if (cudaMallocHost(&c->h_scal, sizeof(double) * (S_COUNT + 8)) != cudaSuccess) return POLFMM_ERR_OUT_OF_MEMORY;
     if (cudaMallocHost(&c->h_counts, sizeof(int) * (kMaxDepth + 1) * 9) != cudaSuccess) return POLFMM_ERR_OUT_OF_MEMORY;
@@ -433,9 +450,17 @@ int rebuild(polfmm_ctx* c) {
 
 // Capture one PCG iteration (FMM dipole-field pass + vector updates) as a CUDA
 // graph on a private stream; later trees update the executable in place.
+// graphs are captured on a private stream of the highest priority; captured
+// kernels keep their stream's priority and the graphs are instantiated to use it
+cudaError_t create_capture_stream(polfmm_ctx* c) {
+    int lo = 0, hi = 0;
+    cudaDeviceGetStreamPriorityRange(&lo, &hi);
+    return cudaStreamCreateWithPriority(&c->cap_stream, cudaStreamNonBlocking, hi);
+}
+
 int capture_pcg_graph(polfmm_ctx* c) {
     if (!c->cap_stream &&
-        cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+        create_capture_stream(c) != cudaSuccess)
         return POLFMM_ERR_CUDA;
     cudaStream_t orig = c->stream;
     const int64_t l0 = c->launches;
@@ -461,7 +486,7 @@ int capture_pcg_graph(polfmm_ctx* c) {
             c->pcg_graph = nullptr;
         }
     }
-    if (!c->pcg_graph && cudaGraphInstantiate(&c->pcg_graph, g, 0) != cudaSuccess) {
+    if (!c->pcg_graph && cudaGraphInstantiate(&c->pcg_graph, g, cudaGraphInstantiateFlagUseNodePriority) != cudaSuccess) {
         cudaGetLastError();
         c->pcg_graph = nullptr;
         cudaGraphDestroy(g);
@@ -489,8 +514,7 @@ int prepare_loop_graph(polfmm_ctx* c) {
         c->loop_failed = true;
         return POLFMM_ERR_CUDA;
     };
-    if (!c->cap_stream && cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
-        return fail();
+    if (!c->cap_stream && create_capture_stream(c) != cudaSuccess) return fail();
     if (!c->loop_g) {
         if (cudaGraphCreate(&c->loop_g, 0) != cudaSuccess) return fail();
         if (cudaGraphConditionalHandleCreate(&c->loop_cond, c->loop_g, 1, cudaGraphCondAssignDefault) != cudaSuccess)
@@ -535,7 +559,9 @@ int prepare_loop_graph(polfmm_ctx* c) {
             c->loop_exec = nullptr;
         }
     }
-    if (!c->loop_exec && cudaGraphInstantiate(&c->loop_exec, c->loop_g, 0) != cudaSuccess) return fail();
+    if (!c->loop_exec &&
+        cudaGraphInstantiate(&c->loop_exec, c->loop_g, cudaGraphInstantiateFlagUseNodePriority) != cudaSuccess)
+        return fail();
     c->loop_dirty = false;
     return POLFMM_OK;
 }
@@ -653,7 +679,11 @@ int fmm_build(polfmm_ctx** out, int64_t n, const double* positions, const double
         for (int i = 0; i < 2 * 4096; i++) cudaEventCreate(&c->ev_pool[i]);
         c->ev_created = true;
     }
-    if (cudaStreamCreateWithFlags(&c->side_stream, cudaStreamNonBlocking) != cudaSuccess ||
+    // the near-field pairs run at the lowest priority: their blocks fill the SMs
+    // that the far-field chain (the critical path) leaves free
+    int prio_lo = 0, prio_hi = 0;
+    cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
+    if (cudaStreamCreateWithPriority(&c->side_stream, cudaStreamNonBlocking, prio_lo) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess) {
         cudaGetLastError();

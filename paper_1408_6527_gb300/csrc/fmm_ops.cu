@@ -42,24 +42,23 @@ __device__ inline double pow2neg<double>(int s) {
     return __longlong_as_double((long long)(1023 - s) << 52);
 }
 
-// W[k] = 4^-k / k!, the 1-D weights of a shift by a quarter of the parent side
+// table of the arithmetic type R from its double / float copies
 template <typename R>
-__device__ inline void shift_weights(R* W, int p) {
-    if ((int)threadIdx.x <= p) {
-        double w = 1.0;
-        for (int k = 1; k <= (int)threadIdx.x; k++) w *= 0.25 / k;
-        W[threadIdx.x] = R(w);
-    }
+__host__ __device__ inline const R* pick(const double* d, const float* f);
+template <>
+__host__ __device__ inline const double* pick<double>(const double* d, const float*) {
+    return d;
+}
+template <>
+__host__ __device__ inline const float* pick<float>(const double*, const float* f) {
+    return f;
 }
 
-// TF32 high part (round to nearest, ties away) and residual of v
-__device__ inline void tf32_split(float v, float& hi, float& lo) {
-    uint32_t h;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(v));
-    hi = __uint_as_float(h);
-    lo = v - hi;
+// copies the first p + 1 entries of a small table into shared memory
+template <typename R>
+__device__ inline void stage_small(R* dst, const R* __restrict__ src, int p) {
+    if ((int)threadIdx.x <= p) dst[threadIdx.x] = src[threadIdx.x];
 }
-__device__ inline void tf32_split(double, float& hi, float& lo) { hi = lo = 0.f; }
 
 // ---------------------------------------------------------------------------
 // upward pass: P2M of every leaf, then M2M up to level 2 inside the same
@@ -76,11 +75,10 @@ __device__ inline void tf32_split(double, float& hi, float& lo) { hi = lo = 0.f;
 //   m^P_n = sum_{k <= n} prod_d (s_d/4)^k_d / k_d!  2^-|n-k| m^C_{n-k},
 // s_d = -1 where the child bit b_d is 1.  The kernel applies it as three
 // one-axis convolutions (exact: the truncation k <= n is a box).
-// With `hi` set (tensor-core M2L), every multipole row of levels >= 2 is also
-// stored as a TF32 high part plus residual.
 // ---------------------------------------------------------------------------
 constexpr int kP2MChunk = 64;
-constexpr int kUpThreads = 128;
+constexpr int kUpThreads = 256;
+constexpr int kUpMaxSlices = 8;
 
 struct UpPtrs {
     void* M[kMaxDepth + 1];
@@ -89,101 +87,113 @@ struct UpPtrs {
     const int* nchild[kMaxDepth + 1];
     const int* key[kMaxDepth + 1];
     int* arrive[kMaxDepth + 1];
-    float* hi[kMaxDepth + 1];
-    float* lo[kMaxDepth + 1];
-    int KP;
 };
 
 template <typename R>
 __host__ __device__ inline size_t upward_smem_bytes(int ncoef) {
-    return sizeof(R) * 16 * (size_t)ncoef + sizeof(int) * 4 * (size_t)ncoef;
+    return sizeof(R) * 16 * (size_t)ncoef + sizeof(int) * (size_t)ncoef;
 }
 
 template <typename R>
 __device__ inline void store_multipole(const UpPtrs& up, int l, int box, int cc, R v, int ld) {
     reinterpret_cast<R*>(up.M[l])[(int64_t)box * ld + cc] = v;
-    if (up.hi[l]) {
-        float h, lo;
-        tf32_split(v, h, lo);
-        up.hi[l][(int64_t)box * up.KP + cc] = h;
-        up.lo[l][(int64_t)box * up.KP + cc] = lo;
-    }
 }
+
+// per-site factors of the P2M sum, axis a, order k (P_a[-1] = 0):
+//   P_a[k] = v_a^k / k!,  D_a[k] = (mu_a / h) P_a[k-1],  A_x[k] = q P_x[k] - D_x[k]
+// so that m_n = sum_i A_x[nx] P_y[ny] P_z[nz] - P_x[nx] (D_y[ny] P_z[nz] + P_y[ny] D_z[nz])
+enum { F_PX = 0, F_PY, F_PZ, F_AX, F_DY, F_DZ, F_NUM };
 
 template <typename R>
 __global__ void __launch_bounds__(kUpThreads) upward_kernel(
     int nleaf, int depth, const int* __restrict__ lstart, const int* __restrict__ lcount,
     const R* __restrict__ ploc, const double* __restrict__ q, const double* __restrict__ mu, UpPtrs up, int ld,
-    int ncoef, int p, const int* __restrict__ mi, const int* __restrict__ dn1, R inv_h) {
+    int ncoef, int p, const int* __restrict__ mi, const R* __restrict__ w4, const R* __restrict__ rinv, R inv_h) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    R* S = reinterpret_cast<R*>(smem_raw);         // [8][ncoef] children, then ping-pong
+    R* S = reinterpret_cast<R*>(smem_raw);         // [8][ncoef] children (and slice partials of P2M)
     R* T = S + 8 * ncoef;                           // [8][ncoef]
-    int* sdn = reinterpret_cast<int*>(T + 8 * ncoef);  // [ncoef][3] index of n - e_d
-    int* sdeg = sdn + 3 * ncoef;                    // [ncoef] |n|
-    // P[site][axis][k + 1] = v^k / k!, v = -(x - z) / h, P[.][.][0] = 0
-    __shared__ R P[kP2MChunk][3][kMaxP + 2];
-    __shared__ R sq[kP2MChunk];
-    __shared__ R sm[kP2MChunk][3];
+    int* smi = reinterpret_cast<int*>(T + 8 * ncoef);  // [ncoef] packed multi-indices
+    __shared__ R fac[kP2MChunk][F_NUM][kMaxP + 1];
     __shared__ R W[kMaxP + 1];
+    __shared__ R RI[kMaxP + 1];
     __shared__ int s_oct[8];
     __shared__ int s_next;
     const int b = blockIdx.x;
     if (b >= nleaf) return;
     const int tid = threadIdx.x;
-    for (int cc = tid; cc < ncoef; cc += kUpThreads) {
-        sdn[3 * cc] = dn1[3 * cc];
-        sdn[3 * cc + 1] = dn1[3 * cc + 1];
-        sdn[3 * cc + 2] = dn1[3 * cc + 2];
-        sdeg[cc] = mi[cc] >> 24;
-    }
-    shift_weights(W, p);
+    for (int cc = tid; cc < ncoef; cc += kUpThreads) smi[cc] = mi[cc];
+    stage_small(W, w4, p);
+    stage_small(RI, rinv, p);
 
-    // P2M of leaf b
-    const int s0 = lstart[b], cnt = lcount[b];
+    // P2M of leaf b: thread (coefficient c, slice sl) sums the sites sl, sl + slices, ...
+    const int slices = ncoef <= kUpThreads ? min(kUpMaxSlices, kUpThreads / ncoef) : 1;
+    const int sl = ncoef <= kUpThreads ? tid / ncoef : 0;
+    const int c_first = ncoef <= kUpThreads ? tid - sl * ncoef : tid;
+    const bool worker = sl < slices;
     constexpr int CPT = (286 + kUpThreads - 1) / kUpThreads;  // coefficients per thread (p <= 10)
     R acc[CPT];
+    int nx[CPT], ny[CPT], nz[CPT];
 #pragma unroll
-    for (int k = 0; k < CPT; k++) acc[k] = R(0);
-    int pk[CPT];
-#pragma unroll
-    for (int k = 0; k < CPT; k++) pk[k] = tid + k * kUpThreads < ncoef ? mi[tid + k * kUpThreads] : 0;
+    for (int k = 0; k < CPT; k++) {
+        acc[k] = R(0);
+        const int cc = c_first + k * kUpThreads;
+        const int pk = worker && cc < ncoef ? mi[cc] : 0;
+        nx[k] = pk & 0xff;
+        ny[k] = (pk >> 8) & 0xff;
+        nz[k] = (pk >> 16) & 0xff;
+    }
+    const int s0 = lstart[b], cnt = lcount[b];
     for (int k0 = 0; k0 < cnt; k0 += kP2MChunk) {
         const int m = min(kP2MChunk, cnt - k0);
         __syncthreads();
         if (tid < m) {
             const int i = s0 + k0 + tid;
+            const R qi = q ? R(q[i]) : R(0);
             for (int a = 0; a < 3; a++) {
                 const R v = -ploc[3 * i + a] * inv_h;
-                R t = R(1);
-                P[tid][a][0] = R(0);
-                P[tid][a][1] = t;
-                for (int k = 1; k <= p; k++) {
-                    t = t * v / R(k);
-                    P[tid][a][k + 1] = t;
+                const R ma = mu ? R(mu[3 * i + a]) * inv_h : R(0);
+                R t = R(1), prev = R(0);
+                for (int k = 0; k <= p; k++) {
+                    if (k > 0) t = t * v * RI[k];
+                    const R dk = ma * prev;  // (mu_a / h) P_a[k-1]
+                    fac[tid][F_PX + a][k] = t;
+                    if (a == 0) fac[tid][F_AX][k] = qi * t - dk;
+                    if (a == 1) fac[tid][F_DY][k] = dk;
+                    if (a == 2) fac[tid][F_DZ][k] = dk;
+                    prev = t;
                 }
-                sm[tid][a] = mu ? R(mu[3 * i + a]) * inv_h : R(0);
             }
-            sq[tid] = q ? R(q[i]) : R(0);
         }
         __syncthreads();
+        if (!worker) continue;
 #pragma unroll
         for (int k = 0; k < CPT; k++) {
-            if (tid + k * kUpThreads >= ncoef) continue;
-            const int nx = pk[k] & 0xff, ny = (pk[k] >> 8) & 0xff, nz = (pk[k] >> 16) & 0xff;
+            if (c_first + k * kUpThreads >= ncoef) continue;
+            const int x = nx[k], y = ny[k], z = nz[k];
             R a = acc[k];
-            for (int s = 0; s < m; s++) {
-                const R px = P[s][0][nx + 1], py = P[s][1][ny + 1], pz = P[s][2][nz + 1];
-                a += sq[s] * px * py * pz;
-                a -= sm[s][0] * P[s][0][nx] * py * pz + sm[s][1] * px * P[s][1][ny] * pz +
-                     sm[s][2] * px * py * P[s][2][nz];
+            for (int s = sl; s < m; s += slices) {
+                const R(*F)[kMaxP + 1] = fac[s];
+                const R pz = F[F_PZ][z], py = F[F_PY][y];
+                a += F[F_AX][x] * py * pz - F[F_PX][x] * (F[F_DY][y] * pz + py * F[F_DZ][z]);
             }
             acc[k] = a;
         }
     }
+    if (slices > 1) {
+        // slice partials through shared memory, added in slice order
+        if (worker && c_first < ncoef) S[sl * ncoef + c_first] = acc[0];
+        __syncthreads();
+        for (int cc = tid; cc < ncoef; cc += kUpThreads) {
+            R a = R(0);
+            for (int u = 0; u < slices; u++) a += S[u * ncoef + cc];
+            store_multipole(up, depth, b, cc, a, ld);
+        }
+    } else {
 #pragma unroll
-    for (int k = 0; k < CPT; k++) {
-        const int cc = tid + k * kUpThreads;
-        if (cc < ncoef) store_multipole(up, depth, b, cc, acc[k], ld);
+        for (int k = 0; k < CPT; k++) {
+            const int cc = c_first + k * kUpThreads;
+            if (worker && cc < ncoef) store_multipole(up, depth, b, cc, acc[k], ld);
+        }
     }
 
     // M2M: climb while this block completes the last child of the parent
@@ -210,10 +220,10 @@ __global__ void __launch_bounds__(kUpThreads) upward_kernel(
         const R* Mc = reinterpret_cast<const R*>(up.M[l]);
         for (int idx = tid; idx < nc * ncoef; idx += kUpThreads) {
             const int j = idx / ncoef, cc = idx - j * ncoef;
-            S[j * ncoef + cc] = __ldcg(Mc + (int64_t)(c0 + j) * ld + cc) * pow2neg<R>(sdeg[cc]);
+            S[j * ncoef + cc] = __ldcg(Mc + (int64_t)(c0 + j) * ld + cc) * pow2neg<R>(smi[cc] >> 24);
         }
         __syncthreads();
-        // g_n = sum_k (s/4)^k/k! m_{n - k e_d}, along x (S -> T), y (T -> S), z (S -> T)
+        // g_n = sum_{k <= n_d} (s/4)^k/k! m_{n - k e_d}, along x (S -> T), y (T -> S), z (S -> T)
         for (int ax = 0; ax < 3; ax++) {
             const R* src = ax == 1 ? T : S;
             R* dst = ax == 1 ? S : T;
@@ -221,12 +231,13 @@ __global__ void __launch_bounds__(kUpThreads) upward_kernel(
                 const int j = idx / ncoef, cc = idx - j * ncoef;
                 const bool neg = (s_oct[j] >> ax) & 1;
                 const R* row = src + j * ncoef;
+                const int pk = smi[cc];
+                const int x = pk & 0xff, y = (pk >> 8) & 0xff, z = (pk >> 16) & 0xff;
+                const int ex = ax == 0, ey = ax == 1, ez = ax == 2;
+                const int kmax = ex * x + ey * y + ez * z;
                 R a = row[cc];
-                int i = cc;
-                for (int k = 1; k <= kMaxP; k++) {
-                    i = sdn[3 * i + ax];
-                    if (i < 0) break;
-                    const R v = W[k] * row[i];
+                for (int k = 1; k <= kmax; k++) {
+                    const R v = W[k] * row[mi_index(x - k * ex, y - k * ey, z - k * ez)];
                     a += (neg && (k & 1)) ? -v : v;
                 }
                 dst[j * ncoef + cc] = a;
@@ -254,74 +265,74 @@ __global__ void __launch_bounds__(kUpThreads) upward_kernel(
 // ---------------------------------------------------------------------------
 struct DownPtrs {
     const void* Lp[kMaxDepth + 1];
-    const int* parent[kMaxDepth + 1];
+    const int* map[kMaxDepth + 1];  // Morton key -> slot
     const int* key[kMaxDepth + 1];
     int cap[kMaxDepth + 1];
-    int depth, nchunk;
+    int depth, nchunk, p;
 };
 
+// one L2L pass along axis ax: a_n = sum_{k <= p - |n|} (t/4)^k... with sign
+// (-1)^k where the shift is negative; indices by formula, so the loads are independent
 template <typename R>
-__device__ inline R shift_up_axis(const R* src, int cc, int ax, bool neg, const int* cinfo, const R* W) {
+__device__ inline R shift_up_axis(const R* src, int cc, int pk, int ax, bool neg, const R* W, int p) {
+    const int x = pk & 0xff, y = (pk >> 8) & 0xff, z = (pk >> 16) & 0xff;
+    const int ex = ax == 0, ey = ax == 1, ez = ax == 2;
+    const int kmax = p - (pk >> 24);
     R a = src[cc];
-    int i = cc;
-    for (int k = 1; k <= kMaxP; k++) {
-        i = cinfo[4 * i + 1 + ax];
-        if (i < 0) break;
-        const R v = W[k] * src[i];
+    for (int k = 1; k <= kmax; k++) {
+        const R v = W[k] * src[mi_index(x + k * ex, y + k * ey, z + k * ez)];
         a += (neg && (k & 1)) ? -v : v;
     }
     return a;
 }
 
-// all threads of the block call it; f, t0, t1: ncoef each in shared memory
+// all threads of the block call it; f, t0, t1: ncoef each, psum: (depth - 1)
+// x ncoef, all in shared memory; cinfo[4 c] = packed multi-index of c.  The
+// ancestors come from the leaf's Morton key, the M2L partials of all of them
+// are read first (independent loads), then the shifts run down the chain.
 template <typename R, int NT>
-__device__ void far_locals(const DownPtrs& dp, int b, R* f, R* t0, R* t1, const int* cinfo, const R* W, int ncoef,
-                           int ld) {
+__device__ void far_locals(const DownPtrs& dp, int b, R* f, R* t0, R* t1, R* psum, const int* cinfo, const R* W,
+                           int ncoef, int ld) {
     __shared__ int chain[kMaxDepth + 1];
     __shared__ int coct[kMaxDepth + 1];
     const int tid = threadIdx.x;
     const int d = dp.depth;
-    if (tid == 0) {
-        int s = b;
-        for (int l = d; l >= 2; l--) {
-            chain[l] = s;
-            coct[l] = dp.key[l][s] & 7;
-            if (l > 2) s = dp.parent[l][s];
-        }
+    if (tid >= 2 && tid <= d) {
+        const uint32_t k = (uint32_t)dp.key[d][b] >> (3 * (d - tid));
+        chain[tid] = tid == d ? b : dp.map[tid][k];
+        coct[tid] = k & 7;
     }
     __syncthreads();
-    constexpr int CPT = (286 + NT - 1) / NT;
-    for (int l = 2; l <= d; l++) {
-        const R* lp = reinterpret_cast<const R*>(dp.Lp[l]) + (int64_t)chain[l] * ld;
-        const int64_t cs = (int64_t)dp.cap[l] * ld;
-        R ps[CPT];
+    const int nchunk = dp.nchunk;
+    for (int it = tid; it < (d - 1) * ncoef; it += NT) {
+        const int li = it / ncoef, cc = it - li * ncoef;
+        const R* lp = reinterpret_cast<const R*>(dp.Lp[2 + li]) + (int64_t)chain[2 + li] * ld + cc;
+        const int64_t cs = (int64_t)dp.cap[2 + li] * ld;
+        R a = R(0);
+        int ch = 0;
+        for (; ch + 8 <= nchunk; ch += 8) {
+            R v[8];
 #pragma unroll
-        for (int k = 0; k < CPT; k++) {
-            const int cc = tid + k * NT;
-            R a = R(0);
-            if (cc < ncoef) {
-#pragma unroll 4
-                for (int ch = 0; ch < dp.nchunk; ch++) a += lp[ch * cs + cc];
-            }
-            ps[k] = a;
+            for (int k = 0; k < 8; k++) v[k] = lp[(ch + k) * cs];
+#pragma unroll
+            for (int k = 0; k < 8; k++) a += v[k];
         }
-        if (l > 2) {
-            const int oct = coct[l];
-            for (int cc = tid; cc < ncoef; cc += NT) t0[cc] = shift_up_axis(f, cc, 0, !(oct & 1), cinfo, W);
-            __syncthreads();
-            for (int cc = tid; cc < ncoef; cc += NT) t1[cc] = shift_up_axis(t0, cc, 1, !(oct & 2), cinfo, W);
-            __syncthreads();
-#pragma unroll
-            for (int k = 0; k < CPT; k++) {
-                const int cc = tid + k * NT;
-                if (cc < ncoef)
-                    ps[k] += pow2neg<R>((cinfo[4 * cc] >> 24) + 1) * shift_up_axis(t1, cc, 2, !(oct & 4), cinfo, W);
-            }
-        }
-#pragma unroll
-        for (int k = 0; k < CPT; k++) {
-            const int cc = tid + k * NT;
-            if (cc < ncoef) f[cc] = ps[k];
+        for (; ch < nchunk; ch++) a += lp[ch * cs];
+        psum[it] = a;
+    }
+    __syncthreads();
+    for (int cc = tid; cc < ncoef; cc += NT) f[cc] = psum[cc];
+    __syncthreads();
+    for (int l = 3; l <= d; l++) {
+        const int oct = coct[l];
+        for (int cc = tid; cc < ncoef; cc += NT) t0[cc] = shift_up_axis(f, cc, cinfo[4 * cc], 0, !(oct & 1), W, dp.p);
+        __syncthreads();
+        for (int cc = tid; cc < ncoef; cc += NT) t1[cc] = shift_up_axis(t0, cc, cinfo[4 * cc], 1, !(oct & 2), W, dp.p);
+        __syncthreads();
+        const R* pl = psum + (l - 2) * ncoef;
+        for (int cc = tid; cc < ncoef; cc += NT) {
+            const int pk = cinfo[4 * cc];
+            f[cc] = pl[cc] + pow2neg<R>((pk >> 24) + 1) * shift_up_axis(t1, cc, pk, 2, !(oct & 4), W, dp.p);
         }
         __syncthreads();
     }
@@ -446,12 +457,12 @@ __device__ inline double rsqrt_pos(double r2) { return r2 > 0.0 ? rsqrt(r2) : 0.
 
 // dynamic shared memory of leaf_kernel<R, MODE>
 template <typename R, int MODE>
-__host__ __device__ inline size_t leaf_smem_bytes(int ncoef) {
+__host__ __device__ inline size_t leaf_smem_bytes(int ncoef, int depth) {
     constexpr int CAP = LeafCap<R>::N;
     size_t b = sizeof(Q4<R>) * CAP;                          // positions + charge
     if (MODE != LEAF_CHARGE_PHI_E) b += sizeof(Q4<R>) * CAP;  // dipoles
     if (MODE == LEAF_CHARGE_PHI_E) b += sizeof(int) * CAP;    // source index (coincidence check)
-    b += sizeof(R) * 4 * (size_t)ncoef;                      // locals, two shift buffers, 1/n!
+    b += sizeof(R) * (4 + (size_t)(depth > 1 ? depth - 1 : 0)) * ncoef;  // locals, shift buffers, 1/n!, partials
     b += sizeof(int) * 4 * (size_t)ncoef;                     // packed n, n + e_d
     if (MODE == LEAF_FULL) b += sizeof(int) * 6 * (size_t)ncoef;
     return b;
@@ -474,10 +485,12 @@ __global__ void pack_dipoles_kernel(int64_t n, const double* __restrict__ mu, Q4
 
 template <typename R, int MODE>
 __global__ void __launch_bounds__(kLeafThreads) leaf_kernel(
-    int nleaf, const int* __restrict__ lkey, const int* __restrict__ lstart, const int* __restrict__ lcount,
-    const int* __restrict__ lmap, const int* __restrict__ order, int depth, const Q4<R>* __restrict__ srcA,
+    const int2* __restrict__ items, const int* __restrict__ nitems, const int* __restrict__ lkey,
+    const int* __restrict__ lstart, const int* __restrict__ lcount, const int* __restrict__ lmap, int depth,
+    const Q4<R>* __restrict__ srcA,
     const Q4<R>* __restrict__ srcB, DownPtrs dp, int ld, int ncoef, int p, const int* __restrict__ mi,
-    const double* __restrict__ inv_fact, const int* __restrict__ up1, const int* __restrict__ up2, R h,
+    const double* __restrict__ inv_fact, const int* __restrict__ up1, const int* __restrict__ up2,
+    const R* __restrict__ w4, R h,
     double* __restrict__ out_phi, double* __restrict__ out_E, double* __restrict__ out_G, int* __restrict__ err,
     int far) {
     constexpr int NC = LeafOut<MODE>::NC;
@@ -502,15 +515,18 @@ __global__ void __launch_bounds__(kLeafThreads) leaf_kernel(
     R* ifact = t1 + ncoef;
     int* cinfo = reinterpret_cast<int*>(ifact + ncoef);  // [ncoef][4]: packed n, n+e_x, n+e_y, n+e_z
     int* cup2 = cinfo + 4 * ncoef;                       // [ncoef][6] (FULL only)
+    R* psum = reinterpret_cast<R*>(cup2 + (HAS_G ? 6 * ncoef : 0));  // [depth - 1][ncoef]
     __shared__ R W[kMaxP + 1];
     __shared__ int nb_start[27];
     __shared__ int nb_pre[28];
     __shared__ R nb_shift[27][3];
     __shared__ R part[NC][kLeafThreads];
 
-    if ((int)blockIdx.x >= nleaf) return;
-    const int b = order[blockIdx.x];
+    if ((int)blockIdx.x >= *nitems) return;
+    const int2 item = items[blockIdx.x];
+    const int b = item.x;
     const int s0 = lstart[b], cnt = lcount[b];
+    const int t_lo = item.y, t_hi = min(cnt, item.y + kLeafTargets);  // this block's targets
     const int tid = threadIdx.x;
     if (tid < 32) {
         int c = 0;
@@ -544,21 +560,21 @@ __global__ void __launch_bounds__(kLeafThreads) leaf_kernel(
         if (HAS_G)
             for (int k = 0; k < 6; k++) cup2[6 * cc + k] = up2[6 * cc + k];
     }
-    shift_weights(W, p);
+    stage_small(W, w4, p);
     __syncthreads();
-    if (far) far_locals<R, kLeafThreads>(dp, b, f, t0, t1, cinfo, W, ncoef, ld);
+    if (far) far_locals<R, kLeafThreads>(dp, b, f, t0, t1, psum, cinfo, W, ncoef, ld);
     const int total = nb_pre[27];
     const R inv_h = R(1) / h;
 
-    for (int tg = 0; tg < cnt; tg += kLeafThreads) {
-        const int nt = min(kLeafThreads, cnt - tg);
+    for (int tg = t_lo; tg < t_hi; tg += kLeafThreads) {
+        const int nt = min(kLeafThreads, t_hi - tg);
         const int slices = kLeafThreads / nt;
         const int t = tid % nt, s = tid / nt;
         const bool active = s < slices;
         const int i = s0 + tg + t;
-        R acc[NC];
+        R acc[NC], acc2[NC];
 #pragma unroll
-        for (int k = 0; k < NC; k++) acc[k] = R(0);
+        for (int k = 0; k < NC; k++) acc[k] = acc2[k] = R(0);
         R xi = R(0), yi = R(0), zi = R(0);
         if (active) {
             const Q4<R> me = srcA[i];
@@ -625,8 +641,9 @@ __global__ void __launch_bounds__(kLeafThreads) leaf_kernel(
             }
             __syncthreads();
             if (!active) continue;
-#pragma unroll 4
-            for (int jj = s; jj < m; jj += slices) {
+            // two independent accumulator sets (sources jj and jj + slices) for
+            // instruction-level parallelism; added in fixed order after the loop
+            auto pair = [&](R* ac, const int jj) {
                 const Q4<R> a = sA[jj];
                 const R rx = xi - a.x, ry = yi - a.y, rz = zi - a.z;
                 const R r2 = rx * rx + ry * ry + rz * rz;
@@ -637,18 +654,18 @@ __global__ void __launch_bounds__(kLeafThreads) leaf_kernel(
                 if (SRC_Q) {
                     const R qj = a.w;
                     const R qr3 = qj * ri3;
-                    if (HAS_PHI) acc[0] += qj * ri;
-                    acc[IE + 0] += qr3 * rx;
-                    acc[IE + 1] += qr3 * ry;
-                    acc[IE + 2] += qr3 * rz;
+                    if (HAS_PHI) ac[0] += qj * ri;
+                    ac[IE + 0] += qr3 * rx;
+                    ac[IE + 1] += qr3 * ry;
+                    ac[IE + 2] += qr3 * rz;
                     if (HAS_G) {
                         const R t5 = R(3) * qr3 * ri2;
-                        acc[IG + 0] += qr3 - t5 * rx * rx;
-                        acc[IG + 1] -= t5 * rx * ry;
-                        acc[IG + 2] -= t5 * rx * rz;
-                        acc[IG + 3] += qr3 - t5 * ry * ry;
-                        acc[IG + 4] -= t5 * ry * rz;
-                        acc[IG + 5] += qr3 - t5 * rz * rz;
+                        ac[IG + 0] += qr3 - t5 * rx * rx;
+                        ac[IG + 1] -= t5 * rx * ry;
+                        ac[IG + 2] -= t5 * rx * rz;
+                        ac[IG + 3] += qr3 - t5 * ry * ry;
+                        ac[IG + 4] -= t5 * ry * rz;
+                        ac[IG + 5] += qr3 - t5 * rz * rz;
                     }
                 }
                 if (SRC_MU) {
@@ -656,24 +673,33 @@ __global__ void __launch_bounds__(kLeafThreads) leaf_kernel(
                     const R mr = mv.x * rx + mv.y * ry + mv.z * rz;
                     const R ri5 = ri3 * ri2;
                     const R a3 = R(3) * mr * ri5;
-                    if (HAS_PHI) acc[0] += mr * ri3;
-                    acc[IE + 0] += a3 * rx - mv.x * ri3;
-                    acc[IE + 1] += a3 * ry - mv.y * ri3;
-                    acc[IE + 2] += a3 * rz - mv.z * ri3;
+                    if (HAS_PHI) ac[0] += mr * ri3;
+                    ac[IE + 0] += a3 * rx - mv.x * ri3;
+                    ac[IE + 1] += a3 * ry - mv.y * ri3;
+                    ac[IE + 2] += a3 * rz - mv.z * ri3;
                     if (HAS_G) {
                         // G_de = 3 (mu_d r_e + mu_e r_d + mr delta_de) / r^5 - 15 mr r_d r_e / r^7
                         const R t5 = R(3) * ri5;
                         const R t7 = R(5) * a3 * ri2;
-                        acc[IG + 0] += t5 * (R(2) * mv.x * rx + mr) - t7 * rx * rx;
-                        acc[IG + 1] += t5 * (mv.x * ry + mv.y * rx) - t7 * rx * ry;
-                        acc[IG + 2] += t5 * (mv.x * rz + mv.z * rx) - t7 * rx * rz;
-                        acc[IG + 3] += t5 * (R(2) * mv.y * ry + mr) - t7 * ry * ry;
-                        acc[IG + 4] += t5 * (mv.y * rz + mv.z * ry) - t7 * ry * rz;
-                        acc[IG + 5] += t5 * (R(2) * mv.z * rz + mr) - t7 * rz * rz;
+                        ac[IG + 0] += t5 * (R(2) * mv.x * rx + mr) - t7 * rx * rx;
+                        ac[IG + 1] += t5 * (mv.x * ry + mv.y * rx) - t7 * rx * ry;
+                        ac[IG + 2] += t5 * (mv.x * rz + mv.z * rx) - t7 * rx * rz;
+                        ac[IG + 3] += t5 * (R(2) * mv.y * ry + mr) - t7 * ry * ry;
+                        ac[IG + 4] += t5 * (mv.y * rz + mv.z * ry) - t7 * ry * rz;
+                        ac[IG + 5] += t5 * (R(2) * mv.z * rz + mr) - t7 * rz * rz;
                     }
                 }
+            };
+            int jj = s;
+#pragma unroll 2
+            for (; jj + slices < m; jj += 2 * slices) {
+                pair(acc, jj);
+                pair(acc2, jj + slices);
             }
+            if (jj < m) pair(acc, jj);
         }
+#pragma unroll
+        for (int k = 0; k < NC; k++) acc[k] += acc2[k];
         // fixed-order reduction over slices
         __syncthreads();
 #pragma unroll
@@ -703,6 +729,7 @@ __global__ void __launch_bounds__(kLeafThreads) leaf_kernel(
 // and the leaf's partial of d.Ad; the last block to finish adds the partials
 // of all leaves in leaf order into scal[S_DAD] (deterministic).
 constexpr int kL2PThreads = 128;
+constexpr int kPowStride = 3 * kMaxP + 1;  // odd: the per-thread rows hit distinct banks
 
 struct PcgFuse {
     const double* alpha;
@@ -714,18 +741,31 @@ struct PcgFuse {
     cudaGraphConditionalHandle cond;  // inside the solve graph: cleared here, set by the update kernel
 };
 
+// f, t0, t1 and the partials of depth - 1 levels, each padded to ld (a
+// multiple of 4) so that the int4 rows of cinfo after them stay 16-byte aligned
+template <typename R>
+__host__ __device__ inline size_t l2p_smem_bytes(int ld, int depth) {
+    return sizeof(R) * (3 + (size_t)(depth > 1 ? depth - 1 : 0)) * ld + sizeof(int) * 4 * (size_t)ld;
+}
+
+// thread (site t, slice sl) of a block of sites evaluates the coefficients
+// sl, sl + slices, ... of the field expansion with its own table of
+// u_a^k / k! (k < p); the slices are added in fixed order
 template <typename R>
 __global__ void __launch_bounds__(kL2PThreads) l2p_field_add_kernel(
     int nleaf, const int* __restrict__ lstart, const int* __restrict__ lcount, const Q4<R>* __restrict__ srcA,
-    DownPtrs dp, int ld, int ncoef, int p, const int* __restrict__ mi, const double* __restrict__ inv_fact,
-    const int* __restrict__ up1, R h, double* __restrict__ out_E, PcgFuse pf) {
+    DownPtrs dp, int ld, int ncoef, int p, const int* __restrict__ mi, const int* __restrict__ up1,
+    const R* __restrict__ w4, const R* __restrict__ rinv, R h, double* __restrict__ out_E, PcgFuse pf) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     R* f = reinterpret_cast<R*>(smem_raw);
-    R* t0 = f + ncoef;
-    R* t1 = t0 + ncoef;
-    R* ifact = t1 + ncoef;
-    int* cinfo = reinterpret_cast<int*>(ifact + ncoef);  // [ncoef][4]
+    R* t0 = f + ld;
+    R* t1 = t0 + ld;
+    R* psum = t1 + ld;                                               // [depth - 1][ncoef]
+    int* cinfo = reinterpret_cast<int*>(psum + (dp.depth - 1) * ld);  // [ncoef][4], 16-byte aligned
+    __shared__ R pw[kL2PThreads * kPowStride];
+    __shared__ R part[3][kL2PThreads];
     __shared__ R W[kMaxP + 1];
+    __shared__ R RI[kMaxP + 1];
     __shared__ double red[kL2PThreads / 32];
     __shared__ bool last;
     const int b = blockIdx.x;
@@ -733,50 +773,93 @@ __global__ void __launch_bounds__(kL2PThreads) l2p_field_add_kernel(
     const int tid = threadIdx.x;
     if (pf.cond && b == 0 && tid == 0) cudaGraphSetConditional(pf.cond, 0u);
     for (int cc = tid; cc < ncoef; cc += kL2PThreads) {
-        ifact[cc] = R(inv_fact[cc]);
         cinfo[4 * cc] = mi[cc];
         cinfo[4 * cc + 1] = up1[3 * cc];
         cinfo[4 * cc + 2] = up1[3 * cc + 1];
         cinfo[4 * cc + 3] = up1[3 * cc + 2];
     }
-    shift_weights(W, p);
-    __syncthreads();
-    far_locals<R, kL2PThreads>(dp, b, f, t0, t1, cinfo, W, ncoef, ld);
+    stage_small(W, w4, p);
+    stage_small(RI, rinv, p);
+    // the first site group's near field, alpha and d, read now so that their
+    // latency hides behind the downward pass
     const int s0 = lstart[b], cnt = lcount[b];
-    const R inv_h = R(1) / h;
-    double dot = 0.0;
-    for (int t = tid; t < cnt; t += kL2PThreads) {
-        const int i = s0 + t;
-        const Q4<R> me = srcA[i];
-        const R ux = me.x * inv_h, uy = me.y * inv_h, uz = me.z * inv_h;
-        R d0 = R(0), d1 = R(0), d2 = R(0);
-        for (int cc = 0; cc < ncoef; cc++) {
-            const int u0 = cinfo[4 * cc + 1];
-            if (u0 < 0) continue;
-            const int pk = cinfo[4 * cc];
-            R wgt = ifact[cc];
-            for (int k = pk & 0xff; k > 0; k--) wgt *= ux;
-            for (int k = (pk >> 8) & 0xff; k > 0; k--) wgt *= uy;
-            for (int k = (pk >> 16) & 0xff; k > 0; k--) wgt *= uz;
-            d0 += wgt * f[u0];
-            d1 += wgt * f[cinfo[4 * cc + 2]];
-            d2 += wgt * f[cinfo[4 * cc + 3]];
-        }
-        const R s2 = -inv_h * inv_h;
-        double e[3];
-        e[0] = out_E[3 * (int64_t)i] + (double)(d0 * s2);
-        e[1] = out_E[3 * (int64_t)i + 1] + (double)(d1 * s2);
-        e[2] = out_E[3 * (int64_t)i + 2] + (double)(d2 * s2);
-        for (int k = 0; k < 3; k++) out_E[3 * (int64_t)i + k] = e[k];
+    double pre[7] = {0, 0, 0, 0, 0, 0, 0};
+    if (tid < cnt) {
+        const int64_t i = s0 + tid;
+        for (int k = 0; k < 3; k++) pre[k] = out_E[3 * i + k];
         if (pf.Ad) {
-            const double a = pf.alpha[i];
-            for (int k = 0; k < 3; k++) {
-                const double dk = pf.d[3 * (int64_t)i + k];
-                const double v = a > 0.0 ? dk / a - e[k] : 0.0;
-                pf.Ad[3 * (int64_t)i + k] = v;
-                dot += dk * v;
+            pre[3] = pf.alpha[i];
+            for (int k = 0; k < 3; k++) pre[4 + k] = pf.d[3 * i + k];
+        }
+    }
+    __syncthreads();
+    far_locals<R, kL2PThreads>(dp, b, f, t0, t1, psum, cinfo, W, ncoef, ld);
+    const int nlow = p * (p + 1) * (p + 2) / 6;  // coefficients with |n| <= p - 1
+    const R inv_h = R(1) / h;
+    const R s2 = -inv_h * inv_h;
+    double dot = 0.0;
+    R* mypw = pw + tid * kPowStride;
+    for (int tg = 0; tg < cnt; tg += kL2PThreads) {
+        const int nt = min(kL2PThreads, cnt - tg);
+        const int slices = kL2PThreads / nt;
+        const int t = tid % nt, sl = tid / nt;
+        R d0 = R(0), d1 = R(0), d2 = R(0);
+        if (sl < slices) {
+            const Q4<R> me = srcA[s0 + tg + t];
+            const R u[3] = {me.x * inv_h, me.y * inv_h, me.z * inv_h};
+            for (int a = 0; a < 3; a++) {
+                R w = R(1);
+                mypw[a * kMaxP] = w;
+                for (int k = 1; k < p; k++) {
+                    w = w * u[a] * RI[k];
+                    mypw[a * kMaxP + k] = w;
+                }
+            }
+            // E_d = -(1/h^2) sum_{|n| <= p-1} u^n/n! f_{n+e_d}
+            for (int cc = sl; cc < nlow; cc += slices) {
+                const int4 ci = *reinterpret_cast<const int4*>(cinfo + 4 * cc);
+                const R wgt = mypw[ci.x & 0xff] * mypw[kMaxP + ((ci.x >> 8) & 0xff)] *
+                              mypw[2 * kMaxP + ((ci.x >> 16) & 0xff)];
+                d0 += wgt * f[ci.y];
+                d1 += wgt * f[ci.z];
+                d2 += wgt * f[ci.w];
             }
         }
+        part[0][tid] = d0;
+        part[1][tid] = d1;
+        part[2][tid] = d2;
+        __syncthreads();
+        if (tid < nt) {
+            const int i = s0 + tg + tid;
+            R e0 = R(0), e1 = R(0), e2 = R(0);
+            for (int u = 0; u < slices; u++) {
+                e0 += part[0][tid + u * nt];
+                e1 += part[1][tid + u * nt];
+                e2 += part[2][tid + u * nt];
+            }
+            if (tg > 0) {
+                for (int k = 0; k < 3; k++) pre[k] = out_E[3 * (int64_t)i + k];
+                if (pf.Ad) {
+                    pre[3] = pf.alpha[i];
+                    for (int k = 0; k < 3; k++) pre[4 + k] = pf.d[3 * (int64_t)i + k];
+                }
+            }
+            double e[3];
+            e[0] = pre[0] + (double)(e0 * s2);
+            e[1] = pre[1] + (double)(e1 * s2);
+            e[2] = pre[2] + (double)(e2 * s2);
+            for (int k = 0; k < 3; k++) out_E[3 * (int64_t)i + k] = e[k];
+            if (pf.Ad) {
+                const double a = pre[3];
+                for (int k = 0; k < 3; k++) {
+                    const double dk = pre[4 + k];
+                    const double v = a > 0.0 ? dk / a - e[k] : 0.0;
+                    pf.Ad[3 * (int64_t)i + k] = v;
+                    dot += dk * v;
+                }
+            }
+        }
+        __syncthreads();
     }
     if (!pf.Ad) return;
     // leaf partial, then the last block adds all leaves in order
@@ -857,12 +940,13 @@ static DownPtrs down_ptrs(polfmm_ctx* c) {
     DownPtrs dp{};
     for (int l = 0; l <= c->depth; l++) {
         dp.Lp[l] = c->lv[l].Lp;
-        dp.parent[l] = c->lv[l].parent;
+        dp.map[l] = c->lv[l].map;
         dp.key[l] = c->lv[l].key;
         dp.cap[l] = c->lv[l].cap;
     }
     dp.depth = c->depth;
     dp.nchunk = c->m2l_chunks;
+    dp.p = c->p;
     return dp;
 }
 
@@ -881,17 +965,18 @@ static void launch_leaf(polfmm_ctx* c, int mode, const double* mu_sorted, double
     LaunchScope ls(c, mode == LEAF_DIPOLE_E ? F_LEAF_DIPOLE : (mode == LEAF_CHARGE_PHI_E ? F_LEAF_STATIC : F_LEAF_FULL));
     const DownPtrs dp = down_ptrs(c);
 #define LEAF_ARGS                                                                                                \
-    L.nbox, L.key, c->lstart, c->lcount, L.map, c->leaf_order, c->depth, A, B, dp, c->ld, c->ncoef, c->p, T.mi, \
-        T.inv_fact, T.up1, T.up2, h, phi, E, G, c->err, far
+    c->leaf_items, c->leaf_nitems, L.key, c->lstart, c->lcount, L.map, c->depth, A, B, dp, c->ld, c->ncoef, c->p, T.mi, \
+        T.inv_fact, T.up1, T.up2, pick<R>(T.w4, T.w4f), h, phi, E, G, c->err, far
+    const int grid = c->leaf_items_grid;
+    const int dsm = far ? c->depth : 0;
     if (mode == LEAF_DIPOLE_E)
         leaf_kernel<R, LEAF_DIPOLE_E>
-            <<<L.nbox, kLeafThreads, leaf_smem_bytes<R, LEAF_DIPOLE_E>(c->ncoef), st>>>(LEAF_ARGS);
+            <<<grid, kLeafThreads, leaf_smem_bytes<R, LEAF_DIPOLE_E>(c->ncoef, dsm), st>>>(LEAF_ARGS);
     else if (mode == LEAF_CHARGE_PHI_E)
         leaf_kernel<R, LEAF_CHARGE_PHI_E>
-            <<<L.nbox, kLeafThreads, leaf_smem_bytes<R, LEAF_CHARGE_PHI_E>(c->ncoef), st>>>(LEAF_ARGS);
+            <<<grid, kLeafThreads, leaf_smem_bytes<R, LEAF_CHARGE_PHI_E>(c->ncoef, dsm), st>>>(LEAF_ARGS);
     else
-        leaf_kernel<R, LEAF_FULL><<<L.nbox, kLeafThreads, leaf_smem_bytes<R, LEAF_FULL>(c->ncoef), st>>>(
-            LEAF_ARGS);
+        leaf_kernel<R, LEAF_FULL><<<grid, kLeafThreads, leaf_smem_bytes<R, LEAF_FULL>(c->ncoef, dsm), st>>>(LEAF_ARGS);
 #undef LEAF_ARGS
 }
 
@@ -911,8 +996,6 @@ size_t source_record_bytes(bool mixed) { return mixed ? sizeof(Q4<float>) : size
 void m2l_tensor_launch(polfmm_ctx* c);  // m2l_tc.cu
 bool m2l_tensor_enabled(polfmm_ctx* c);
 
-bool m2l_tensor_split_targets(polfmm_ctx* c, float** hi, float** lo, int* KP);  // m2l_tc.cu
-
 static UpPtrs up_ptrs(polfmm_ctx* c) {
     UpPtrs up{};
     for (int l = 0; l <= c->depth; l++) {
@@ -922,16 +1005,6 @@ static UpPtrs up_ptrs(polfmm_ctx* c) {
         up.nchild[l] = c->lv[l].nchild;
         up.key[l] = c->lv[l].key;
         up.arrive[l] = c->lv[l].arrive;
-    }
-    float* hi[kMaxDepth + 1] = {nullptr};
-    float* lo[kMaxDepth + 1] = {nullptr};
-    int KP = 0;
-    if (m2l_tensor_split_targets(c, hi, lo, &KP)) {
-        for (int l = 2; l <= c->depth; l++) {
-            up.hi[l] = hi[l];
-            up.lo[l] = lo[l];
-        }
-        up.KP = KP;
     }
     return up;
 }
@@ -958,7 +1031,7 @@ static bool pass_impl(polfmm_ctx* c, int mode, bool use_q, const double* mu_sort
             R inv_h = R((double)(1 << d) / c->side);
             upward_kernel<R><<<Lf.nbox, kUpThreads, upward_smem_bytes<R>(c->ncoef), c->stream>>>(
                 Lf.nbox, d, c->lstart, c->lcount, (const R*)c->ploc, use_q ? c->q_s : nullptr, mu_sorted,
-                up_ptrs(c), c->ld, c->ncoef, c->p, T.mi, T.dn1, inv_h);
+                up_ptrs(c), c->ld, c->ncoef, c->p, T.mi, pick<R>(T.w4, T.w4f), pick<R>(T.rinv, T.rinvf), inv_h);
         }
         // M2L, all levels >= 2 in one launch
         if (m2l_tensor_enabled(c)) {
@@ -977,14 +1050,14 @@ static bool pass_impl(polfmm_ctx* c, int mode, bool use_q, const double* mu_sort
         cudaStreamWaitEvent(c->stream, c->ev_join, 0);
         LaunchScope ls(c, F_LEAF_DIPOLE);
         const R h = R(c->side / (double)(1 << d));
-        size_t smem = (4 * sizeof(R) + 4 * sizeof(int)) * (size_t)c->ncoef;
+        const size_t smem = l2p_smem_bytes<R>(c->ld, d);
         PcgFuse pf{};
         if (pcg)
             pf = PcgFuse{c->alpha_s, c->d,      c->Ad, c->leaf_partial,
                          c->scal,    c->ticket, c->capturing_loop ? c->loop_cond : 0};
         l2p_field_add_kernel<R><<<Lf.nbox, kL2PThreads, smem, c->stream>>>(
             Lf.nbox, c->lstart, c->lcount, reinterpret_cast<const Q4<R>*>(c->srcA), down_ptrs(c), c->ld, c->ncoef,
-            c->p, T.mi, T.inv_fact, T.up1, h, E, pf);
+            c->p, T.mi, T.up1, pick<R>(T.w4, T.w4f), pick<R>(T.rinv, T.rinvf), h, E, pf);
         return pcg;
     }
     launch_leaf<R>(c, mode, mu_sorted, phi, E, G, mu_packed, c->stream, d >= 2 ? 1 : 0);
@@ -1013,9 +1086,14 @@ int fmm_ops_init_attributes(polfmm_ctx*) {
         cudaFuncSetAttribute(upward_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)upward_smem_bytes<float>(nc_max)) != cudaSuccess)
         return POLFMM_ERR_CUDA;
+    if (cudaFuncSetAttribute(l2p_field_add_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)l2p_smem_bytes<double>((nc_max + 3) & ~3, kMaxDepth)) != cudaSuccess ||
+        cudaFuncSetAttribute(l2p_field_add_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)l2p_smem_bytes<float>((nc_max + 3) & ~3, kMaxDepth)) != cudaSuccess)
+        return POLFMM_ERR_CUDA;
 #define LEAF_ATTR(R, M)                                                                                 \
     if (cudaFuncSetAttribute(leaf_kernel<R, M>, cudaFuncAttributeMaxDynamicSharedMemorySize,            \
-                             (int)leaf_smem_bytes<R, M>(nc_max)) != cudaSuccess)                        \
+                             (int)leaf_smem_bytes<R, M>(nc_max, kMaxDepth)) != cudaSuccess)                        \
         return POLFMM_ERR_CUDA;
     LEAF_ATTR(float, LEAF_DIPOLE_E)
     LEAF_ATTR(float, LEAF_CHARGE_PHI_E)

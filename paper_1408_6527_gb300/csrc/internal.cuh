@@ -28,8 +28,16 @@ constexpr int kMaxDepth = 8;
 constexpr int kNumOffsets = 189;    // interaction-list offsets per octant class
 constexpr int kOffsetGrid = 7;      // offsets live in [-3, 3]^3
 constexpr int kM2LTileBoxes = 32;   // target boxes per multipole-to-local tile
+constexpr int kLeafTargets = 16;    // targets per near-field block (heavy leaves span several blocks)
 
 inline int ncoef_of(int p) { return (p + 1) * (p + 2) * (p + 3) / 6; }
+
+// position of the multi-index (x, y, z) in the coefficient order: degree
+// o = x + y + z ascending, then x descending, then y descending (z ascending)
+__host__ __device__ inline int mi_index(int x, int y, int z) {
+    const int o = x + y + z, a = o - x;
+    return o * (o + 1) * (o + 2) / 6 + a * (a + 1) / 2 + z;
+}
 
 // ---------------------------------------------------------------------------
 // index tables for one expansion order p (device copies)
@@ -45,6 +53,10 @@ struct Tables {
     int* pre = nullptr;               // [ncoef]: number of m with |m| <= p - |n| (a prefix)
     short* add = nullptr;             // [ncoef][ncoef]: index of n + m (valid for m < pre[n])
     int* dn1 = nullptr;               // [ncoef][3]: index of n - e_d or -1
+    double* w4 = nullptr;             // [kMaxP + 1]: 4^-k / k!, 1-D weights of a quarter-side shift
+    float* w4f = nullptr;
+    double* rinv = nullptr;           // [kMaxP + 1]: 1 / k (0 at k = 0)
+    float* rinvf = nullptr;
     double* D = nullptr;              // [343][ncoef] normalised derivatives of 1/r at integer offsets
     float* Df = nullptr;
     int* class_off = nullptr;         // [8][189] packed offsets (ox+3) | (oy+3)<<4 | (oz+3)<<8
@@ -116,6 +128,10 @@ struct polfmm_ctx {
     int* lstart = nullptr;
     int* lcount = nullptr;
     int* leaf_order = nullptr;    // leaves by descending near-field work
+    int2* leaf_items = nullptr;   // near-field blocks: (leaf, first target), heaviest leaves first
+    int* leaf_nitems = nullptr;   // device count of leaf_items
+    int leaf_items_cap = 0;       // capacity of leaf_items
+    int leaf_items_grid = 0;      // launch bound of the current tree: leaves + n / kLeafTargets + 1
     polfmm::Level lv[polfmm::kMaxDepth + 1];
     polfmm::Tables tab;
     // M2L work list

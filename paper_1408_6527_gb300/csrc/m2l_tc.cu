@@ -7,23 +7,25 @@
 //
 // One CTA = one tile of up to 128 same-class target boxes (the M = 128 rows of
 // the MMA) and a range of the class's 189 offsets.  Per offset:
-//   * every thread gathers the multipole row of its box's source B - o
-//     (zero-filled where the source box is empty or outside the tree) with
-//     16-byte cp.async copies into the no-swizzle K-major core-matrix layout;
-//     the upward pass stores every multipole row of levels >= 2 pre-split into
-//     a TF32 high part and the residual, zero-padded to KP inputs;
-//   * one thread bulk-copies the pre-split, block-sparse image of K_o (only
-//     the (output band, input prefix) blocks allowed by |n| + |m| <= p) with
-//     cp.async.bulk completing on an mbarrier;
-//   * the same thread issues tcgen05.mma kind::tf32 for the three products
-//     A_hi B_hi + A_hi B_lo + A_lo B_hi (FP32-level accuracy from TF32 inputs),
-//     accumulating into a TMEM accumulator of 128 lanes x NP columns, and
-//     commits them to an mbarrier that every thread waits on before the next
-//     gather overwrites shared memory.
+//   * the warps gather the FP32 multipole row of every box's source B - o
+//     (zero where the source box is empty or outside the tree) with 16-byte
+//     cp.async copies into the no-swizzle K-major core-matrix layout, eight
+//     rows x 64 contiguous bytes per instruction; one thread bulk-copies the
+//     pre-split image of K_o with cp.async.bulk completing on an mbarrier;
+//   * the threads split the gathered rows into a TF32 high part and the
+//     residual in shared memory;
+//   * one thread issues tcgen05.mma kind::tf32 for A_hi B_lo + A_lo B_hi +
+//     A_hi B_hi (FP32-level accuracy from TF32 inputs).  Inputs come in steps
+//     of 8; step k only feeds the outputs n with |n| + (degree of input 8k) <= p,
+//     a prefix of the outputs, so each step is ONE MMA whose N is that prefix
+//     (rounded to 16): the image of K_o is stored as one slab per step;
+//   * every thread waits for the commit, then folds the offset's accumulator
+//     into a running sum held in TMEM with round-to-nearest FP32 additions.
 // At the end each warp reads its 32 TMEM lanes (tcgen05.ld) and writes the
 // partial locals of its boxes; partials of different offset ranges are summed
-// in fixed order by the downward pass of the leaf kernels.  Every wait is bounded: on timeout the CTA
-// raises an error bit, stops issuing and still frees its TMEM.
+// in fixed order by the downward pass of the leaf kernels.  Every wait is
+// bounded: on timeout the CTA raises an error bit, stops issuing and still
+// frees its TMEM.
 #include <math.h>
 #include <string.h>
 
@@ -35,19 +37,27 @@ namespace polfmm {
 
 constexpr int kTcRows = 128;
 constexpr int kTcThreads = 128;
-constexpr int kTcMaxEntries = 12;
+constexpr int kTcMaxSteps = 24;  // input steps of 8 (p <= 8: KP <= 168)
 constexpr uint64_t kTcWaitNs = 2000000000ull;  // 2 s bound on every wait
 
 struct TcSchedule {
-    int nent;
-    int n0[kTcMaxEntries];    // first output column of the block
-    int nn[kTcMaxEntries];    // block width (multiple of 16)
-    int ks[kTcMaxEntries];    // input steps of 8 (prefix of the inputs)
-    int boff[kTcMaxEntries];  // float offset of the block inside one K_o image part
-    int KP;                   // padded input count (multiple of 8)
-    int NP;                   // padded output count (multiple of 16)
-    int bpart;                // floats per image part (hi or lo) per offset
-    int tmem_cols;            // power of two >= NP
+    int nks;                   // input steps of 8 (KP / 8)
+    int width[kTcMaxSteps];    // outputs fed by step k (multiple of 16, non-increasing)
+    int soff[kTcMaxSteps];     // float offset of step k's slab inside one image part
+    int KP;                    // padded input count (multiple of 8)
+    int NP;                    // padded output count (multiple of 16) = width[0]
+    int bpart;                 // floats per image part (hi or lo) per offset
+    int tmem_cols;             // power of two >= 2 NP
+    int nmma;                  // MMAs per offset: 3 products x nks
+    int tab_off;               // byte offset of the MMA table in dynamic shared memory
+};
+
+// one tcgen05.mma of the per-offset sequence: the stage buffers sit at fixed
+// shared addresses, so the descriptors are the same for every offset
+struct TcMma {
+    uint64_t a, b;      // shared-memory matrix descriptors
+    uint32_t idesc;     // instruction descriptor
+    uint32_t acc;       // 0: overwrite the accumulator, 1: add
 };
 
 struct TcTile {
@@ -59,13 +69,10 @@ struct TcTile {
 struct TcState {
     TcSchedule sch;
     float* Bimg = nullptr;                   // [343][2][bpart]
-    float* Mhi[kMaxDepth + 1] = {nullptr};   // [cap][KP]
-    float* Mlo[kMaxDepth + 1] = {nullptr};
     int2* rows = nullptr;                    // (level, slot) of every box of levels >= 2, by class
     TcTile* tiles = nullptr;
     int ntiles = 0, tiles_cap = 0;
     size_t stage_bytes = 0;
-    int stages = 1;
     size_t smem = 0;
     bool ready = false;
 };
@@ -182,6 +189,14 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const float* v) {
 
 __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
+// TF32 high part (round to nearest, ties away) and FP32 residual of v
+__device__ __forceinline__ void tf32_split(float v, float& hi, float& lo) {
+    uint32_t h;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(v));
+    hi = __uint_as_float(h);
+    lo = v - hi;
+}
+
 // shared-memory matrix descriptor, K-major, no swizzle: core matrices of
 // 8 rows x 16 bytes; lbo = byte step between core matrices along K, sbo =
 // byte step between 8-row groups along M / N.
@@ -224,29 +239,32 @@ __global__ void tc_rows_kernel(int nbox, int level, const int* __restrict__ by_c
 struct TcLevelPtrs {
     const int* key[kMaxDepth + 1];
     const int* map[kMaxDepth + 1];
-    const float* Mhi[kMaxDepth + 1];
-    const float* Mlo[kMaxDepth + 1];
+    const float* M[kMaxDepth + 1];  // multipoles [cap][ld]
     float* Lp[kMaxDepth + 1];
     int cap[kMaxDepth + 1];
 };
 
-// NST = 1: gather, wait, multiply, wait.  NST = 2: the gather of offset t + 1
-// runs while the MMAs of offset t are in flight (double-buffered stages).
-template <int NST>
+// One stage per CTA: gather, split, multiply, fold; two CTAs per SM overlap
+// one CTA's gather with the other's MMAs.
 __global__ void __launch_bounds__(kTcThreads, 1) m2l_tc_kernel(const TcTile* __restrict__ tiles,
                                                                const int2* __restrict__ rows, TcLevelPtrs lp,
                                                                const float* __restrict__ Bimg,
                                                                const int* __restrict__ class_off, TcSchedule sch,
-                                                               int ncoef, int ld, int nchunk, int stage_floats,
+                                                               int ncoef, int ld, int nchunk,
                                                                int* __restrict__ err) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     const int KP = sch.KP;
-    // stage s: A_hi [KP/4][16][8][4] floats, A_lo (same), B image hi, B image lo
-    float* stage0 = reinterpret_cast<float*>(smem_raw);
-    __shared__ __align__(8) uint64_t bar_b[NST];
-    __shared__ __align__(8) uint64_t bar_m[NST];
+    // A_hi [KP/4][16][8][4] floats, A_lo (same), K_o image hi, K_o image lo, MMA table
+    float* const Ahi = reinterpret_cast<float*>(smem_raw);
+    float* const Alo = Ahi + kTcRows * KP;
+    float* const Bhi = Alo + kTcRows * KP;
+    float* const Blo = Bhi + sch.bpart;
+    __shared__ __align__(8) uint64_t bar_b;  // K_o image landed
+    __shared__ __align__(8) uint64_t bar_m;  // MMAs of the offset done
     __shared__ uint32_t tmem_base_sh;
     __shared__ int fail_sh;
+    __shared__ int s_src[2][kTcRows];
+    __shared__ int s_lvl[kTcRows];
 
     const TcTile tile = tiles[blockIdx.x];
     const int chunk = blockIdx.y;
@@ -255,10 +273,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) m2l_tc_kernel(const TcTile* __r
 
     if (warp == 0) tmem_alloc(&tmem_base_sh, (uint32_t)sch.tmem_cols);
     if (tid == 0) {
-        for (int s = 0; s < NST; s++) {
-            mbar_init(&bar_b[s], 1);
-            mbar_init(&bar_m[s], 1);
-        }
+        mbar_init(&bar_b, 1);
+        mbar_init(&bar_m, 1);
         fail_sh = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -279,108 +295,126 @@ __global__ void __launch_bounds__(kTcThreads, 1) m2l_tc_kernel(const TcTile* __r
         bz = (int)compact3(k >> 2);
     }
     const int nside = 1 << level;
-    const float* Mhi = slot >= 0 ? lp.Mhi[level] : nullptr;
-    const float* Mlo = slot >= 0 ? lp.Mlo[level] : nullptr;
     const int* map = slot >= 0 ? lp.map[level] : nullptr;
+    s_lvl[tid] = level;
 
     const int per = (kNumOffsets + nchunk - 1) / nchunk;
     const int t0 = min(kNumOffsets, chunk * per), t1 = min(kNumOffsets, t0 + per);
     const int nt = t1 - t0;
     const uint32_t a_lbo = kTcRows / 8 * 128;  // bytes between K chunks of A
     const uint32_t bbytes = (uint32_t)sch.bpart * 4u;
-    const int row_off = (tid >> 3) * 32 + (tid & 7) * 4;  // floats: core matrix row of this thread
-    uint32_t pb[NST], pm[NST];
-#pragma unroll
-    for (int s = 0; s < NST; s++) pb[s] = pm[s] = 0;
+    uint32_t pb = 0, pm = 0;  // mbarrier phases
 
-    auto stage_ptr = [&](int s) { return stage0 + (size_t)s * stage_floats; };
-    // gather of offset t into stage s: A rows by this thread, the K_o image by thread 0
-    auto issue = [&](int t, int s) {
-        float* Ahi = stage_ptr(s);
-        float* Alo = Ahi + kTcRows * KP;
-        float* Bhi = Alo + kTcRows * KP;
-        float* Blo = Bhi + sch.bpart;
-        const int o = class_off[tile.cls * kNumOffsets + t];
-        const int ox = (o & 15) - 3, oy = ((o >> 4) & 15) - 3, oz = ((o >> 8) & 15) - 3;
+    // the MMA sequence of one offset, built once: product (A_hi B_lo, A_lo B_hi,
+    // A_hi B_hi: the two small correction products first) x input step k, one
+    // MMA of N = width[k] at accumulator column 0; the first one overwrites
+    TcMma* mtab = reinterpret_cast<TcMma*>(smem_raw + sch.tab_off);
+    {
+        const uint32_t a_hi = smem_u32(Ahi), a_lo = smem_u32(Alo);
+        const uint32_t b_hi = smem_u32(Bhi), b_lo = smem_u32(Blo);
+        for (int j = tid; j < sch.nmma; j += kTcThreads) {
+            const int prod = j / sch.nks, k = j - prod * sch.nks;
+            const int w = sch.width[k];
+            const uint32_t b_lbo = (uint32_t)(w / 8) * 128u;
+            const uint32_t a_base = prod == 1 ? a_lo : a_hi;
+            const uint32_t b_base = (prod == 0 ? b_lo : b_hi) + (uint32_t)sch.soff[k] * 4u;
+            TcMma m;
+            m.a = smem_desc(a_base + 2u * (uint32_t)k * a_lbo, a_lbo, 128u);
+            m.b = smem_desc(b_base, b_lbo, 128u);
+            m.idesc = idesc_tf32(kTcRows, w);
+            m.acc = j == 0 ? 0u : 1u;
+            mtab[j] = m;
+        }
+    }
+
+    // source row of this thread's box for offset t (-1: empty or outside), one
+    // offset ahead of the gather that uses it; the gather reads it from shared memory
+    auto lookup = [&](int t) {
         int src = -1;
         if (slot >= 0) {
+            const int o = class_off[tile.cls * kNumOffsets + t];
+            const int ox = (o & 15) - 3, oy = ((o >> 4) & 15) - 3, oz = ((o >> 8) & 15) - 3;
             const int ax = bx - ox, ay = by - oy, az = bz - oz;
             if (ax >= 0 && ay >= 0 && az >= 0 && ax < nside && ay < nside && az < nside)
                 src = map[morton3(ax, ay, az)];
         }
+        s_src[(t - t0) & 1][tid] = src;
+    };
+
+    // gather of offset t: warp w copies the 8-row groups w, w + 4, .. with lane =
+    // (row in group) + 8 (chunk in a group of 4 chunks): each instruction moves
+    // 8 rows x 64 contiguous bytes and its shared stores hit distinct banks.
+    // Inputs ncoef .. KP - 1 are zero-filled.  The K_o image by thread 0.
+    const int lane = tid & 31;
+    const int rr = lane & 7, cq = lane >> 3;
+    const int nch = KP / 4;
+    auto issue = [&](int t) {
         if (tid == 0) {
+            const int o = class_off[tile.cls * kNumOffsets + t];
+            const int ox = (o & 15) - 3, oy = ((o >> 4) & 15) - 3, oz = ((o >> 8) & 15) - 3;
             const int oidx = (ox + 3) + kOffsetGrid * ((oy + 3) + kOffsetGrid * (oz + 3));
             const float* img = Bimg + (size_t)oidx * 2 * sch.bpart;
-            mbar_arrive_expect_tx(&bar_b[s], 2 * bbytes);
-            bulk_g2s(Bhi, img, bbytes, &bar_b[s]);
-            bulk_g2s(Blo, img + sch.bpart, bbytes, &bar_b[s]);
+            mbar_arrive_expect_tx(&bar_b, 2 * bbytes);
+            bulk_g2s(Bhi, img, bbytes, &bar_b);
+            bulk_g2s(Blo, img + sch.bpart, bbytes, &bar_b);
         }
-        const uint32_t nbytes = src >= 0 ? 16u : 0u;
-        const size_t so = src >= 0 ? (size_t)src * KP : 0;
-        const float* gh = src >= 0 ? Mhi + so : Bimg;  // any valid address when nothing is read
-        const float* gl = src >= 0 ? Mlo + so : Bimg;
-        for (int c = 0; c < KP / 4; c++) {
-            const int off = c * (kTcRows / 8) * 32 + row_off;
-            cp_async16(Ahi + off, gh + (src >= 0 ? 4 * c : 0), nbytes);
-            cp_async16(Alo + off, gl + (src >= 0 ? 4 * c : 0), nbytes);
+        const int* srcs = s_src[(t - t0) & 1];
+        for (int rg = warp; rg < kTcRows / 8; rg += kTcThreads / 32) {
+            const int row = rg * 8 + rr;
+            const int src = srcs[row];
+            const float* g = src >= 0 ? lp.M[s_lvl[row]] + (size_t)src * ld : Bimg;  // any valid address when nothing is read
+            const int off0 = rg * 32 + rr * 4;
+            for (int c = cq; c < nch; c += 4) {
+                const int valid = src >= 0 ? min(4, max(0, ncoef - 4 * c)) : 0;
+                cp_async16(Ahi + c * (kTcRows / 8) * 32 + off0, valid ? g + 4 * c : Bimg, (uint32_t)(4 * valid));
+            }
         }
         asm volatile("cp.async.commit_group;" ::: "memory");
     };
 
-    if (nt > 0) issue(t0, 0);
+    if (nt > 0) lookup(t0);
+    __syncthreads();
+    if (nt > 0) issue(t0);
+    if (nt > 1) lookup(t0 + 1);
+    float4* const ah4 = reinterpret_cast<float4*>(Ahi);
+    float4* const al4 = reinterpret_cast<float4*>(Alo);
     for (int i = 0; i < nt; i++) {
-        const int s = NST == 2 ? (i & 1) : 0;
-        const bool prefetch = NST == 2 && i + 1 < nt;
-        if (prefetch) {
-            const int s1 = (i + 1) & 1;  // the MMAs of offset i - 1 (stage s1) finished last iteration
-            issue(t0 + i + 1, s1);
-            asm volatile("cp.async.wait_group 1;" ::: "memory");
-        } else {
-            asm volatile("cp.async.wait_group 0;" ::: "memory");
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+        __syncthreads();
+        // FP32 rows -> TF32 high part (round to nearest, ties away) + residual
+        for (int q = tid; q < kTcRows * KP / 4; q += kTcThreads) {
+            const float4 v = ah4[q];
+            float4 h, l;
+            tf32_split(v.x, h.x, l.x);
+            tf32_split(v.y, h.y, l.y);
+            tf32_split(v.z, h.z, l.z);
+            tf32_split(v.w, h.w, l.w);
+            ah4[q] = h;
+            al4[q] = l;
         }
         fence_proxy_async();
         __syncthreads();
         if (fail_sh) break;
         if (tid == 0) {
-            if (!mbar_wait_bounded(&bar_b[s], pb[s])) {
+            if (!mbar_wait_bounded(&bar_b, pb)) {
                 atomicOr(err, 4);
                 fail_sh = 1;
             } else {
                 tc_fence_after();
-                const uint32_t a_hi = smem_u32(stage_ptr(s));
-                const uint32_t a_lo = a_hi + (uint32_t)(kTcRows * KP) * 4u;
-                const uint32_t b_hi = a_lo + (uint32_t)(kTcRows * KP) * 4u;
-                const uint32_t b_lo = b_hi + bbytes;
-                // this offset alone into the accumulator: the two small correction
-                // products first, the main product last; the first MMA of each band
-                // overwrites
-                for (int e = 0; e < sch.nent; e++) {
-                    const uint32_t idesc = idesc_tf32(kTcRows, sch.nn[e]);
-                    const uint32_t b_lbo = (uint32_t)(sch.nn[e] / 8) * 128u;
-                    const uint32_t d = tmem + (uint32_t)sch.n0[e];
-                    int first = 1;
-                    for (int pi = 0; pi < 3; pi++) {
-                        const int prod = pi == 0 ? 1 : (pi == 1 ? 2 : 0);  // hi*lo, lo*hi, hi*hi
-                        const uint32_t a_base = prod == 2 ? a_lo : a_hi;
-                        const uint32_t b_base = (prod == 1 ? b_lo : b_hi) + (uint32_t)sch.boff[e] * 4u;
-                        for (int k = 0; k < sch.ks[e]; k++) {
-                            const uint64_t ad = smem_desc(a_base + 2u * (uint32_t)k * a_lbo, a_lbo, 128u);
-                            const uint64_t bd = smem_desc(b_base + 2u * (uint32_t)k * b_lbo, b_lbo, 128u);
-                            mma_tf32(d, ad, bd, idesc, first ? 0u : 1u);
-                            first = 0;
-                        }
-                    }
+                for (int j = 0; j < sch.nmma; j++) {
+                    const TcMma m = mtab[j];
+                    mma_tf32(tmem, m.a, m.b, m.idesc, m.acc);
                 }
-                mma_commit(&bar_m[s]);
+                mma_commit(&bar_m);
             }
         }
-        pb[s] ^= 1;
+        pb ^= 1;
         // wait for this offset's MMAs, then fold the accumulator into the running
         // sum with round-to-nearest FP32 additions (warp w: TMEM lanes 32 w ..)
         __syncthreads();
         if (fail_sh) break;
-        if (!mbar_wait_bounded(&bar_m[s], pm[s])) atomicOr(err, 4), fail_sh = 1;
-        pm[s] ^= 1;
+        if (!mbar_wait_bounded(&bar_m, pm)) atomicOr(err, 4), fail_sh = 1;
+        pm ^= 1;
         tc_fence_after();
         {
             const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
@@ -399,7 +433,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) m2l_tc_kernel(const TcTile* __r
         tc_fence_before();
         __syncthreads();
         if (fail_sh) break;
-        if (NST == 1 && i + 1 < nt) issue(t0 + i + 1, 0);  // the single stage is free again
+        if (i + 1 < nt) {
+            issue(t0 + i + 1);  // the stage is free again
+            if (i + 2 < nt) lookup(t0 + i + 2);
+        }
     }
     __syncthreads();
 
@@ -463,44 +500,46 @@ int m2l_tensor_prepare(polfmm_ctx* c) {
         memset(&sch, 0, sizeof(sch));
         sch.KP = (nc + 7) / 8 * 8;
         sch.NP = (nc + 15) / 16 * 16;
-        // output bands of 16 columns; each needs the input prefix ncoef(p - min degree)
-        int nbands = sch.NP / 16;
-        std::vector<int> need(nbands, 0);
-        for (int bnd = 0; bnd < nbands; bnd++)
-            for (int n = bnd * 16; n < bnd * 16 + 16 && n < nc; n++)
-                need[bnd] = std::max(need[bnd], ncoef_of(p - degree_of(n, p)));
+        sch.nks = sch.KP / 8;
+        if (sch.nks > kTcMaxSteps) {
+            delete S;
+            c->tc = nullptr;
+            return POLFMM_OK;  // the SIMT kernel stays in use
+        }
+        // input step k (inputs 8k .. 8k + 7, lowest degree that of input 8k) feeds
+        // the outputs n with |n| <= p - degree(8k): a prefix of the outputs
         int off = 0;
-        for (int bnd = 0; bnd < nbands;) {
-            int ks = (need[bnd] + 7) / 8;
-            int e = bnd;
-            while (e + 1 < nbands && (need[e + 1] + 7) / 8 == ks && (e + 2 - bnd) * 16 <= 256) e++;
-            if (sch.nent >= kTcMaxEntries) return POLFMM_ERR_INVALID_ARG;
-            int k = sch.nent++;
-            sch.n0[k] = bnd * 16;
-            sch.nn[k] = (e - bnd + 1) * 16;
-            sch.ks[k] = ks;
-            sch.boff[k] = off;
-            off += sch.nn[k] * ks * 8;
-            bnd = e + 1;
+        for (int k = 0; k < sch.nks; k++) {
+            const int dmax = p - degree_of(8 * k, p);
+            const int nout = dmax >= 0 ? ncoef_of(dmax) : 0;
+            sch.width[k] = std::max(16, (nout + 15) / 16 * 16);
+            sch.soff[k] = off;
+            off += sch.width[k] * 8;
         }
         sch.bpart = off;
         // TMEM: one accumulator for the current offset and one running sum (NP columns each)
         sch.tmem_cols = 32;
         while (sch.tmem_cols < 2 * sch.NP) sch.tmem_cols *= 2;
-        if (sch.tmem_cols > 512) return POLFMM_OK;  // the SIMT kernel stays in use
+        if (sch.tmem_cols > 512) {
+            delete S;
+            c->tc = nullptr;
+            return POLFMM_OK;  // the SIMT kernel stays in use
+        }
         S->stage_bytes = sizeof(float) * (2 * (size_t)kTcRows * sch.KP + 2 * (size_t)sch.bpart);
+        sch.nmma = 3 * sch.nks;
+        sch.tab_off = (int)((S->stage_bytes + 15) / 16 * 16);
         const size_t limit = 227 * 1024;
         // one stage per CTA: two CTAs (or a CTA and near-field blocks) per SM hide
         // the gather latency better than double buffering inside one CTA
-        S->stages = 1;
-        S->smem = S->stages * S->stage_bytes + 1024;
+        S->smem = (size_t)sch.tab_off + sizeof(TcMma) * (size_t)sch.nmma;
         if (S->smem > limit) {
             delete S;
             c->tc = nullptr;
             return POLFMM_OK;  // does not fit: the SIMT kernel stays in use
         }
-        // K_o images: block e holds rows n0..n0+nn, inputs 0..8 ks, core-matrix layout
-        // element (n, k) at (k/4)*(nn/8)*32 + (n/8)*32 + (n%8)*4 + k%4
+        // K_o images, one slab per input step: slab k holds outputs 0 .. width[k] - 1
+        // x inputs 8k .. 8k + 7 in the core-matrix layout, element (n, kk) at
+        // (kk/4)*(width/8)*32 + (n/8)*32 + (n%8)*4 + kk%4; split into a TF32 part and residual
         std::vector<double> Dd((size_t)343 * nc);
         if (cudaMemcpy(Dd.data(), c->tab.D, sizeof(double) * Dd.size(), cudaMemcpyDeviceToHost) != cudaSuccess)
             return POLFMM_ERR_CUDA;
@@ -517,22 +556,21 @@ int m2l_tensor_prepare(polfmm_ctx* c) {
         for (int oi = 0; oi < 343; oi++) {
             float* hi = &img[(size_t)oi * 2 * sch.bpart];
             float* lo = hi + sch.bpart;
-            for (int e = 0; e < sch.nent; e++) {
-                for (int nl = 0; nl < sch.nn[e]; nl++) {
-                    int n = sch.n0[e] + nl;
-                    for (int k = 0; k < sch.ks[e] * 8; k++) {
+            for (int k = 0; k < sch.nks; k++) {
+                const int w = sch.width[k];
+                for (int n = 0; n < w; n++)
+                    for (int kk = 0; kk < 8; kk++) {
+                        const int m = 8 * k + kk;
                         float v = 0.f;
-                        if (n < nc && k < nc && degree_of(n, p) + degree_of(k, p) <= p) {
-                            int s = lut[((mx[n] + mx[k]) * (p + 1) + my[n] + my[k]) * (p + 1) + mz[n] + mz[k]];
-                            v = (float)Dd[(size_t)oi * nc + s];
+                        if (n < nc && m < nc && degree_of(n, p) + degree_of(m, p) <= p) {
+                            int s2 = lut[((mx[n] + mx[m]) * (p + 1) + my[n] + my[m]) * (p + 1) + mz[n] + mz[m]];
+                            v = (float)Dd[(size_t)oi * nc + s2];
                         }
-                        size_t pos = sch.boff[e] + (size_t)(k / 4) * (sch.nn[e] / 8) * 32 + (nl / 8) * 32 +
-                                     (nl % 8) * 4 + k % 4;
-                        float h = tf32_round(v);
+                        const size_t pos = sch.soff[k] + (size_t)(kk / 4) * (w / 8) * 32 + (n / 8) * 32 + (n % 8) * 4 + kk % 4;
+                        const float h = tf32_round(v);
                         hi[pos] = h;
                         lo[pos] = v - h;
                     }
-                }
             }
         }
         if (cudaMalloc(&S->Bimg, sizeof(float) * img.size()) != cudaSuccess) {
@@ -541,25 +579,13 @@ int m2l_tensor_prepare(polfmm_ctx* c) {
         }
         if (cudaMemcpy(S->Bimg, img.data(), sizeof(float) * img.size(), cudaMemcpyHostToDevice) != cudaSuccess)
             return POLFMM_ERR_CUDA;
-        for (int l = 2; l <= c->depth; l++) {
-            size_t cnt = (size_t)c->lv[l].cap * sch.KP;
-            if (cudaMalloc(&S->Mhi[l], sizeof(float) * cnt) != cudaSuccess ||
-                cudaMalloc(&S->Mlo[l], sizeof(float) * cnt) != cudaSuccess) {
-                cudaGetLastError();
-                return POLFMM_ERR_OUT_OF_MEMORY;
-            }
-            // the padding inputs ncoef .. KP - 1 stay zero; the upward pass writes the rest
-            if (cudaMemset(S->Mhi[l], 0, sizeof(float) * cnt) != cudaSuccess ||
-                cudaMemset(S->Mlo[l], 0, sizeof(float) * cnt) != cudaSuccess)
-                return POLFMM_ERR_CUDA;
-        }
         size_t rows_cap = 0;
         for (int l = 2; l <= c->depth; l++) rows_cap += c->lv[l].cap;
         if (cudaMalloc(&S->rows, sizeof(int2) * std::max<size_t>(rows_cap, 1)) != cudaSuccess) {
             cudaGetLastError();
             return POLFMM_ERR_OUT_OF_MEMORY;
         }
-        cudaError_t e1 = cudaFuncSetAttribute(m2l_tc_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e1 = cudaFuncSetAttribute(m2l_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                               (int)S->smem);
         if (e1 != cudaSuccess) {
             cudaGetLastError();
@@ -617,17 +643,6 @@ int m2l_tensor_prepare(polfmm_ctx* c) {
     return POLFMM_OK;
 }
 
-bool m2l_tensor_split_targets(polfmm_ctx* c, float** hi, float** lo, int* KP) {
-    if (!m2l_tensor_enabled(c)) return false;
-    TcState* S = state(c);
-    for (int l = 2; l <= c->depth; l++) {
-        hi[l] = S->Mhi[l];
-        lo[l] = S->Mlo[l];
-    }
-    *KP = S->sch.KP;
-    return true;
-}
-
 void m2l_tensor_launch(polfmm_ctx* c) {
     TcState* S = state(c);
     const TcSchedule& sch = S->sch;
@@ -636,16 +651,14 @@ void m2l_tensor_launch(polfmm_ctx* c) {
         Level& B = c->lv[l];
         lp.key[l] = B.key;
         lp.map[l] = B.map;
-        lp.Mhi[l] = S->Mhi[l];
-        lp.Mlo[l] = S->Mlo[l];
+        lp.M[l] = (const float*)B.M;
         lp.Lp[l] = (float*)B.Lp;
         lp.cap[l] = B.cap;
     }
     LaunchScope ls(c, F_M2L);
     dim3 grid(S->ntiles, c->m2l_chunks);
-    const int stage_floats = (int)(S->stage_bytes / sizeof(float));
-    m2l_tc_kernel<1><<<grid, kTcThreads, S->smem, c->stream>>>(S->tiles, S->rows, lp, S->Bimg, c->tab.class_off, sch,
-                                                               c->ncoef, c->ld, c->m2l_chunks, stage_floats, c->err);
+    m2l_tc_kernel<<<grid, kTcThreads, S->smem, c->stream>>>(S->tiles, S->rows, lp, S->Bimg, c->tab.class_off, sch,
+                                                            c->ncoef, c->ld, c->m2l_chunks, c->err);
 }
 
 void m2l_tensor_release(polfmm_ctx* c) {
@@ -654,10 +667,6 @@ void m2l_tensor_release(polfmm_ctx* c) {
     if (S->Bimg) cudaFree(S->Bimg);
     if (S->rows) cudaFree(S->rows);
     if (S->tiles) cudaFree(S->tiles);
-    for (int l = 0; l <= kMaxDepth; l++) {
-        if (S->Mhi[l]) cudaFree(S->Mhi[l]);
-        if (S->Mlo[l]) cudaFree(S->Mlo[l]);
-    }
     delete S;
     c->tc = nullptr;
 }

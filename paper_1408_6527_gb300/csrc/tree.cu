@@ -406,6 +406,24 @@ __global__ void leaf_work_kernel(int nleaf, int depth, const int* __restrict__ l
     idx[b] = b;
 }
 
+// near-field blocks: leaf r of the work order covers ceil(count / kLeafTargets)
+// blocks of at most kLeafTargets targets each
+__global__ void leaf_split_count_kernel(int nleaf, const int* __restrict__ order, const int* __restrict__ lcount,
+                                        int* __restrict__ nsplit) {
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= nleaf) return;
+    nsplit[r] = (lcount[order[r]] + kLeafTargets - 1) / kLeafTargets;
+}
+
+__global__ void leaf_items_kernel(int nleaf, const int* __restrict__ order, const int* __restrict__ lcount,
+                                  const int* __restrict__ first, int2* __restrict__ items, int cap) {
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= nleaf) return;
+    const int b = order[r], cnt = lcount[b];
+    int o = first[r];
+    for (int t = 0; t < cnt && o < cap; t += kLeafTargets) items[o++] = make_int2(b, t);
+}
+
 int tree_build(polfmm_ctx* c, const double* x_in) {
     const int64_t n = c->n;
     const int d = c->depth;
@@ -529,7 +547,19 @@ int tree_tables(polfmm_ctx* c, const double* x_in, const double* q_in, const dou
         uint32_t* kb = reinterpret_cast<uint32_t*>(c->flags);
         radix_pass<8>(c, c->key_tmp, c->val_tmp, kb, c->val_a, nullptr, nl, 0);
         radix_pass<8>(c, kb, c->val_a, c->key_tmp, c->leaf_order, nullptr, nl, 8);
+        // heavy leaves split by targets, in the same order
+        {
+            LaunchScope ls(c, F_TREE);
+            leaf_split_count_kernel<<<grid_for(nl, 256), 256, 0, st>>>(nl, c->leaf_order, c->lcount, c->flags);
+        }
+        scan_exclusive_dev(c, c->flags, c->val_a, nullptr, nl, c->leaf_nitems);
+        {
+            LaunchScope ls(c, F_TREE);
+            leaf_items_kernel<<<grid_for(nl, 256), 256, 0, st>>>(nl, c->leaf_order, c->lcount, c->val_a,
+                                                                 c->leaf_items, c->leaf_items_cap);
+        }
     }
+    c->leaf_items_grid = (int)std::min<int64_t>(c->leaf_items_cap, (int64_t)c->h_counts[d] + n / kLeafTargets + 1);
     for (int l = 0; l <= d; l++) {
         Level& B = c->lv[l];
         B.nbox = c->h_counts[l];
