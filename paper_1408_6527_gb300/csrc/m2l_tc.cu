@@ -68,6 +68,8 @@ struct TcTile {
 
 struct TcState {
     TcSchedule sch;
+    bool tmem_a = false;                     // A operands in TMEM (m2l_tca_kernel), else in shared memory
+    size_t row_stride = 0;                   // m2l_tca_kernel: floats per gathered row
     float* Bimg = nullptr;                   // [343][2][bpart]
     int2* rows = nullptr;                    // (level, slot) of every box of levels >= 2, by class
     TcTile* tiles = nullptr;
@@ -184,6 +186,25 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const float* v) {
         "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])), "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])),
         "r"(__float_as_uint(v[8])), "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])),
         "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])), "r"(__float_as_uint(v[15]))
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const float* v) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(taddr),
+                 "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
+                 "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
+                 "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7]))
+                 : "memory");
+}
+
+// D (TMEM) (+)= A (TMEM, lane = row, column = input) x B (shared-memory descriptor)
+__device__ __forceinline__ void mma_tf32_ta(uint32_t d_tmem, uint32_t a_tmem, uint64_t bdesc, uint32_t idesc,
+                                            uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "r"(a_tmem), "l"(bdesc), "r"(idesc), "r"(accumulate)
         : "memory");
 }
 
@@ -464,6 +485,273 @@ __global__ void __launch_bounds__(kTcThreads, 1) m2l_tc_kernel(const TcTile* __r
 }
 
 // ---------------------------------------------------------------------------
+// the tensor-core M2L kernel with A in tensor memory (one CTA per SM, p <= 6)
+//
+// Same contraction and MMA schedule as m2l_tc_kernel.  Eight worker warps
+// gather FP32 rows two offsets ahead through a two-stage shared-memory ring,
+// split them into TF32 high / low parts written straight into TMEM (lane =
+// box, column = input) and fold each offset's accumulator into a running sum
+// held in registers; a ninth warp issues the MMAs, which read A from TMEM and
+// only the K_o image (double-buffered) from shared memory.  A is
+// double-buffered in TMEM, so the split of offset t + 1 runs while the MMAs of
+// offset t execute.  TMEM columns: accumulator [0, NP), A buffer b at
+// NP + 2 KP b (high part) and NP + 2 KP b + KP (low part).
+// Worker warp w owns TMEM lanes 32 (w % 4) .. + 31 and the 16-column chunks
+// of parity w / 4.
+// ---------------------------------------------------------------------------
+constexpr int kTcaWorkers = 256;
+constexpr int kTcaThreads = kTcaWorkers + 32;
+constexpr int kTcaMaxNP = 128;  // running sum: NP / 2 registers per thread
+
+struct TcaMma {
+    uint64_t b;         // B descriptor (first image buffer)
+    uint32_t a_col;     // TMEM column of the A operand (buffer 0)
+    uint32_t idesc;
+};
+
+__device__ __forceinline__ void workers_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kTcaWorkers) : "memory"); }
+
+__global__ void __launch_bounds__(kTcaThreads, 1) m2l_tca_kernel(const TcTile* __restrict__ tiles,
+                                                                 const int2* __restrict__ rows, TcLevelPtrs lp,
+                                                                 const float* __restrict__ Bimg,
+                                                                 const int* __restrict__ class_off, TcSchedule sch,
+                                                                 int ncoef, int ld, int nchunk, int rs,
+                                                                 int* __restrict__ err) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    const int KP = sch.KP, NP = sch.NP;
+    // gather ring [2][kTcRows][rs] floats, K_o images [2][hi | lo], MMA table
+    float* const ring = reinterpret_cast<float*>(smem_raw);
+    float* const Bbuf = ring + 2 * (size_t)kTcRows * rs;
+    TcaMma* const mtab = reinterpret_cast<TcaMma*>(Bbuf + 4 * (size_t)sch.bpart);
+    __shared__ __align__(8) uint64_t bar_b[2];  // K_o image landed
+    __shared__ __align__(8) uint64_t bar_m;     // MMAs of an offset done
+    __shared__ uint32_t tmem_base_sh;
+    __shared__ int fail_sh;
+    __shared__ int s_src[4][kTcRows];
+    __shared__ int s_lvl[kTcRows];
+
+    const TcTile tile = tiles[blockIdx.x];
+    const int chunk = blockIdx.y;
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5, lane = tid & 31;
+    const bool worker = warp < kTcaWorkers / 32;
+    const int quarter = warp & 3, half = (warp >> 2) & 1;
+    const int myrow = quarter * 32 + lane;
+
+    if (warp == 0) tmem_alloc(&tmem_base_sh, 512u);
+    if (tid == 0) {
+        mbar_init(&bar_b[0], 1);
+        mbar_init(&bar_b[1], 1);
+        mbar_init(&bar_m, 1);
+        fail_sh = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base_sh;
+    const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
+    const uint32_t abuf_cols = 2u * (uint32_t)KP;
+
+    // target box of row tid (threads 0..127), any level >= 2
+    int level = 0, slot = -1, bx = 0, by = 0, bz = 0;
+    if (tid < kTcRows && tid < tile.count) {
+        const int2 r = rows[tile.first + tid];
+        level = r.x;
+        slot = r.y;
+        const uint32_t k = (uint32_t)lp.key[level][slot];
+        bx = (int)compact3(k);
+        by = (int)compact3(k >> 1);
+        bz = (int)compact3(k >> 2);
+    }
+    if (tid < kTcRows) s_lvl[tid] = level;
+    const int nside = 1 << level;
+    const int* map = slot >= 0 ? lp.map[level] : nullptr;
+
+    const int per = (kNumOffsets + nchunk - 1) / nchunk;
+    const int t0 = min(kNumOffsets, chunk * per), t1 = min(kNumOffsets, t0 + per);
+    const int nt = t1 - t0;
+    const uint32_t bbytes = (uint32_t)sch.bpart * 4u;
+
+    // MMA table: product (A_hi B_lo, A_lo B_hi, A_hi B_hi) x input step k
+    {
+        const uint32_t b_hi = smem_u32(Bbuf), b_lo = b_hi + bbytes;
+        for (int j = tid; j < sch.nmma; j += kTcaThreads) {
+            const int prod = j / sch.nks, k = j - prod * sch.nks;
+            const int w = sch.width[k];
+            TcaMma m;
+            m.b = smem_desc((prod == 0 ? b_lo : b_hi) + (uint32_t)sch.soff[k] * 4u, (uint32_t)(w / 8) * 128u, 128u);
+            m.a_col = (uint32_t)NP + (prod == 1 ? (uint32_t)KP : 0u) + 8u * (uint32_t)k;
+            m.idesc = idesc_tf32(kTcRows, w);
+            mtab[j] = m;
+        }
+    }
+
+    auto lookup = [&](int t) {  // threads 0..127: source row of this box for offset t
+        if (tid >= kTcRows || t >= t1) return;
+        int src = -1;
+        if (slot >= 0) {
+            const int o = class_off[tile.cls * kNumOffsets + t];
+            const int ox = (o & 15) - 3, oy = ((o >> 4) & 15) - 3, oz = ((o >> 8) & 15) - 3;
+            const int ax = bx - ox, ay = by - oy, az = bz - oz;
+            if (ax >= 0 && ay >= 0 && az >= 0 && ax < nside && ay < nside && az < nside)
+                src = map[morton3(ax, ay, az)];
+        }
+        s_src[(t - t0) & 3][tid] = src;
+    };
+    // workers: FP32 rows of offset t into ring stage (t - t0) & 1, 8 rows x 64
+    // contiguous bytes per instruction; inputs ncoef .. KP - 1 are zero; always
+    // commits one group
+    const int rr = lane & 7, cq = lane >> 3;
+    const int nch = KP / 4;
+    auto gather = [&](int t) {
+        if (t < t1) {
+            const int* srcs = s_src[(t - t0) & 3];
+            float* dst = ring + (size_t)((t - t0) & 1) * kTcRows * rs;
+            for (int rg = warp; rg < kTcRows / 8; rg += kTcaWorkers / 32) {
+                const int row = rg * 8 + rr;
+                const int src = srcs[row];
+                const float* g = src >= 0 ? lp.M[s_lvl[row]] + (size_t)src * ld : Bimg;
+                float* drow = dst + (size_t)row * rs;
+                for (int c = cq; c < nch; c += 4) {
+                    const int valid = src >= 0 ? min(4, max(0, ncoef - 4 * c)) : 0;
+                    cp_async16(drow + 4 * c, valid ? g + 4 * c : Bimg, (uint32_t)(4 * valid));
+                }
+            }
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    // workers: ring stage of offset t -> TMEM A buffer (t - t0) & 1 (row myrow)
+    auto split = [&](int t) {
+        const float* src = ring + (size_t)((t - t0) & 1) * kTcRows * rs + (size_t)myrow * rs;
+        const uint32_t col = (uint32_t)NP + abuf_cols * (uint32_t)((t - t0) & 1);
+        for (int c0 = 8 * half; c0 < KP; c0 += 16) {
+            const float4 v0 = *reinterpret_cast<const float4*>(src + c0);
+            const float4 v1 = *reinterpret_cast<const float4*>(src + c0 + 4);
+            float h[8], l[8];
+            tf32_split(v0.x, h[0], l[0]);
+            tf32_split(v0.y, h[1], l[1]);
+            tf32_split(v0.z, h[2], l[2]);
+            tf32_split(v0.w, h[3], l[3]);
+            tf32_split(v1.x, h[4], l[4]);
+            tf32_split(v1.y, h[5], l[5]);
+            tf32_split(v1.z, h[6], l[6]);
+            tf32_split(v1.w, h[7], l[7]);
+            tmem_st8(lane_base + col + (uint32_t)c0, h);
+            tmem_st8(lane_base + col + (uint32_t)KP + (uint32_t)c0, l);
+        }
+        tmem_wait_st();
+    };
+    auto load_b = [&](int t) {  // issuer: K_o image of offset t into buffer (t - t0) & 1
+        const int o = class_off[tile.cls * kNumOffsets + t];
+        const int ox = (o & 15) - 3, oy = ((o >> 4) & 15) - 3, oz = ((o >> 8) & 15) - 3;
+        const int oidx = (ox + 3) + kOffsetGrid * ((oy + 3) + kOffsetGrid * (oz + 3));
+        const float* img = Bimg + (size_t)oidx * 2 * sch.bpart;
+        const int bi = (t - t0) & 1;
+        float* bh = Bbuf + (size_t)bi * 2 * sch.bpart;
+        mbar_arrive_expect_tx(&bar_b[bi], 2 * bbytes);
+        bulk_g2s(bh, img, bbytes, &bar_b[bi]);
+        bulk_g2s(bh + sch.bpart, img + sch.bpart, bbytes, &bar_b[bi]);
+    };
+
+    // running sum of this thread's row and column chunks c0 = 16 half + 32 j
+    float sum[kTcaMaxNP / 32][16];
+#pragma unroll
+    for (int j = 0; j < kTcaMaxNP / 32; j++)
+#pragma unroll
+        for (int k = 0; k < 16; k++) sum[j][k] = 0.f;
+
+    // prologue: lookups of four offsets, gathers of two, split of the first, images of two
+    for (int t = t0; t < t0 + 4; t++) lookup(t);
+    __syncthreads();
+    const bool issuer = warp == kTcaWorkers / 32 && lane == 0;
+    uint32_t pbits = 0, pm = 0;  // phases: image buffers (bit b), MMA barrier
+    if (worker) {
+        gather(t0);
+        gather(t0 + 1);
+        if (nt > 0) {
+            asm volatile("cp.async.wait_group 1;" ::: "memory");
+            workers_sync();
+            split(t0);
+            workers_sync();
+        }
+        gather(t0 + 2);
+    } else if (issuer) {
+        if (nt > 0) load_b(t0);
+        if (nt > 1) load_b(t0 + 1);
+    }
+    tc_fence_before();
+    __syncthreads();
+
+    for (int i = 0; i < nt; i++) {
+        const int t = t0 + i;
+        tc_fence_after();
+        if (issuer) {
+            const int bi = i & 1;
+            if (!mbar_wait_bounded(&bar_b[bi], (pbits >> bi) & 1u)) {
+                atomicOr(err, 4);
+                fail_sh = 1;
+            } else {
+                const uint64_t boff = (uint64_t)((bi * 2u * bbytes) >> 4);  // descriptor address field
+                const uint32_t aoff = abuf_cols * (uint32_t)bi;
+                for (int j = 0; j < sch.nmma; j++) {
+                    const TcaMma m = mtab[j];
+                    mma_tf32_ta(tmem, tmem + m.a_col + aoff, m.b + boff, m.idesc, j == 0 ? 0u : 1u);
+                }
+                mma_commit(&bar_m);
+            }
+            pbits ^= 1u << bi;
+            // the image buffer of offset t is free once its MMAs are done
+            if (!mbar_wait_bounded(&bar_m, pm)) atomicOr(err, 4), fail_sh = 1;
+            if (i + 2 < nt) load_b(t + 2);
+        } else if (worker) {
+            // while the MMAs of offset t run: split offset t + 1 into the other A buffer
+            if (i + 1 < nt) {
+                asm volatile("cp.async.wait_group 1;" ::: "memory");
+                workers_sync();
+                split(t + 1);
+                workers_sync();  // every row of the stage is read: refill it
+                gather(t + 3);
+                lookup(t + 4);
+            }
+            // fold offset t into the running sum
+            if (!mbar_wait_bounded(&bar_m, pm)) atomicOr(err, 4), fail_sh = 1;
+            tc_fence_after();
+#pragma unroll
+            for (int j = 0; j < kTcaMaxNP / 32; j++) {
+                const int c0 = 16 * half + 32 * j;
+                if (c0 < NP) {
+                    float a[16];
+                    tmem_ld16(lane_base + (uint32_t)c0, a);
+#pragma unroll
+                    for (int k = 0; k < 16; k++) sum[j][k] += a[k];
+                }
+            }
+        }
+        pm ^= 1;
+        tc_fence_before();
+        __syncthreads();  // A buffer of t + 1 written, accumulator read: the next MMAs may start
+        if (fail_sh) break;
+    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    // epilogue: row myrow, this warp's column chunks
+    if (worker && !fail_sh && myrow < tile.count) {
+        const int2 r = rows[tile.first + myrow];
+        float* out = lp.Lp[r.x] + ((size_t)chunk * lp.cap[r.x] + r.y) * ld;
+#pragma unroll
+        for (int j = 0; j < kTcaMaxNP / 32; j++) {
+            const int c0 = 16 * half + 32 * j;
+            if (c0 < NP)
+                for (int k = 0; k < 16; k++)
+                    if (c0 + k < ncoef) out[c0 + k] = sum[j][k];
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, 512u);
+}
+
+// ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
 static TcState* state(polfmm_ctx* c) { return reinterpret_cast<TcState*>(c->tc); }
@@ -529,9 +817,14 @@ int m2l_tensor_prepare(polfmm_ctx* c) {
         sch.nmma = 3 * sch.nks;
         sch.tab_off = (int)((S->stage_bytes + 15) / 16 * 16);
         const size_t limit = 227 * 1024;
-        // one stage per CTA: two CTAs (or a CTA and near-field blocks) per SM hide
-        // the gather latency better than double buffering inside one CTA
-        S->smem = (size_t)sch.tab_off + sizeof(TcMma) * (size_t)sch.nmma;
+        // A in TMEM (accumulator, running sum, A_hi, A_lo within the 512 columns of
+        // an SM) with a two-stage gather ring and double-buffered images; else one
+        // shared-memory stage per CTA and two CTAs per SM
+        S->row_stride = (size_t)sch.KP + 4;  // odd multiple of 4 floats: conflict-free row reads
+        const size_t tca_smem = sizeof(float) * (2 * (size_t)kTcRows * S->row_stride + 4 * (size_t)sch.bpart) +
+                                sizeof(TcaMma) * (size_t)sch.nmma;
+        S->tmem_a = sch.NP + 4 * sch.KP <= 512 && sch.NP <= kTcaMaxNP && tca_smem <= limit;
+        S->smem = S->tmem_a ? tca_smem : (size_t)sch.tab_off + sizeof(TcMma) * (size_t)sch.nmma;
         if (S->smem > limit) {
             delete S;
             c->tc = nullptr;
@@ -585,8 +878,10 @@ int m2l_tensor_prepare(polfmm_ctx* c) {
             cudaGetLastError();
             return POLFMM_ERR_OUT_OF_MEMORY;
         }
-        cudaError_t e1 = cudaFuncSetAttribute(m2l_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              (int)S->smem);
+        cudaError_t e1 = S->tmem_a ? cudaFuncSetAttribute(m2l_tca_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                          (int)S->smem)
+                                   : cudaFuncSetAttribute(m2l_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                          (int)S->smem);
         if (e1 != cudaSuccess) {
             cudaGetLastError();
             return POLFMM_ERR_CUDA;
@@ -635,9 +930,10 @@ int m2l_tensor_prepare(polfmm_ctx* c) {
         cudaMemcpyAsync(S->tiles, tl.data(), sizeof(TcTile) * S->ntiles, cudaMemcpyHostToDevice, c->stream) !=
             cudaSuccess)
         return POLFMM_ERR_CUDA;
-    // the tensor-core kernel runs one or two CTAs per SM: split the offsets further
+    // split the offsets so that the CTAs fill the SMs in one wave: one CTA per
+    // SM with A in TMEM, two otherwise
     if (S->ntiles > 0) {
-        int want = (2 * c->num_sms + S->ntiles - 1) / S->ntiles;
+        int want = S->tmem_a ? c->num_sms / S->ntiles : (2 * c->num_sms + S->ntiles - 1) / S->ntiles;
         c->m2l_chunks = std::max(1, std::min(want, 27));
     }
     return POLFMM_OK;
@@ -657,8 +953,13 @@ void m2l_tensor_launch(polfmm_ctx* c) {
     }
     LaunchScope ls(c, F_M2L);
     dim3 grid(S->ntiles, c->m2l_chunks);
-    m2l_tc_kernel<<<grid, kTcThreads, S->smem, c->stream>>>(S->tiles, S->rows, lp, S->Bimg, c->tab.class_off, sch,
-                                                            c->ncoef, c->ld, c->m2l_chunks, c->err);
+    if (S->tmem_a)
+        m2l_tca_kernel<<<grid, kTcaThreads, S->smem, c->stream>>>(S->tiles, S->rows, lp, S->Bimg, c->tab.class_off,
+                                                                  sch, c->ncoef, c->ld, c->m2l_chunks,
+                                                                  (int)S->row_stride, c->err);
+    else
+        m2l_tc_kernel<<<grid, kTcThreads, S->smem, c->stream>>>(S->tiles, S->rows, lp, S->Bimg, c->tab.class_off, sch,
+                                                                c->ncoef, c->ld, c->m2l_chunks, c->err);
 }
 
 void m2l_tensor_release(polfmm_ctx* c) {
