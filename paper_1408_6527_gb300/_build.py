@@ -12,7 +12,9 @@ OBJDIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libpolfmm.so")
 SOURCES = ["api.cu", "tree.cu", "fmm_ops.cu", "solver.cu", "m2l_tc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
+# -ftz=true: single-precision denormals flush to zero (the FP32 path works on
+# normalised O(1) coefficients and 1/r powers far from the denormal range)
+FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-ftz=true", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "--expt-relaxed-constexpr", "-I", INCLUDE]
 
 

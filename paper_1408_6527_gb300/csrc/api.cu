@@ -326,6 +326,7 @@ int allocate(polfmm_ctx* c) {
         B.by_class = A.get<int>(B.cap);
         B.M = A.get<unsigned char>((size_t)B.cap * c->ld * rsz);
         B.arrive = A.get<int>(B.cap);
+        if (l >= 3) B.Msh = A.get<unsigned char>((size_t)B.cap * c->ld * rsz);
     }
     c->lstart = A.get<int>(c->lv[c->depth].cap);
     c->leaf_partial = A.get<double>(c->lv[c->depth].cap);

@@ -62,10 +62,10 @@ __device__ inline void stage_small(R* dst, const R* __restrict__ src, int p) {
 
 // ---------------------------------------------------------------------------
 // upward pass: P2M of every leaf, then M2M up to level 2 inside the same
-// launch.  The block that completes the last child of a parent (counted with
-// one atomic per parent) forms that parent; the parent's sum runs over its
-// children in Morton order whichever block does it, so the result does not
-// depend on the schedule.
+// launch.  Each box shifts its own multipole to its parent's centre as soon as
+// it is known; the block that completes the last child of a parent (counted
+// with one atomic per parent) adds the children's shifted rows in Morton order
+// whichever block does it, so the result does not depend on the schedule.
 //
 // P2M (Eq. multipole, normalised): m_n = sum_i q_i v_i^n/n! - sum_d
 // (mu_i,d/h) v_i^(n-e_d)/(n-e_d)!, v_i = -(x_i - z)/h; a point dipole is the
@@ -87,11 +87,12 @@ struct UpPtrs {
     const int* nchild[kMaxDepth + 1];
     const int* key[kMaxDepth + 1];
     int* arrive[kMaxDepth + 1];
+    void* Msh[kMaxDepth + 1];  // multipoles shifted to the parent's centre
 };
 
 template <typename R>
 __host__ __device__ inline size_t upward_smem_bytes(int ncoef) {
-    return sizeof(R) * 16 * (size_t)ncoef + sizeof(int) * (size_t)ncoef;
+    return sizeof(R) * 9 * (size_t)ncoef + sizeof(int) * (size_t)ncoef;
 }
 
 template <typename R>
@@ -110,13 +111,12 @@ __global__ void __launch_bounds__(kUpThreads) upward_kernel(
     const R* __restrict__ ploc, const double* __restrict__ q, const double* __restrict__ mu, UpPtrs up, int ld,
     int ncoef, int p, const int* __restrict__ mi, const R* __restrict__ w4, const R* __restrict__ rinv, R inv_h) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    R* S = reinterpret_cast<R*>(smem_raw);         // [8][ncoef] children (and slice partials of P2M)
-    R* T = S + 8 * ncoef;                           // [8][ncoef]
-    int* smi = reinterpret_cast<int*>(T + 8 * ncoef);  // [ncoef] packed multi-indices
+    R* S = reinterpret_cast<R*>(smem_raw);         // [8][ncoef] slice partials of P2M, then shift rows
+    R* Mrow = S + 8 * ncoef;                        // [ncoef] multipole of the current box
+    int* smi = reinterpret_cast<int*>(Mrow + ncoef);  // [ncoef] packed multi-indices
     __shared__ R fac[kP2MChunk][F_NUM][kMaxP + 1];
     __shared__ R W[kMaxP + 1];
     __shared__ R RI[kMaxP + 1];
-    __shared__ int s_oct[8];
     __shared__ int s_next;
     const int b = blockIdx.x;
     if (b >= nleaf) return;
@@ -179,6 +179,7 @@ __global__ void __launch_bounds__(kUpThreads) upward_kernel(
             acc[k] = a;
         }
     }
+    // the leaf's multipole -> Mrow (shared) and global memory
     if (slices > 1) {
         // slice partials through shared memory, added in slice order
         if (worker && c_first < ncoef) S[sl * ncoef + c_first] = acc[0];
@@ -186,20 +187,54 @@ __global__ void __launch_bounds__(kUpThreads) upward_kernel(
         for (int cc = tid; cc < ncoef; cc += kUpThreads) {
             R a = R(0);
             for (int u = 0; u < slices; u++) a += S[u * ncoef + cc];
+            Mrow[cc] = a;
             store_multipole(up, depth, b, cc, a, ld);
         }
     } else {
 #pragma unroll
         for (int k = 0; k < CPT; k++) {
             const int cc = c_first + k * kUpThreads;
-            if (worker && cc < ncoef) store_multipole(up, depth, b, cc, acc[k], ld);
+            if (worker && cc < ncoef) {
+                Mrow[cc] = acc[k];
+                store_multipole(up, depth, b, cc, acc[k], ld);
+            }
         }
     }
 
-    // M2M: climb while this block completes the last child of the parent
+    // M2M, split between the children and the parent: every box shifts its own
+    // multipole to its parent's centre (Msh); the block that completes a
+    // parent's last child adds the children's shifted rows in Morton order
+    R* T0 = S;           // shift work rows
+    R* T1 = S + ncoef;
     int box = b;
     for (int l = depth; l > 2; l--) {
-        __threadfence();  // this block's multipoles are visible before the count
+        __syncthreads();  // Mrow complete
+        const bool neg_x = (up.key[l][box] & 1) != 0, neg_y = (up.key[l][box] & 2) != 0,
+                   neg_z = (up.key[l][box] & 4) != 0;
+        for (int cc = tid; cc < ncoef; cc += kUpThreads) T0[cc] = Mrow[cc] * pow2neg<R>(smi[cc] >> 24);
+        __syncthreads();
+        // g_n = sum_{k <= n_d} (s/4)^k/k! m_{n - k e_d}, along x (T0 -> T1), y (T1 -> T0), z (T0 -> T1)
+        for (int ax = 0; ax < 3; ax++) {
+            const R* src = ax == 1 ? T1 : T0;
+            R* dst = ax == 1 ? T0 : T1;
+            const bool neg = ax == 0 ? neg_x : (ax == 1 ? neg_y : neg_z);
+            for (int cc = tid; cc < ncoef; cc += kUpThreads) {
+                const int pk = smi[cc];
+                const int x = pk & 0xff, y = (pk >> 8) & 0xff, z = (pk >> 16) & 0xff;
+                const int ex = ax == 0, ey = ax == 1, ez = ax == 2;
+                const int kmax = ex * x + ey * y + ez * z;
+                R a = src[cc];
+                for (int k = 1; k <= kmax; k++) {
+                    const R v = W[k] * src[mi_index(x - k * ex, y - k * ey, z - k * ez)];
+                    a += (neg && (k & 1)) ? -v : v;
+                }
+                dst[cc] = a;
+            }
+            __syncthreads();
+        }
+        R* msh = reinterpret_cast<R*>(up.Msh[l]) + (int64_t)box * ld;
+        for (int cc = tid; cc < ncoef; cc += kUpThreads) msh[cc] = T1[cc];
+        __threadfence();  // the shifted row is visible before the count
         __syncthreads();
         if (tid == 0) {
             const int par = up.parent[l][box];
@@ -216,37 +251,11 @@ __global__ void __launch_bounds__(kUpThreads) upward_kernel(
         if (par < 0) return;
         __threadfence();
         const int c0 = up.child0[l - 1][par], nc = up.nchild[l - 1][par];
-        if (tid < nc) s_oct[tid] = up.key[l][c0 + tid] & 7;
-        const R* Mc = reinterpret_cast<const R*>(up.M[l]);
-        for (int idx = tid; idx < nc * ncoef; idx += kUpThreads) {
-            const int j = idx / ncoef, cc = idx - j * ncoef;
-            S[j * ncoef + cc] = __ldcg(Mc + (int64_t)(c0 + j) * ld + cc) * pow2neg<R>(smi[cc] >> 24);
-        }
-        __syncthreads();
-        // g_n = sum_{k <= n_d} (s/4)^k/k! m_{n - k e_d}, along x (S -> T), y (T -> S), z (S -> T)
-        for (int ax = 0; ax < 3; ax++) {
-            const R* src = ax == 1 ? T : S;
-            R* dst = ax == 1 ? S : T;
-            for (int idx = tid; idx < nc * ncoef; idx += kUpThreads) {
-                const int j = idx / ncoef, cc = idx - j * ncoef;
-                const bool neg = (s_oct[j] >> ax) & 1;
-                const R* row = src + j * ncoef;
-                const int pk = smi[cc];
-                const int x = pk & 0xff, y = (pk >> 8) & 0xff, z = (pk >> 16) & 0xff;
-                const int ex = ax == 0, ey = ax == 1, ez = ax == 2;
-                const int kmax = ex * x + ey * y + ez * z;
-                R a = row[cc];
-                for (int k = 1; k <= kmax; k++) {
-                    const R v = W[k] * row[mi_index(x - k * ex, y - k * ey, z - k * ez)];
-                    a += (neg && (k & 1)) ? -v : v;
-                }
-                dst[j * ncoef + cc] = a;
-            }
-            __syncthreads();
-        }
+        const R* shc = reinterpret_cast<const R*>(up.Msh[l]);
         for (int cc = tid; cc < ncoef; cc += kUpThreads) {
             R a = R(0);
-            for (int j = 0; j < nc; j++) a += T[j * ncoef + cc];
+            for (int j = 0; j < nc; j++) a += __ldcg(shc + (int64_t)(c0 + j) * ld + cc);
+            Mrow[cc] = a;
             store_multipole(up, l - 1, par, cc, a, ld);
         }
         box = par;
@@ -575,6 +584,11 @@ __global__ void __launch_bounds__(kLeafThreads) leaf_kernel(
         R acc[NC], acc2[NC];
 #pragma unroll
         for (int k = 0; k < NC; k++) acc[k] = acc2[k] = R(0);
+        // dipole field of the sources, E = 3 er - em with er = sum (mu.r) r / r^5 and
+        // em = sum mu / r^3 (two sets, like acc / acc2)
+        R er[2][3], em[2][3];
+#pragma unroll
+        for (int k = 0; k < 3; k++) er[0][k] = er[1][k] = em[0][k] = em[1][k] = R(0);
         R xi = R(0), yi = R(0), zi = R(0);
         if (active) {
             const Q4<R> me = srcA[i];
@@ -643,7 +657,7 @@ __global__ void __launch_bounds__(kLeafThreads) leaf_kernel(
             if (!active) continue;
             // two independent accumulator sets (sources jj and jj + slices) for
             // instruction-level parallelism; added in fixed order after the loop
-            auto pair = [&](R* ac, const int jj) {
+            auto pair = [&](R* ac, R* ar, R* am, const int jj) {
                 const Q4<R> a = sA[jj];
                 const R rx = xi - a.x, ry = yi - a.y, rz = zi - a.z;
                 const R r2 = rx * rx + ry * ry + rz * rz;
@@ -672,12 +686,16 @@ __global__ void __launch_bounds__(kLeafThreads) leaf_kernel(
                     const Q4<R> mv = sB[jj];
                     const R mr = mv.x * rx + mv.y * ry + mv.z * rz;
                     const R ri5 = ri3 * ri2;
-                    const R a3 = R(3) * mr * ri5;
+                    const R a = mr * ri5;
                     if (HAS_PHI) ac[0] += mr * ri3;
-                    ac[IE + 0] += a3 * rx - mv.x * ri3;
-                    ac[IE + 1] += a3 * ry - mv.y * ri3;
-                    ac[IE + 2] += a3 * rz - mv.z * ri3;
+                    ar[0] = fma(a, rx, ar[0]);
+                    ar[1] = fma(a, ry, ar[1]);
+                    ar[2] = fma(a, rz, ar[2]);
+                    am[0] = fma(ri3, mv.x, am[0]);
+                    am[1] = fma(ri3, mv.y, am[1]);
+                    am[2] = fma(ri3, mv.z, am[2]);
                     if (HAS_G) {
+                        const R a3 = R(3) * a;
                         // G_de = 3 (mu_d r_e + mu_e r_d + mr delta_de) / r^5 - 15 mr r_d r_e / r^7
                         const R t5 = R(3) * ri5;
                         const R t7 = R(5) * a3 * ri2;
@@ -693,13 +711,17 @@ __global__ void __launch_bounds__(kLeafThreads) leaf_kernel(
             int jj = s;
 #pragma unroll 2
             for (; jj + slices < m; jj += 2 * slices) {
-                pair(acc, jj);
-                pair(acc2, jj + slices);
+                pair(acc, er[0], em[0], jj);
+                pair(acc2, er[1], em[1], jj + slices);
             }
-            if (jj < m) pair(acc, jj);
+            if (jj < m) pair(acc, er[0], em[0], jj);
         }
 #pragma unroll
         for (int k = 0; k < NC; k++) acc[k] += acc2[k];
+        if (SRC_MU) {
+#pragma unroll
+            for (int k = 0; k < 3; k++) acc[IE + k] += R(3) * (er[0][k] + er[1][k]) - (em[0][k] + em[1][k]);
+        }
         // fixed-order reduction over slices
         __syncthreads();
 #pragma unroll
@@ -1005,6 +1027,7 @@ static UpPtrs up_ptrs(polfmm_ctx* c) {
         up.nchild[l] = c->lv[l].nchild;
         up.key[l] = c->lv[l].key;
         up.arrive[l] = c->lv[l].arrive;
+        up.Msh[l] = c->lv[l].Msh;
     }
     return up;
 }

@@ -95,6 +95,7 @@ struct Level {
     void* M = nullptr;    // [cap][ld]
     void* Lp = nullptr;   // [m2l_chunks][cap][ld] M2L partial locals
     int* arrive = nullptr;  // [cap] children whose multipoles are done (0 between passes)
+    void* Msh = nullptr;    // [cap][ld] multipoles shifted to the parent's centre (levels >= 3)
 };
 
 // profiling families
