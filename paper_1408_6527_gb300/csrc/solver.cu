@@ -17,15 +17,16 @@ namespace polfmm {
 
 constexpr int kRedThreads = 256;
 
+// block-wide sum in a fixed order (warp shuffles, then the warp sums in warp
+// order); every thread gets the result.  sh holds kRedThreads doubles.
 __device__ inline double block_sum(double v, double* sh) {
-    sh[threadIdx.x] = v;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5;
+    __syncthreads();  // sh may still be read by a previous call
+    if ((threadIdx.x & 31) == 0) sh[w] = v;
     __syncthreads();
-    for (int w = kRedThreads / 2; w > 0; w >>= 1) {
-        if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
-        __syncthreads();
-    }
-    double r = sh[0];
-    __syncthreads();
+    double r = 0.0;
+    for (int k = 0; k < kRedThreads / 32; k++) r += sh[k];
     return r;
 }
 
