@@ -38,10 +38,20 @@ sys.path.insert(0, ROOT)
 METRIC = "atoms/s polarizable FMM energy+forces, mixed vs FP64, at ≤1e-5 RMS force err"
 WORKLOAD_INDEX = 2
 TOL = {"mixed": 1e-6, "fp64": 1e-8}
+
+
+def tol_for(mode, n):
+    """PCG tolerance (relative residual).  FP64: 1e-8.  MIXED: 1e-6 up to 1e5
+    sites, 3e-7 above: the force error against FP64 grows with the system
+    (1.2e-5 at 1e-6 on the 4M shell, 1.5e-6 at 1e-7), and every MIXED line must
+    stay within the 1e-5 relative RMS force gate."""
+    if mode == "fp64":
+        return TOL["fp64"]
+    return TOL["mixed"] if n <= 100_000 else 3e-7
 FP32_LANES_PER_SM = 128
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
 # current kernels from one ncu capture (profiles/); None where not captured
-TRAFFIC = {("m2l", "mixed"): 7629824}
+TRAFFIC = {("m2l", "mixed"): 7043584, ("leaf_dipole", "mixed"): 1056512}
 NUM_SMS = 152
 SM_MAX_MHZ = 2070.0
 
@@ -79,14 +89,18 @@ def m2l_flops_per_box_pair(p):
 
 
 def tc_issued_macs_per_row(p):
-    """MACs per tile row and offset issued by the tensor-core M2L: output bands
-    of 16 columns, each over the input prefix its lowest degree needs."""
+    """MACs per tile row, offset and product issued by the tensor-core M2L: one
+    MMA per input step of 8, whose N is the prefix of outputs that step feeds
+    (|n| <= p - degree of the step's first input), rounded up to 16."""
     nc = ncoef(p)
-    deg = [next(s for s in range(p + 1) if i < ncoef(s)) for i in range(nc)]
-    NP = (nc + 15) // 16 * 16
-    need = [max((ncoef(p - deg[n]) for n in range(b * 16, min(b * 16 + 16, nc))), default=0)
-            for b in range(NP // 16)]
-    return sum(16 * ((k + 7) // 8) * 8 for k in need)
+    kp = (nc + 7) // 8 * 8
+    deg = lambda i: next(s for s in range(p + 1) if i < ncoef(s))
+    total = 0
+    for k in range(kp // 8):
+        dmax = p - deg(8 * k)
+        nout = ncoef(dmax) if dmax >= 0 else 0
+        total += max(16, (nout + 15) // 16 * 16) * 8
+    return total
 
 
 def load_peaks():
@@ -244,21 +258,21 @@ def run_gpu(args, rank, world, local_rank):
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
-    def make(mode, src=None, profile=False):
+    def make(mode, src=None, profile=False, max_iter=500):
         s = src if src is not None else (pos_d, q_d, a_d)
-        return PolFMM(*s, p=w.p, depth=w.depth, mode=mode, max_iter=500, m2l=args.m2l, profile=profile,
+        return PolFMM(*s, p=w.p, depth=w.depth, mode=mode, max_iter=max_iter, m2l=args.m2l, profile=profile,
                       graphs=not args.no_graphs)
 
-    def step(ctx, mode, pos):
+    def step(ctx, mode, pos, tol=None):
         ctx.update_positions(pos)
         ctx.reset_dipoles()
-        info = ctx.solve(TOL[mode])
+        info = ctx.solve(tol_for(mode, n) if tol is None else tol)
         out = ctx.energy_forces()
         return info, out
 
-    def timed(ctx, mode, steps, warmup, sample_clocks=False):
+    def timed(ctx, mode, steps, warmup, sample_clocks=False, tol=None):
         for _ in range(warmup):
-            step(ctx, mode, pos_d)
+            step(ctx, mode, pos_d, tol)
         torch.cuda.synchronize()
         if dist:
             tdist.barrier()
@@ -272,7 +286,7 @@ def run_gpu(args, rank, world, local_rank):
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            info, out = step(ctx, mode, pos_d)
+            info, out = step(ctx, mode, pos_d, tol)
             e1.record(stream)
             e1.synchronize()
             total_ms += e0.elapsed_time(e1)
@@ -310,6 +324,12 @@ def run_gpu(args, rank, world, local_rank):
     F64, Fmx = (F_other, F_main) if other == "fp64" else (F_main, F_other)
     rms_err = float(np.sqrt(np.sum((Fmx - F64) ** 2) / np.sum(F64 ** 2)))
     n2 = max(2, args.steps // 2)
+
+    # the paper's timing protocol: exactly 10 dipole iterations per step
+    ctx10 = make(args.mode, max_iter=10)
+    t10, it10, _, _, _, _ = timed(ctx10, args.mode, max(2, args.steps // 2), 1, tol=0.0)
+    ctx10.close()
+    n10 = max(2, args.steps // 2)
 
     # per-kernel CUDA-event durations, recorded on the launching stream over
     # separately profiled steps of the same workload
@@ -382,10 +402,14 @@ def run_gpu(args, rank, world, local_rank):
         "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64" if args.mode == "mixed" else "f64", "data": "synthetic",
         "config": {"workload": f"{w.name} {n} sites p={w.p} depth={w.depth} {args.mode}", "n_sites": n, "p": w.p,
-                   "depth": w.depth, "mode": args.mode, "tol": TOL[args.mode], "m2l": args.m2l,
+                   "depth": w.depth, "mode": args.mode, "tol": tol_for(args.mode, n), "m2l": args.m2l,
                    "parallelism": "replicas" if world > 1 else "single",
                    "l2": "flushed before every step (256 MB write, outside the step interval)"},
         "iterations": iters[-1], "converged": bool(info["converged"]),
+        "fmm_passes_per_step": iters[-1] + 3,
+        "atoms_per_s_per_pass": round(value * (iters[-1] + 3), 1),
+        "fixed_10_iterations": {"value": round(world * n * n10 / (t10 / 1e3), 1), "ms_per_step": round(t10 / n10, 4),
+                                "iterations": it10[-1]},
         "rms_force_err_mixed_vs_fp64": rms_err,
         other: {"value": round(n * n2 / (t2 / 1e3), 1), "ms_per_step": round(t2 / n2, 4), "iterations": it2[-1]},
         "gpu_launches": int(launches),
@@ -421,13 +445,14 @@ def run_reference(args):
 
     w = make_workload(args.workload)
     lo, side = oracle.root_box(w.pos)
+    tol = tol_for(args.mode, w.n)
     for _ in range(args.warmup):
-        cpu_baseline(w, lo, side, TOL[args.mode])
+        cpu_baseline(w, lo, side, tol)
     total = 0.0
     for _ in range(args.steps):
         t0 = time.perf_counter()
         oracle.polarizable_energy(w.pos, w.q, w.alpha, method="fmm", p=w.p, depth=w.depth, root=(lo, side),
-                                  tol=TOL[args.mode], max_iter=500)
+                                  tol=tol, max_iter=500)
         total += time.perf_counter() - t0
     value = w.n * args.steps / total
     cores = oracle.num_threads()
@@ -436,7 +461,7 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * total / args.steps, 2),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": f"{w.name} {w.n} sites p={w.p} depth={w.depth} {args.mode}", "n_sites": w.n,
-                   "p": w.p, "depth": w.depth, "mode": args.mode, "tol": TOL[args.mode]},
+                   "p": w.p, "depth": w.depth, "mode": args.mode, "tol": tol},
         "cpu_baseline": {"value": round(value, 2), "unit": "atoms/s", "cores": cores, "kind": "oracle",
                          "sample": "each step one complete oracle step of the full workload"},
         "e2e": {"value": round(value, 2), "unit": "atoms/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
