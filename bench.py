@@ -340,7 +340,8 @@ def run_gpu(args, rank, world, local_rank):
     for _ in range(3):
         flush.zero_()
         step(ctxp, args.mode, pos_d)
-    fams = ["tree", "p2m", "m2m", "m2l", "l2l", "leaf_dipole", "leaf_static", "leaf_full", "solver", "assemble"]
+    fams = ["tree", "p2m", "m2m", "m2l", "l2l", "leaf_dipole", "l2p", "leaf_static", "leaf_full", "solver",
+            "assemble"]
     prof = {f: ctxp.profile(f) for f in fams}
     ctxp.close()
     prof_total = sum(v[0] for v in prof.values())
@@ -355,7 +356,7 @@ def run_gpu(args, rank, world, local_rank):
     fp32_peak = NUM_SMS * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
     tf32_peak = bf16_sust * 1.1 / 2.25
     fams = {
-        "leaf_dipole": dict(flops=near_pairs * 34 + n * 6 * ncoef(p - 1), bound="alu",
+        "leaf_dipole": dict(flops=near_pairs * 34, bound="alu",
                             peak=fp32_peak if mixed else 1.25,
                             peak_note="FP32 FMA nominal: 152 SMs x 128 lanes x 2 x 2070 MHz" if mixed
                             else "FP64 nominal 1.25 TFLOP/s"),

@@ -186,10 +186,11 @@ POLFMM_API int fmm_root_box(polfmm_ctx* ctx, double* lo, double* side);
 /* Profiling (options.profile = 1): total CUDA-event milliseconds and launch
  * count of one kernel family since the last reset.  Families: "tree", "p2m"
  * (the upward pass: P2M and every M2M level in one launch), "m2l",
- * "leaf_dipole" (L2L + L2P + near field of the solver's dipole-field pass),
- * "leaf_static" (same, static pass), "leaf_full" (same, energy / force pass),
- * "solver", "assemble"; "m2m" and "l2l" are accepted and stay at zero (those
- * steps run inside the "p2m" and "leaf_*" kernels).
+ * "leaf_dipole" (near field of the solver's dipole-field pass), "l2p" (L2L +
+ * L2P of that pass, with the d.Ad reduction), "leaf_static" (L2L + L2P + near
+ * field, static pass), "leaf_full" (same, energy / force pass), "solver",
+ * "assemble"; "m2m" and "l2l" are accepted and stay at zero (those steps run
+ * inside the "p2m", "l2p" and "leaf_*" kernels).
  * Unknown names return POLFMM_ERR_INVALID_ARG. */
 POLFMM_API int fmm_profile_get(polfmm_ctx* ctx, const char* family, double* total_ms, int64_t* launches);
 POLFMM_API int fmm_profile_reset(polfmm_ctx* ctx);

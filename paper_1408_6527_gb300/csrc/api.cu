@@ -924,7 +924,8 @@ int fmm_root_box(polfmm_ctx* c, double* lo, double* side) {
 }
 
 int fmm_profile_get(polfmm_ctx* c, const char* family, double* total_ms, int64_t* launches) {
-    static const char* names[F_COUNT] = {"tree", "p2m", "m2m", "m2l", "l2l", "leaf_dipole", "leaf_static", "leaf_full", "solver", "assemble"};
+    static const char* names[F_COUNT] = {"tree",      "p2m",       "m2m",    "m2l",      "l2l", "leaf_dipole",
+                                         "leaf_static", "leaf_full", "solver", "assemble", "l2p"};
     if (!c || !family) return POLFMM_ERR_INVALID_ARG;
     profile_flush(c);
     for (int f = 0; f < F_COUNT; f++)

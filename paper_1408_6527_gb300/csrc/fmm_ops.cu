@@ -1039,13 +1039,17 @@ static bool pass_impl(polfmm_ctx* c, int mode, bool use_q, const double* mu_sort
     const Tables& T = c->tab;
     Level& Lf = c->lv[d];
     // solver passes: the near-field pair sums run on a second stream while the
-    // far-field chain (upward pass, M2L) runs here; the far field is added after the join
-    const bool overlap = mode == LEAF_DIPOLE_E && d >= 2 && c->side_stream && !c->opt.profile;
-    if (overlap) {
-        cudaEventRecord(c->ev_fork, c->stream);
-        cudaStreamWaitEvent(c->side_stream, c->ev_fork, 0);
-        launch_leaf<R>(c, mode, mu_sorted, phi, E, G, mu_packed, c->side_stream, 0);
-        cudaEventRecord(c->ev_join, c->side_stream);
+    // far-field chain (upward pass, M2L) runs here; the far field is added after
+    // the join.  Profiling keeps the same kernels on one stream.
+    const bool split = mode == LEAF_DIPOLE_E && d >= 2;
+    const bool overlap = split && c->side_stream && !c->opt.profile;
+    if (split) {
+        if (overlap) {
+            cudaEventRecord(c->ev_fork, c->stream);
+            cudaStreamWaitEvent(c->side_stream, c->ev_fork, 0);
+        }
+        launch_leaf<R>(c, mode, mu_sorted, phi, E, G, mu_packed, overlap ? c->side_stream : c->stream, 0);
+        if (overlap) cudaEventRecord(c->ev_join, c->side_stream);
     }
     if (d >= 2) {
         // P2M and M2M up to level 2 (one launch)
@@ -1069,9 +1073,9 @@ static bool pass_impl(polfmm_ctx* c, int mode, bool use_q, const double* mu_sort
         }
     }
     // L2L runs inside the leaf kernels below
-    if (overlap) {
-        cudaStreamWaitEvent(c->stream, c->ev_join, 0);
-        LaunchScope ls(c, F_LEAF_DIPOLE);
+    if (split) {
+        if (overlap) cudaStreamWaitEvent(c->stream, c->ev_join, 0);
+        LaunchScope ls(c, F_L2P);
         const R h = R(c->side / (double)(1 << d));
         const size_t smem = l2p_smem_bytes<R>(c->ld, d);
         PcgFuse pf{};

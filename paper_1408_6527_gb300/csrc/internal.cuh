@@ -99,7 +99,7 @@ struct Level {
 };
 
 // profiling families
-enum Family { F_TREE = 0, F_P2M, F_M2M, F_M2L, F_L2L, F_LEAF_DIPOLE, F_LEAF_STATIC, F_LEAF_FULL, F_SOLVER, F_ASSEMBLE, F_COUNT };
+enum Family { F_TREE = 0, F_P2M, F_M2M, F_M2L, F_L2L, F_LEAF_DIPOLE, F_LEAF_STATIC, F_LEAF_FULL, F_SOLVER, F_ASSEMBLE, F_L2P, F_COUNT };
 
 // leaf evaluation modes
 enum LeafMode { LEAF_DIPOLE_E = 0, LEAF_CHARGE_PHI_E = 1, LEAF_FULL = 2 };

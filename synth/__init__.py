@@ -422,7 +422,9 @@ def workload(index: int, n: int | None = None, depth: int | None = None) -> Work
         return Workload("ring6", pts, q, alpha, 6, depth or 5, 1e-6, {**meta, "lobes": 6, "ring_radius": 60.0})
     if index == 5:
         n = n or 250000
-        d = depth or {250000: 5, 1000000: 6, 4000000: 7}.get(n, max(3, int(round(math.log(n / 8.0, 8)))))
+        # depth minimising the measured cost of one FMM pass at p = 8 (near-field
+        # pairs x 1.6 ps + M2L box pairs x 0.64 ns): 4 / 5 / 6 at 250k / 1M / 4M
+        d = depth or max(3, int(round(math.log(n / 40.0, 8))))
         pts = _cached_positions(f"shell_fcc_{n}_{seed}", lambda: sites_shell(rng, n)[0])
         rng2 = np.random.Generator(np.random.PCG64(seed + 1000))
         q = charges_normal(rng2, n)
