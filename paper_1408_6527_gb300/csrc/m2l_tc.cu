@@ -504,8 +504,8 @@ constexpr int kTcaThreads = kTcaWorkers + 32;
 constexpr int kTcaMaxNP = 128;  // running sum: NP / 2 registers per thread
 
 struct TcaMma {
-    uint64_t b;         // B descriptor (first image buffer)
-    uint32_t a_col;     // TMEM column of the A operand (buffer 0)
+    uint64_t b;         // B descriptor
+    uint32_t a_tmem;    // TMEM address of the A operand
     uint32_t idesc;
 };
 
@@ -522,13 +522,14 @@ __global__ void __launch_bounds__(kTcaThreads, 1) m2l_tca_kernel(const TcTile* _
     // gather ring [2][kTcRows][rs] floats, K_o images [2][hi | lo], MMA table
     float* const ring = reinterpret_cast<float*>(smem_raw);
     float* const Bbuf = ring + 2 * (size_t)kTcRows * rs;
-    TcaMma* const mtab = reinterpret_cast<TcaMma*>(Bbuf + 4 * (size_t)sch.bpart);
+    TcaMma* const mtab = reinterpret_cast<TcaMma*>(Bbuf + 4 * (size_t)sch.bpart);  // [2][nmma]
     __shared__ __align__(8) uint64_t bar_b[2];  // K_o image landed
     __shared__ __align__(8) uint64_t bar_m;     // MMAs of an offset done
     __shared__ uint32_t tmem_base_sh;
     __shared__ int fail_sh;
     __shared__ int s_src[4][kTcRows];
     __shared__ int s_lvl[kTcRows];
+    __shared__ int s_off[kNumOffsets];  // this CTA's offsets (packed)
 
     const TcTile tile = tiles[blockIdx.x];
     const int chunk = blockIdx.y;
@@ -573,31 +574,39 @@ __global__ void __launch_bounds__(kTcaThreads, 1) m2l_tca_kernel(const TcTile* _
     const int nt = t1 - t0;
     const uint32_t bbytes = (uint32_t)sch.bpart * 4u;
 
-    // MMA table: product (A_hi B_lo, A_lo B_hi, A_hi B_hi) x input step k
-    {
-        const uint32_t b_hi = smem_u32(Bbuf), b_lo = b_hi + bbytes;
-        for (int j = tid; j < sch.nmma; j += kTcaThreads) {
-            const int prod = j / sch.nks, k = j - prod * sch.nks;
-            const int w = sch.width[k];
-            TcaMma m;
-            m.b = smem_desc((prod == 0 ? b_lo : b_hi) + (uint32_t)sch.soff[k] * 4u, (uint32_t)(w / 8) * 128u, 128u);
-            m.a_col = (uint32_t)NP + (prod == 1 ? (uint32_t)KP : 0u) + 8u * (uint32_t)k;
-            m.idesc = idesc_tf32(kTcRows, w);
-            mtab[j] = m;
-        }
+    // MMA table for each buffer pair (A buffer b, image buffer b): product
+    // (A_hi B_lo, A_lo B_hi, A_hi B_hi) x input step k, complete descriptors so
+    // that the issuing thread does one shared load per MMA
+    for (int jb = tid; jb < 2 * sch.nmma; jb += kTcaThreads) {
+        const int bi = jb / sch.nmma, j = jb - bi * sch.nmma;
+        const int prod = j / sch.nks, k = j - prod * sch.nks;
+        const int w = sch.width[k];
+        const uint32_t b_hi = smem_u32(Bbuf) + (uint32_t)bi * 2u * bbytes, b_lo = b_hi + bbytes;
+        TcaMma m;
+        m.b = smem_desc((prod == 0 ? b_lo : b_hi) + (uint32_t)sch.soff[k] * 4u, (uint32_t)(w / 8) * 128u, 128u);
+        m.a_tmem = tmem + (uint32_t)NP + abuf_cols * (uint32_t)bi + (prod == 1 ? (uint32_t)KP : 0u) + 8u * (uint32_t)k;
+        m.idesc = idesc_tf32(kTcRows, w);
+        mtab[jb] = m;
     }
 
-    auto lookup = [&](int t) {  // threads 0..127: source row of this box for offset t
-        if (tid >= kTcRows || t >= t1) return;
+    // source row of this thread's box (threads 0..127) for offset t: the map load
+    // is issued one iteration before its value is stored (lookup_load, then the
+    // store of the previous result), so its latency stays off the worker path
+    for (int t = t0 + tid; t < t1; t += kTcaThreads) s_off[t - t0] = class_off[tile.cls * kNumOffsets + t];
+    __syncthreads();
+    auto lookup_load = [&](int t) -> int {
         int src = -1;
-        if (slot >= 0) {
-            const int o = class_off[tile.cls * kNumOffsets + t];
+        if (tid < kTcRows && t < t1 && slot >= 0) {
+            const int o = s_off[t - t0];
             const int ox = (o & 15) - 3, oy = ((o >> 4) & 15) - 3, oz = ((o >> 8) & 15) - 3;
             const int ax = bx - ox, ay = by - oy, az = bz - oz;
             if (ax >= 0 && ay >= 0 && az >= 0 && ax < nside && ay < nside && az < nside)
                 src = map[morton3(ax, ay, az)];
         }
-        s_src[(t - t0) & 3][tid] = src;
+        return src;
+    };
+    auto lookup_store = [&](int t, int src) {
+        if (tid < kTcRows && t < t1) s_src[(t - t0) & 3][tid] = src;
     };
     // workers: FP32 rows of offset t into ring stage (t - t0) & 1, 8 rows x 64
     // contiguous bytes per instruction; inputs ncoef .. KP - 1 are zero; always
@@ -662,7 +671,8 @@ __global__ void __launch_bounds__(kTcaThreads, 1) m2l_tca_kernel(const TcTile* _
         for (int k = 0; k < 16; k++) sum[j][k] = 0.f;
 
     // prologue: lookups of four offsets, gathers of two, split of the first, images of two
-    for (int t = t0; t < t0 + 4; t++) lookup(t);
+    for (int t = t0; t < t0 + 4; t++) lookup_store(t, lookup_load(t));
+    int pend = lookup_load(t0 + 4);  // in flight until the first iteration stores it
     __syncthreads();
     const bool issuer = warp == kTcaWorkers / 32 && lane == 0;
     uint32_t pbits = 0, pm = 0;  // phases: image buffers (bit b), MMA barrier
@@ -692,11 +702,12 @@ __global__ void __launch_bounds__(kTcaThreads, 1) m2l_tca_kernel(const TcTile* _
                 atomicOr(err, 4);
                 fail_sh = 1;
             } else {
-                const uint64_t boff = (uint64_t)((bi * 2u * bbytes) >> 4);  // descriptor address field
-                const uint32_t aoff = abuf_cols * (uint32_t)bi;
-                for (int j = 0; j < sch.nmma; j++) {
-                    const TcaMma m = mtab[j];
-                    mma_tf32_ta(tmem, tmem + m.a_col + aoff, m.b + boff, m.idesc, j == 0 ? 0u : 1u);
+                const TcaMma* tb = mtab + bi * sch.nmma;
+                const int nm = sch.nmma;
+                mma_tf32_ta(tmem, tb[0].a_tmem, tb[0].b, tb[0].idesc, 0u);
+                for (int j = 1; j < nm; j++) {
+                    const TcaMma m = tb[j];
+                    mma_tf32_ta(tmem, m.a_tmem, m.b, m.idesc, 1u);
                 }
                 mma_commit(&bar_m);
             }
@@ -712,7 +723,8 @@ __global__ void __launch_bounds__(kTcaThreads, 1) m2l_tca_kernel(const TcTile* _
                 split(t + 1);
                 workers_sync();  // every row of the stage is read: refill it
                 gather(t + 3);
-                lookup(t + 4);
+                lookup_store(t + 4, pend);
+                pend = lookup_load(t + 5);
             }
             // fold offset t into the running sum
             if (!mbar_wait_bounded(&bar_m, pm)) atomicOr(err, 4), fail_sh = 1;
@@ -822,7 +834,7 @@ int m2l_tensor_prepare(polfmm_ctx* c) {
         // shared-memory stage per CTA and two CTAs per SM
         S->row_stride = (size_t)sch.KP + 4;  // odd multiple of 4 floats: conflict-free row reads
         const size_t tca_smem = sizeof(float) * (2 * (size_t)kTcRows * S->row_stride + 4 * (size_t)sch.bpart) +
-                                sizeof(TcaMma) * (size_t)sch.nmma;
+                                2 * sizeof(TcaMma) * (size_t)sch.nmma;
         S->tmem_a = sch.NP + 4 * sch.KP <= 512 && sch.NP <= kTcaMaxNP && tca_smem <= limit;
         S->smem = S->tmem_a ? tca_smem : (size_t)sch.tab_off + sizeof(TcMma) * (size_t)sch.nmma;
         if (S->smem > limit) {
