@@ -111,6 +111,27 @@ __device__ __forceinline__ uint64_t global_ns() {
     return t;
 }
 
+// try_wait that lets the hardware suspend the thread for up to hint_ns
+__device__ __forceinline__ bool mbar_try_wait_hint(uint64_t* bar, uint32_t phase, uint32_t hint_ns) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(phase), "r"(hint_ns)
+        : "memory");
+    return ok != 0;
+}
+
+// bounded wait of threads that have nothing else to do: suspended between polls
+__device__ __forceinline__ bool mbar_wait_bounded_idle(uint64_t* bar, uint32_t phase) {
+    const uint64_t t0 = global_ns();
+    while (!mbar_try_wait_hint(bar, phase, 1000u))
+        if (global_ns() - t0 >= kTcWaitNs) return false;
+    return true;
+}
+
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t phase) {
     if (mbar_try_wait(bar, phase)) return true;
     const uint64_t t0 = global_ns();
@@ -705,7 +726,15 @@ __global__ void __launch_bounds__(kTcaThreads, 1) m2l_tca_kernel(const TcTile* _
                 const TcaMma* tb = mtab + bi * sch.nmma;
                 const int nm = sch.nmma;
                 mma_tf32_ta(tmem, tb[0].a_tmem, tb[0].b, tb[0].idesc, 0u);
-                for (int j = 1; j < nm; j++) {
+                int j = 1;
+                for (; j + 4 <= nm; j += 4) {  // table entries loaded ahead of their MMAs
+                    const TcaMma m0 = tb[j], m1 = tb[j + 1], m2 = tb[j + 2], m3 = tb[j + 3];
+                    mma_tf32_ta(tmem, m0.a_tmem, m0.b, m0.idesc, 1u);
+                    mma_tf32_ta(tmem, m1.a_tmem, m1.b, m1.idesc, 1u);
+                    mma_tf32_ta(tmem, m2.a_tmem, m2.b, m2.idesc, 1u);
+                    mma_tf32_ta(tmem, m3.a_tmem, m3.b, m3.idesc, 1u);
+                }
+                for (; j < nm; j++) {
                     const TcaMma m = tb[j];
                     mma_tf32_ta(tmem, m.a_tmem, m.b, m.idesc, 1u);
                 }
@@ -726,8 +755,9 @@ __global__ void __launch_bounds__(kTcaThreads, 1) m2l_tca_kernel(const TcTile* _
                 lookup_store(t + 4, pend);
                 pend = lookup_load(t + 5);
             }
-            // fold offset t into the running sum
-            if (!mbar_wait_bounded(&bar_m, pm)) atomicOr(err, 4), fail_sh = 1;
+            // fold offset t into the running sum (suspended while the MMAs run, so
+            // that the issuing warp keeps its issue slots)
+            if (!mbar_wait_bounded_idle(&bar_m, pm)) atomicOr(err, 4), fail_sh = 1;
             tc_fence_after();
 #pragma unroll
             for (int j = 0; j < kTcaMaxNP / 32; j++) {
