@@ -43,7 +43,7 @@ extern "C" {
 
 /* Status codes. */
 #define POLFMM_OK 0
-#define POLFMM_ERR_INVALID_ARG 1   /* n < 1, p outside [1,10], depth outside [1,8], alpha < 0, non-finite input */
+#define POLFMM_ERR_INVALID_ARG 1   /* n outside [1, 2^28], p outside [1,10], depth outside [1,8], alpha < 0, non-finite input */
 #define POLFMM_ERR_COINCIDENT 2    /* two distinct sites at the same position */
 #define POLFMM_ERR_NOT_CONVERGED 3 /* dipole solve stopped at max_iter or diverged; dipoles stay readable */
 #define POLFMM_ERR_OUT_OF_MEMORY 4

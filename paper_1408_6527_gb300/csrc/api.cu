@@ -636,7 +636,8 @@ int fmm_build(polfmm_ctx** out, int64_t n, const double* positions, const double
               int inputs_on_device) {
     if (!out) return POLFMM_ERR_INVALID_ARG;
     *out = nullptr;
-    if (n < 1 || n > (int64_t)1 << 30 || !positions || !charges || !polarizabilities) return POLFMM_ERR_INVALID_ARG;
+    // 3 n must fit the 32-bit indices of the per-component solver loops
+    if (n < 1 || n > (int64_t)1 << 28 || !positions || !charges || !polarizabilities) return POLFMM_ERR_INVALID_ARG;
     if (order_p < 1 || order_p > kMaxP || tree_depth < 1 || tree_depth > kMaxDepth) return POLFMM_ERR_INVALID_ARG;
     polfmm_options o;
     if (opt)

@@ -83,7 +83,9 @@ __global__ void reduce_final_kernel(const double* __restrict__ partial, int nslo
     }
 }
 
-#define RED_LOOP(i, n) for (int64_t i = blockIdx.x * (int64_t)kRedThreads + threadIdx.x; i < (n); i += (int64_t)kRedBlocks * kRedThreads)
+// 32-bit indices: fmm_build limits n to 2^28, so 3 n < 2^31 (i / 3 is then a
+// multiply and shift)
+#define RED_LOOP(i, n) for (int i = blockIdx.x * kRedThreads + threadIdx.x; i < (int)(n); i += kRedBlocks * kRedThreads)
 
 __device__ inline bool active_site(const double* alpha, int64_t site) { return alpha[site] > 0.0; }
 

@@ -47,12 +47,19 @@ __global__ void bbox_partial_kernel(const double* __restrict__ x, int64_t n, dou
     if (threadIdx.x < 6) part[threadIdx.x * gridDim.x + blockIdx.x] = s[threadIdx.x][0];
 }
 
+// one warp per component (min x, y, z, max x, y, z): lanes stride over the
+// block partials, then a shuffle reduction (min / max are exact in any order)
 __global__ void bbox_final_kernel(const double* __restrict__ part, int nblk, double* __restrict__ out) {
-    int a = threadIdx.x;
+    const int a = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (a >= 6) return;
-    double v = part[a * nblk];
-    for (int b = 1; b < nblk; b++) v = a < 3 ? fmin(v, part[a * nblk + b]) : fmax(v, part[a * nblk + b]);
-    out[a] = v;
+    const bool is_min = a < 3;
+    double v = is_min ? INFINITY : -INFINITY;
+    for (int b = lane; b < nblk; b += 32) v = is_min ? fmin(v, part[a * nblk + b]) : fmax(v, part[a * nblk + b]);
+    for (int o = 16; o > 0; o >>= 1) {
+        const double w = __shfl_down_sync(0xffffffffu, v, o);
+        v = is_min ? fmin(v, w) : fmax(v, w);
+    }
+    if (lane == 0) out[a] = v;
 }
 
 // ---------------------------------------------------------------------------
@@ -589,7 +596,7 @@ int tree_root_box(polfmm_ctx* c, const double* x_dev, double* part_dev, double* 
     }
     {
         LaunchScope ls(c, F_TREE);
-        bbox_final_kernel<<<1, 32, 0, c->stream>>>(part_dev, kBBoxBlocks, part_dev + 6 * kBBoxBlocks);
+        bbox_final_kernel<<<1, 6 * 32, 0, c->stream>>>(part_dev, kBBoxBlocks, part_dev + 6 * kBBoxBlocks);
     }
     cudaMemcpyAsync(h_pinned, part_dev + 6 * kBBoxBlocks, 6 * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
     if (cudaStreamSynchronize(c->stream) != cudaSuccess) return POLFMM_ERR_CUDA;
@@ -710,7 +717,7 @@ extern "C" POLFMM_API int fmm_sort_sites_noalloc(int64_t n, const double* positi
     if (cudaMemsetAsync(err, 0, sizeof(int) * 4, st) != cudaSuccess) return POLFMM_ERR_CUDA;
     // root cube: same reduction and the same FP64 rule as fmm_build
     bbox_partial_kernel<<<kBBoxBlocks, 256, 0, st>>>(positions, n, bbox);
-    bbox_final_kernel<<<1, 32, 0, st>>>(bbox, kBBoxBlocks, bbox + 6 * kBBoxBlocks);
+    bbox_final_kernel<<<1, 6 * 32, 0, st>>>(bbox, kBBoxBlocks, bbox + 6 * kBBoxBlocks);
     double hb[6];
     if (cudaMemcpyAsync(hb, bbox + 6 * kBBoxBlocks, sizeof(hb), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess)
