@@ -449,7 +449,7 @@ template <typename R>
 struct LeafCap;
 template <>
 struct LeafCap<float> {
-    static constexpr int N = 256;
+    static constexpr int N = 1024;
 };
 template <>
 struct LeafCap<double> {
@@ -463,6 +463,34 @@ struct LeafOut {
 
 __device__ inline float rsqrt_pos(float r2) { return r2 > 0.f ? rsqrtf(r2) : 0.f; }
 __device__ inline double rsqrt_pos(double r2) { return r2 > 0.0 ? rsqrt(r2) : 0.0; }
+
+// two FP32 values in one 64-bit register for the packed f32x2 arithmetic of
+// sm_100 and later (one instruction, two lanes; IEEE round to nearest)
+typedef unsigned long long F2;
+__device__ inline F2 f2_pack(float lo, float hi) {
+    F2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ inline void f2_unpack(F2 v, float& lo, float& hi) { asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v)); }
+__device__ inline F2 f2_sub(F2 a, F2 b) {
+    F2 d;
+    asm("sub.rn.ftz.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ inline F2 f2_mul(F2 a, F2 b) {
+    F2 d;
+    asm("mul.rn.ftz.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ inline F2 f2_fma(F2 a, F2 b, F2 c) {
+    F2 d;
+    asm("fma.rn.ftz.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+// a padding source for an odd count: far away (|r|^-3 underflows to zero) and
+// without dipole, so that it adds exactly zero
+constexpr float kFarPad = 3.0e18f;
 
 // dynamic shared memory of leaf_kernel<R, MODE>
 template <typename R, int MODE>
@@ -511,6 +539,10 @@ __global__ void __launch_bounds__(kLeafThreads) leaf_kernel(
     constexpr bool CHECK = MODE == LEAF_CHARGE_PHI_E;
     constexpr int IE = HAS_PHI ? 1 : 0;  // component layout: [phi] E(3) [G(6)]
     constexpr int IG = IE + 3;
+    // FP32 dipole field: two sources per thread step in packed f32x2 arithmetic;
+    // the staged sources are then stored as pairs, 12 floats per pair
+    // (x0 x1 y0 y1 | z0 z1 mx0 mx1 | my0 my1 mz0 mz1), over the sA/sB space
+    constexpr bool PACKED = MODE == LEAF_DIPOLE_E && sizeof(R) == 4;
 
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Q4<R>* sA = reinterpret_cast<Q4<R>*>(smem_raw);
@@ -589,6 +621,7 @@ __global__ void __launch_bounds__(kLeafThreads) leaf_kernel(
         R er[2][3], em[2][3];
 #pragma unroll
         for (int k = 0; k < 3; k++) er[0][k] = er[1][k] = em[0][k] = em[1][k] = R(0);
+        F2 per[3] = {0, 0, 0}, pem[3] = {0, 0, 0};  // packed er / em (PACKED)
         R xi = R(0), yi = R(0), zi = R(0);
         if (active) {
             const Q4<R> me = srcA[i];
@@ -637,6 +670,7 @@ __global__ void __launch_bounds__(kLeafThreads) leaf_kernel(
         for (int base = 0; base < total; base += CAP) {
             const int m = min(CAP, total - base);
             __syncthreads();
+#pragma unroll 4
             for (int idx = tid; idx < m; idx += blockDim.x) {
                 const int g = base + idx;
                 int lo = 0, hi = 26;  // range r with nb_pre[r] <= g < nb_pre[r + 1]
@@ -649,12 +683,56 @@ __global__ void __launch_bounds__(kLeafThreads) leaf_kernel(
                 a.x += nb_shift[lo][0];
                 a.y += nb_shift[lo][1];
                 a.z += nb_shift[lo][2];
-                sA[idx] = a;
-                if (SRC_MU) sB[idx] = srcB[j];
-                if (CHECK) sidx[idx] = j;
+                if constexpr (PACKED) {
+                    const Q4<R> mv = srcB[j];
+                    float* q = reinterpret_cast<float*>(sA) + 12 * (idx >> 1) + (idx & 1);
+                    q[0] = a.x;
+                    q[2] = a.y;
+                    q[4] = a.z;
+                    q[6] = mv.x;
+                    q[8] = mv.y;
+                    q[10] = mv.z;
+                } else {
+                    sA[idx] = a;
+                    if (SRC_MU) sB[idx] = srcB[j];
+                    if (CHECK) sidx[idx] = j;
+                }
+            }
+            if constexpr (PACKED) {
+                if ((m & 1) && tid == 0) {
+                    float* q = reinterpret_cast<float*>(sA) + 12 * (m >> 1) + 1;
+                    q[0] = q[2] = q[4] = kFarPad;
+                    q[6] = q[8] = q[10] = 0.f;
+                }
             }
             __syncthreads();
             if (!active) continue;
+            if constexpr (PACKED) {
+                // er += (mu.r) r / r^5, em += mu / r^3 for the sources 2 pp and 2 pp + 1
+                const ulonglong2* sp = reinterpret_cast<const ulonglong2*>(sA);
+                const F2 XI = f2_pack(xi, xi), YI = f2_pack(yi, yi), ZI = f2_pack(zi, zi);
+                const int np = (m + 1) >> 1;
+#pragma unroll 2
+                for (int pp = s; pp < np; pp += slices) {
+                    const ulonglong2 A = sp[3 * pp], B = sp[3 * pp + 1], C = sp[3 * pp + 2];
+                    const F2 rx = f2_sub(XI, A.x), ry = f2_sub(YI, A.y), rz = f2_sub(ZI, B.x);
+                    const F2 r2 = f2_fma(rz, rz, f2_fma(ry, ry, f2_mul(rx, rx)));
+                    float r2a, r2b;
+                    f2_unpack(r2, r2a, r2b);
+                    const F2 ri = f2_pack(rsqrt_pos(r2a), rsqrt_pos(r2b));  // 0 for the self pair
+                    const F2 ri2 = f2_mul(ri, ri);
+                    const F2 ri3 = f2_mul(ri, ri2);
+                    const F2 mr = f2_fma(C.y, rz, f2_fma(C.x, ry, f2_mul(B.y, rx)));
+                    const F2 am = f2_mul(mr, f2_mul(ri3, ri2));
+                    per[0] = f2_fma(am, rx, per[0]);
+                    per[1] = f2_fma(am, ry, per[1]);
+                    per[2] = f2_fma(am, rz, per[2]);
+                    pem[0] = f2_fma(ri3, B.y, pem[0]);
+                    pem[1] = f2_fma(ri3, C.x, pem[1]);
+                    pem[2] = f2_fma(ri3, C.y, pem[2]);
+                }
+                continue;
+            }
             // two independent accumulator sets (sources jj and jj + slices) for
             // instruction-level parallelism; added in fixed order after the loop
             auto pair = [&](R* ac, R* ar, R* am, const int jj) {
@@ -718,6 +796,18 @@ __global__ void __launch_bounds__(kLeafThreads) leaf_kernel(
         }
 #pragma unroll
         for (int k = 0; k < NC; k++) acc[k] += acc2[k];
+        if constexpr (PACKED) {
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+                float r0, r1, m0, m1;
+                f2_unpack(per[k], r0, r1);
+                f2_unpack(pem[k], m0, m1);
+                er[0][k] = r0;
+                er[1][k] = r1;
+                em[0][k] = m0;
+                em[1][k] = m1;
+            }
+        }
         if (SRC_MU) {
 #pragma unroll
             for (int k = 0; k < 3; k++) acc[IE + k] += R(3) * (er[0][k] + er[1][k]) - (em[0][k] + em[1][k]);
@@ -898,8 +988,18 @@ __global__ void __launch_bounds__(kL2PThreads) l2p_field_add_kernel(
     __syncthreads();
     if (!last) return;
     __threadfence();
+    // four loads in flight per thread
     double v = 0.0;
-    for (int k = tid; k < nleaf; k += kL2PThreads) v += __ldcg(pf.partial + k);
+    int k = tid;
+    for (; k + 3 * kL2PThreads < nleaf; k += 4 * kL2PThreads) {
+        const double a = __ldcg(pf.partial + k), b2 = __ldcg(pf.partial + k + kL2PThreads);
+        const double c2 = __ldcg(pf.partial + k + 2 * kL2PThreads), d2 = __ldcg(pf.partial + k + 3 * kL2PThreads);
+        v += a;
+        v += b2;
+        v += c2;
+        v += d2;
+    }
+    for (; k < nleaf; k += kL2PThreads) v += __ldcg(pf.partial + k);
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
     __syncthreads();
     if ((tid & 31) == 0) red[tid >> 5] = v;

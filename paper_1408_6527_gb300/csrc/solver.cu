@@ -44,7 +44,7 @@ __device__ inline bool last_block(int* ticket) {
 
 __device__ inline double sum_partials(const double* __restrict__ partial, int row, double* sh) {
     double v = 0.0;
-    for (int b = threadIdx.x; b < kRedBlocks; b += kRedThreads) v += *((volatile const double*)&partial[row * kRedBlocks + b]);
+    for (int b = threadIdx.x; b < kRedBlocks; b += kRedThreads) v += __ldcg(partial + row * kRedBlocks + b);
     return block_sum(v, sh);
 }
 
