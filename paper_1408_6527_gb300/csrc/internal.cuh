@@ -28,7 +28,7 @@ constexpr int kMaxDepth = 8;
 constexpr int kNumOffsets = 189;    // interaction-list offsets per octant class
 constexpr int kOffsetGrid = 7;      // offsets live in [-3, 3]^3
 constexpr int kM2LTileBoxes = 32;   // target boxes per multipole-to-local tile
-constexpr int kLeafTargets = 16;    // targets per near-field block (heavy leaves span several blocks)
+constexpr int kLeafTargets = 32;    // targets per near-field block (heavy leaves span several blocks)
 
 inline int ncoef_of(int p) { return (p + 1) * (p + 2) * (p + 3) / 6; }
 

@@ -504,3 +504,19 @@ def test_workload1_dipole_matrix_is_positive_definite():
                                               tol=1e-10, max_iter=200)
     assert res <= 1e-10 and it < 120
     assert oracle.rel_rms(mu2, mu) < 1e-8
+
+
+def test_smoke_input_is_positive_definite():
+    """The induced-dipole equations (Sec. II.A) have a unique solution only where
+    diag(1/alpha) - T is positive definite; the smoke cluster must lie there
+    (dense eigenvalues of the 1200 x 1200 operator)."""
+    import __graft_entry__ as g
+
+    pos, q, alpha = synth.small_random(2024, 400, box=16.0, alpha_range=g.SMOKE_ALPHA)
+    n = len(pos)
+    r = pos[:, None, :] - pos[None, :, :]
+    d = np.linalg.norm(r, axis=2)
+    np.fill_diagonal(d, np.inf)
+    T = (3 * r[:, :, :, None] * r[:, :, None, :] / d[:, :, None, None] ** 2 - np.eye(3)) / d[:, :, None, None] ** 3
+    A = np.diag(np.repeat(1 / alpha, 3)) - T.transpose(0, 2, 1, 3).reshape(3 * n, 3 * n)
+    assert np.linalg.eigvalsh(A)[0] > 0.1
