@@ -332,7 +332,7 @@ int allocate(polfmm_ctx* c) {
     c->leaf_partial = A.get<double>(c->lv[c->depth].cap);
     c->lcount = A.get<int>(c->lv[c->depth].cap);
     c->leaf_order = A.get<int>(c->lv[c->depth].cap);
-    c->leaf_items_cap = (int)std::min<int64_t>((int64_t)c->lv[c->depth].cap + n / kLeafTargets + 1, 2 * n + 1);
+    c->leaf_items_cap = (int)std::min<int64_t>((int64_t)c->lv[c->depth].cap + n / kLeafTargetsMin + 1, 2 * n + 1);
     c->leaf_items = A.get<int2>(c->leaf_items_cap);
     c->leaf_nitems = A.get<int>(4);
     if (!A.ok) return POLFMM_ERR_OUT_OF_MEMORY;

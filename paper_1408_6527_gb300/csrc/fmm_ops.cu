@@ -567,7 +567,7 @@ __global__ void __launch_bounds__(kLeafThreads) leaf_kernel(
     const int2 item = items[blockIdx.x];
     const int b = item.x;
     const int s0 = lstart[b], cnt = lcount[b];
-    const int t_lo = item.y, t_hi = min(cnt, item.y + kLeafTargets);  // this block's targets
+    const int t_lo = item.y, t_hi = min(cnt, item.y + leaf_targets(sizeof(R) == 4));  // this block's targets
     const int tid = threadIdx.x;
     if (tid < 32) {
         int c = 0;

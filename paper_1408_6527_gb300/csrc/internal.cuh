@@ -28,7 +28,13 @@ constexpr int kMaxDepth = 8;
 constexpr int kNumOffsets = 189;    // interaction-list offsets per octant class
 constexpr int kOffsetGrid = 7;      // offsets live in [-3, 3]^3
 constexpr int kM2LTileBoxes = 32;   // target boxes per multipole-to-local tile
-constexpr int kLeafTargets = 32;    // targets per near-field block (heavy leaves span several blocks)
+// targets per near-field block (heavy leaves span several blocks): the FP32
+// kernel stages up to 1,024 sources per chunk and gains from serving more
+// targets with each; the FP64 kernel stages 128 and is fastest at 16
+constexpr int kLeafTargetsF32 = 64;
+constexpr int kLeafTargetsF64 = 16;
+constexpr int kLeafTargetsMin = 16;  // bound of the work-list length
+__host__ __device__ constexpr int leaf_targets(bool fp32) { return fp32 ? kLeafTargetsF32 : kLeafTargetsF64; }
 
 inline int ncoef_of(int p) { return (p + 1) * (p + 2) * (p + 3) / 6; }
 
@@ -132,7 +138,7 @@ struct polfmm_ctx {
     int2* leaf_items = nullptr;   // near-field blocks: (leaf, first target), heaviest leaves first
     int* leaf_nitems = nullptr;   // device count of leaf_items
     int leaf_items_cap = 0;       // capacity of leaf_items
-    int leaf_items_grid = 0;      // launch bound of the current tree: leaves + n / kLeafTargets + 1
+    int leaf_items_grid = 0;      // launch bound of the current tree: leaves + n / leaf_targets + 1
     polfmm::Level lv[polfmm::kMaxDepth + 1];
     polfmm::Tables tab;
     // M2L work list

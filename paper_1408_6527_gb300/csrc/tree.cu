@@ -413,22 +413,22 @@ __global__ void leaf_work_kernel(int nleaf, int depth, const int* __restrict__ l
     idx[b] = b;
 }
 
-// near-field blocks: leaf r of the work order covers ceil(count / kLeafTargets)
-// blocks of at most kLeafTargets targets each
+// near-field blocks: leaf r of the work order covers ceil(count / targets)
+// blocks of at most targets targets each
 __global__ void leaf_split_count_kernel(int nleaf, const int* __restrict__ order, const int* __restrict__ lcount,
-                                        int* __restrict__ nsplit) {
+                                        int targets, int* __restrict__ nsplit) {
     int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= nleaf) return;
-    nsplit[r] = (lcount[order[r]] + kLeafTargets - 1) / kLeafTargets;
+    nsplit[r] = (lcount[order[r]] + targets - 1) / targets;
 }
 
 __global__ void leaf_items_kernel(int nleaf, const int* __restrict__ order, const int* __restrict__ lcount,
-                                  const int* __restrict__ first, int2* __restrict__ items, int cap) {
+                                  const int* __restrict__ first, int targets, int2* __restrict__ items, int cap) {
     int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= nleaf) return;
     const int b = order[r], cnt = lcount[b];
     int o = first[r];
-    for (int t = 0; t < cnt && o < cap; t += kLeafTargets) items[o++] = make_int2(b, t);
+    for (int t = 0; t < cnt && o < cap; t += targets) items[o++] = make_int2(b, t);
 }
 
 int tree_build(polfmm_ctx* c, const double* x_in) {
@@ -557,16 +557,19 @@ int tree_tables(polfmm_ctx* c, const double* x_in, const double* q_in, const dou
         // heavy leaves split by targets, in the same order
         {
             LaunchScope ls(c, F_TREE);
-            leaf_split_count_kernel<<<grid_for(nl, 256), 256, 0, st>>>(nl, c->leaf_order, c->lcount, c->flags);
+            leaf_split_count_kernel<<<grid_for(nl, 256), 256, 0, st>>>(nl, c->leaf_order, c->lcount,
+                                                                       leaf_targets(c->mixed), c->flags);
         }
         scan_exclusive_dev(c, c->flags, c->val_a, nullptr, nl, c->leaf_nitems);
         {
             LaunchScope ls(c, F_TREE);
             leaf_items_kernel<<<grid_for(nl, 256), 256, 0, st>>>(nl, c->leaf_order, c->lcount, c->val_a,
-                                                                 c->leaf_items, c->leaf_items_cap);
+                                                                 leaf_targets(c->mixed), c->leaf_items,
+                                                                 c->leaf_items_cap);
         }
     }
-    c->leaf_items_grid = (int)std::min<int64_t>(c->leaf_items_cap, (int64_t)c->h_counts[d] + n / kLeafTargets + 1);
+    c->leaf_items_grid =
+        (int)std::min<int64_t>(c->leaf_items_cap, (int64_t)c->h_counts[d] + n / leaf_targets(c->mixed) + 1);
     for (int l = 0; l <= d; l++) {
         Level& B = c->lv[l];
         B.nbox = c->h_counts[l];
