@@ -234,6 +234,24 @@ WORKLOADS = {"globule30k": (2, None), "cube1k": (1, None), "ring300k": (3, None)
              "shell250k": (5, 250000), "shell1M": (5, 1000000), "shell4M": (5, 4000000)}
 
 
+def max_over_ranks(total_ms, dist, device):
+    """The job's time is the slowest rank's: MAX all-reduce of the timed
+    interval (a no-op on one rank)."""
+    if not dist:
+        return total_ms
+    import torch
+    import torch.distributed as tdist
+
+    t = torch.tensor([total_ms], dtype=torch.float64, device=device)
+    tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world, n, steps, total_ms):
+    """Whole-job atoms/s: every rank runs an independent replica of n sites."""
+    return world * n * steps / (total_ms / 1e3)
+
+
 def make_workload(name):
     import synth
 
@@ -300,17 +318,14 @@ def run_gpu(args, rank, world, local_rank):
 
     ctx = make(args.mode)
     total_ms, iters, launches, info, out, clocks = timed(ctx, args.mode, args.steps, args.warmup, True)
-    if dist:
-        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, dist, "cuda")
     F_main = out["F"].detach().cpu().numpy()
     lo, side = ctx.root_box()
     ctx.close()
     if rank != 0:
         return None
     ms_per_step = total_ms / args.steps
-    value = world * n * args.steps / (total_ms / 1e3)
+    value = job_value(world, n, args.steps, total_ms)
     if args.only_main:
         return {"metric": METRIC, "value": round(value, 1), "unit": "atoms/s", "ms_per_step": round(ms_per_step, 4),
                 "iterations": iters[-1], "gpu_launches": int(launches), "only_main": True}
