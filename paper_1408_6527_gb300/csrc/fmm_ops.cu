@@ -432,11 +432,13 @@ __global__ void __launch_bounds__(256) m2l_simt_kernel(const M2LTile* __restrict
 //
 // Sources are packed per site as two 4-vectors: (x, y, z, q) with x relative
 // to the site's own leaf centre, and (mu_x, mu_y, mu_z, 0).  One block per
-// target leaf stages the sources of all 27 neighbour leaves (shifted into the
-// target leaf's frame, exact small-integer multiples of the leaf side) into
-// shared memory with one barrier pair per CAP sources; thread (t, s) owns
-// target t and every slices-th source, and the slices are added in a fixed
-// order at the end.  The self pair has r = 0 exactly and is masked.
+// work item (a leaf and up to leaf_targets of its sites) stages the sources
+// of all 27 neighbour leaves (shifted into the target leaf's frame, exact
+// small-integer multiples of the leaf side) into shared memory with one
+// barrier pair per CAP sources; thread (t, s) owns target t and every
+// slices-th source (the FP32 dipole field: every slices-th pair of sources),
+// and the slices are added in a fixed order at the end.  The self pair has
+// r = 0 exactly and is masked.
 // ---------------------------------------------------------------------------
 constexpr int kLeafThreads = 256;
 
