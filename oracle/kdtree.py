@@ -140,8 +140,27 @@ def _zero(v, shape):
     return np.zeros(shape) if v is None else v
 
 
-def kdtree_fields(pos, q=None, mu=None, p=5, theta=0.5, n_bucket=8, n_direct=64, pad=1e-3):
-    """Phi, E and G = grad E at every site by the kd-tree FMM of Sec. III."""
+def _leaf_multipole(p, z, x, q, mu, dl):
+    """P2M of a leaf. With dl > 0 each point dipole enters as the pair of
+    Sec. II.C: charges +q_mu at x + dl mu/|mu| and -q_mu at x - dl mu/|mu|,
+    q_mu = |mu| / (2 dl), so that mu = 2 q_mu dl; dl = 0 takes the analytic
+    point-dipole multipole (the dl -> 0 limit)."""
+    if dl <= 0.0:
+        return p2m(p, z, x, q, mu)
+    norm = np.linalg.norm(mu, axis=1)
+    has = norm > 0.0
+    u = mu[has] / norm[has, None]
+    qm = norm[has] / (2.0 * dl)
+    pts = np.concatenate([x, x[has] + dl * u, x[has] - dl * u])
+    chg = np.concatenate([q, qm, -qm])
+    return p2m(p, z, pts, chg, None)
+
+
+def kdtree_fields(pos, q=None, mu=None, p=5, theta=0.5, n_bucket=8, n_direct=64, pad=1e-3, dipole_dl=0.0):
+    """Phi, E and G = grad E at every site by the kd-tree FMM of Sec. III.
+    dipole_dl > 0 builds the multipoles of the dipoles from the +-q pairs of
+    Sec. II.C at that separation; the direct sums always use the dipoles
+    themselves, as the paper does."""
     pos = np.asarray(pos, dtype=np.float64)
     n = pos.shape[0]
     qv = _zero(None if q is None else np.asarray(q, dtype=np.float64), n)
@@ -152,7 +171,7 @@ def kdtree_fields(pos, q=None, mu=None, p=5, theta=0.5, n_bucket=8, n_direct=64,
     # upward pass: P2M at the leaves about their centres, M2M to the parents
     for c in reversed(allc):
         if c.leaf:
-            c.M = p2m(p, c.z, pos[c.idx], qv[c.idx], mv[c.idx])
+            c.M = _leaf_multipole(p, c.z, pos[c.idx], qv[c.idx], mv[c.idx], dipole_dl)
         else:
             c.M = sum(m2m(p, c.z - ch.z, ch.M) for ch in c.children)
         c.F = np.zeros(nc)

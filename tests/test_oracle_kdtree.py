@@ -111,3 +111,38 @@ def test_sphere_test_matches_the_paper():
     e = oracle.per_site_rel_err(q[:, None] * f["E"], q[:, None] * d["E"])
     assert (e < 1e-4).mean() >= g["fraction_below_1e-4"]
     assert e.max() < g["max_rel_force_error"]
+
+
+def _sphere_with_dipoles():
+    g = json.load(open(os.path.join(GOLDEN, "paper_sphere_test.json")))
+    pos, q = _sphere(16, g["n_sites"], g["radius_A"])
+    mu = _rng(17).normal(0.0, 0.2, pos.shape)
+    return g, pos, q, mu
+
+
+def test_dipole_pairs_approach_the_analytic_multipole_as_dl_squared():
+    """Sec. II.C: a dipole is the +-q pair with mu = 2 q_mu dl; its multipoles
+    differ from the point dipole's by O(dl^2)."""
+    g, pos, q, mu = _sphere_with_dipoles()
+    a = kdtree.kdtree_fields(pos, q, mu, p=g["order_p"], theta=g["theta"])
+    diff = [oracle.rel_rms(kdtree.kdtree_fields(pos, q, mu, p=g["order_p"], theta=g["theta"], dipole_dl=dl)["E"],
+                           a["E"]) for dl in (1e-1, 1e-2)]
+    assert 98.0 < diff[0] / diff[1] < 102.0
+
+
+def test_dipole_pair_separation_leaves_the_error_distribution_unchanged():
+    """Sec. IV.A, Fig. pol-radius: over dl = 1e-5 ... 1e-1 A the paper finds no
+    difference in the force errors at theta = 0.5."""
+    g, pos, q, mu = _sphere_with_dipoles()
+    d = oracle.direct_fields(pos, q, mu)
+
+    def dist(dl):
+        f = kdtree.kdtree_fields(pos, q, mu, p=g["order_p"], theta=g["theta"], dipole_dl=dl)
+        e = oracle.per_site_rel_err(f["E"], d["E"])
+        return np.percentile(e, 80), (e < 1e-4).mean()
+
+    p80, frac = dist(0.0)
+    for dl in (1e-5, 1e-3, 1e-1):
+        p80_dl, frac_dl = dist(dl)
+        assert abs(p80_dl - p80) < 1e-3 * p80
+        assert abs(frac_dl - frac) < 1e-3
