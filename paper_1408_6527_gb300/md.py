@@ -86,8 +86,30 @@ class Repulsion:
         return float(U), F
 
 
+def respa(x, v, acc_slow, acc_fast, slow, fast, dt, inner):
+    """One outer step of the reversible multiple-time-step integrator (r-RESPA):
+    a half kick of the slow acceleration over the outer step inner * dt,
+    `inner` velocity-Verlet steps of dt under the fast acceleration, and the
+    closing slow half kick. slow(x) and fast(x) return accelerations; the
+    accelerations at the current x are passed in and the new ones returned:
+    (x, v, acc_slow, acc_fast). With inner = 1 this is velocity Verlet under
+    the sum of the two."""
+    h = 0.5 * inner * dt
+    v = v + h * acc_slow
+    for _ in range(inner):
+        v = v + 0.5 * dt * acc_fast
+        x = x + dt * v
+        acc_fast = fast(x)
+        v = v + 0.5 * dt * acc_fast
+    acc_slow = slow(x)
+    v = v + h * acc_slow
+    return x, v, acc_slow, acc_fast
+
+
 class Dynamics:
-    """Velocity Verlet with FMM electrostatics + polarization and the wall."""
+    """Velocity Verlet with FMM electrostatics + polarization and the wall;
+    with inner > 1 the multiple-time-step form (the FMM forces every inner
+    steps, the wall every step)."""
 
     def __init__(self, pos, q, alpha, masses, p=6, depth=5, mode="fp64", tol=1e-8, repulsion=None):
         import torch
@@ -117,9 +139,20 @@ class Dynamics:
     def kinetic(self, v):
         return float(0.5 * (self.m[:, None] * v * v).sum() / ACC)
 
-    def run(self, v, steps, dt=1.0):
+    def _slow(self):
+        """FMM electrostatics and polarization at self.x: (U, F)."""
+        self.fmm.update_positions(self.x)
+        info = self.fmm.solve(self.tol)
+        self.iterations.append(info["iterations"])
+        out = self.fmm.energy_forces(forces=True, dq=False, dalpha=False)
+        return out["U"], out["F"]
+
+    def run(self, v, steps, dt=1.0, inner=1):
         """Returns the total energy before and after each step (kcal/mol) and the
-        final velocities."""
+        final velocities. With inner > 1 a step is one outer step of inner * dt:
+        the wall is integrated at dt and the FMM forces at inner * dt (r-RESPA)."""
+        if inner > 1:
+            return self._run_respa(v, steps, dt, inner)
         H = [self.kinetic(v) + self.U]
         a = self.F / self.m[:, None] * ACC
         for _ in range(steps):
@@ -129,6 +162,30 @@ class Dynamics:
             a = self.F / self.m[:, None] * ACC
             v = v + 0.5 * dt * a
             H.append(self.kinetic(v) + self.U)
+        return np.array(H), v
+
+    def _run_respa(self, v, steps, dt, inner):
+        inv_m = ACC / self.m[:, None]
+        ur, fr = self.rep(self.x)
+        us, fs = self.U - ur, self.F - fr  # the first forces hold both parts
+        state = {"ur": ur, "us": us}
+
+        def fast(x):
+            state["ur"], f = self.rep(x)
+            return f * inv_m
+
+        def slow(x):
+            self.x = x
+            state["us"], f = self._slow()
+            return f * inv_m
+
+        H = [self.kinetic(v) + us + ur]
+        a_s, a_f = fs * inv_m, fr * inv_m
+        for _ in range(steps):
+            self.x, v, a_s, a_f = respa(self.x, v, a_s, a_f, slow, fast, dt, inner)
+            H.append(self.kinetic(v) + state["us"] + state["ur"])
+        self.U = state["us"] + state["ur"]
+        self.F = (a_s + a_f) / inv_m
         return np.array(H), v
 
     def close(self):
@@ -200,6 +257,8 @@ def main(argv=None):
     ap.add_argument("--sites", type=int, default=100000)
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--dt", type=float, default=1.0)
+    ap.add_argument("--inner", type=int, default=1,
+                    help="wall steps per FMM force evaluation (multiple time steps; 1 = velocity Verlet)")
     ap.add_argument("--temperature", type=float, default=300.0)
     ap.add_argument("--fd-sites", type=int, default=64)
     ap.add_argument("--alpha-scale", type=float, default=0.5)
@@ -210,7 +269,8 @@ def main(argv=None):
     masses = rng.uniform(1.0, 16.0, w.n)
     v0 = maxwell_velocities(masses, args.temperature, args.seed + 1)
     result = {"config": {"workload": f"globule {w.n} sites p={w.p} depth={w.depth}", "steps": args.steps,
-                         "dt_fs": args.dt, "temperature_K": args.temperature, "masses_amu": "U(1, 16)",
+                         "dt_fs": args.dt, "inner_steps": args.inner, "temperature_K": args.temperature,
+                         "masses_amu": "U(1, 16)",
                          "repulsion": "repulsive Lennard-Jones wall, eps 5 kcal/mol, sigma 2.05 A, zero beyond 2.30 A",
                          "alpha_scale_dynamics": args.alpha_scale}}
     if args.fd_sites > 0:
@@ -223,7 +283,7 @@ def main(argv=None):
         v = torch.as_tensor(v0, dtype=torch.float64, device="cuda")
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        H, v = dyn.run(v, args.steps, args.dt)
+        H, v = dyn.run(v, args.steps, args.dt, args.inner)
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
         ke0 = float(0.5 * (masses[:, None] * v0 * v0).sum() / ACC)

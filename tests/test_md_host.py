@@ -61,3 +61,74 @@ def test_maxwell_velocities_have_no_net_momentum_and_the_target_temperature():
     ke = 0.5 * (masses[:, None] * v * v).sum() / md.ACC  # kcal/mol
     T = 2 * ke / (3 * masses.shape[0] * md.KB)
     assert abs(T - 300.0) < 6.0  # 3 N = 60,000 degrees of freedom: sd ~ 300 sqrt(2 / 3N) = 1.7 K
+
+
+def _chain(n=16, seed=0):
+    """Stiff springs along a chain (fast) in a weak harmonic trap (slow), unit masses."""
+    g = torch.Generator().manual_seed(seed)
+    x0 = torch.randn(n, 3, dtype=torch.float64, generator=g) * 3
+    v0 = torch.randn(n, 3, dtype=torch.float64, generator=g) * 0.3
+    L0 = torch.linalg.norm(x0[1:] - x0[:-1], dim=1)
+
+    def fast_u(x):
+        d = torch.linalg.norm(x[1:] - x[:-1], dim=1)
+        return 0.5 * ((d - L0) ** 2).sum()
+
+    def slow_u(x):
+        return 0.5 * 0.0025 * (x * x).sum()
+
+    def acc(u):
+        def f(x):
+            x = x.clone().requires_grad_(True)
+            (g_,) = torch.autograd.grad(u(x), x)
+            return -g_.detach()
+        return f
+
+    return x0, v0, acc(slow_u), acc(fast_u), lambda x, v: float(0.5 * (v * v).sum() + fast_u(x) + slow_u(x))
+
+
+def test_respa_with_one_inner_step_is_velocity_verlet():
+    x0, v0, slow, fast, _ = _chain()
+    x, v, a_s, a_f = x0, v0, slow(x0), fast(x0)
+    xv, vv = x0, v0
+    a = slow(xv) + fast(xv)
+    for _ in range(50):
+        x, v, a_s, a_f = md.respa(x, v, a_s, a_f, slow, fast, 0.05, 1)
+        vv = vv + 0.025 * a
+        xv = xv + 0.05 * vv
+        a = slow(xv) + fast(xv)
+        vv = vv + 0.025 * a
+    assert torch.abs(x - xv).max() < 1e-12 and torch.abs(v - vv).max() < 1e-12
+
+
+def test_respa_is_time_reversible():
+    x0, v0, slow, fast, _ = _chain()
+    x, v, a_s, a_f = x0, v0, slow(x0), fast(x0)
+    for _ in range(100):
+        x, v, a_s, a_f = md.respa(x, v, a_s, a_f, slow, fast, 0.05, 10)
+    v = -v
+    for _ in range(100):
+        x, v, a_s, a_f = md.respa(x, v, a_s, a_f, slow, fast, 0.05, 10)
+    assert torch.abs(x - x0).max() < 1e-9 and torch.abs(v + v0).max() < 1e-9
+
+
+def test_respa_is_stable_where_verlet_at_the_outer_step_is_not():
+    """The point of multiple time steps: the slow force at a step (1.5) past
+    the stability limit of the fast springs, which are integrated at 0.05."""
+    x0, v0, slow, fast, energy = _chain()
+    H0 = energy(x0, v0)
+    x, v, a_s, a_f = x0, v0, slow(x0), fast(x0)
+    dev = 0.0
+    for _ in range(400):
+        x, v, a_s, a_f = md.respa(x, v, a_s, a_f, slow, fast, 0.05, 30)
+        dev = max(dev, abs(energy(x, v) - H0))
+    assert dev < 1e-2 * H0
+    xv, vv = x0, v0
+    a = slow(xv) + fast(xv)
+    for _ in range(400):
+        vv = vv + 0.75 * a
+        xv = xv + 1.5 * vv
+        a = slow(xv) + fast(xv)
+        vv = vv + 0.75 * a
+    Hv = energy(xv, vv)
+    assert not np.isfinite(Hv) or abs(Hv - H0) > 1.0 * H0
