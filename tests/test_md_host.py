@@ -132,3 +132,48 @@ def test_respa_is_stable_where_verlet_at_the_outer_step_is_not():
         vv = vv + 0.75 * a
     Hv = energy(xv, vv)
     assert not np.isfinite(Hv) or abs(Hv - H0) > 1.0 * H0
+
+
+class _TrapFMM:
+    """Stands in for the FMM context: an analytic slow force (a harmonic trap)
+    with the context's update / solve / energy_forces calls."""
+
+    def __init__(self, k=0.3):
+        self.k, self.x = k, None
+
+    def update_positions(self, x):
+        self.x = x
+
+    def solve(self, tol):
+        return {"iterations": 1}
+
+    def energy_forces(self, forces=True, dq=False, dalpha=False):
+        return {"U": float(0.5 * self.k * (self.x * self.x).sum()), "F": -self.k * self.x}
+
+
+def test_dynamics_multiple_time_steps_drive_the_slow_and_fast_forces():
+    x0 = torch.as_tensor(synth.workload(1).pos)
+    x0 = x0 - x0.mean(0)
+    n = x0.shape[0]
+    m = torch.full((n,), 12.0, dtype=torch.float64)
+    v0 = torch.as_tensor(md.maxwell_velocities(m.numpy(), 300.0, 3))
+    dyn = md.Dynamics.__new__(md.Dynamics)
+    dyn.x, dyn.m, dyn.tol, dyn.iterations = x0.clone(), m, 1e-8, []
+    dyn.rep, dyn.fmm = md.Repulsion(), _TrapFMM()
+    dyn.fmm.update_positions(dyn.x)
+    u_s = dyn.fmm.energy_forces()
+    u_r, f_r = dyn.rep(dyn.x)
+    dyn.U, dyn.F = u_s["U"] + u_r, u_s["F"] + f_r
+    H, v = dyn.run(v0.clone(), 20, dt=0.5, inner=4)
+    # the same steps through the integrator itself
+    inv_m = md.ACC / m[:, None]
+    slow = lambda x: -0.3 * x * inv_m
+    fast = lambda x: md.Repulsion()(x)[1] * inv_m
+    x, vv, a_s, a_f = x0.clone(), v0.clone(), slow(x0), fast(x0)
+    for _ in range(20):
+        x, vv, a_s, a_f = md.respa(x, vv, a_s, a_f, slow, fast, 0.5, 4)
+    assert torch.abs(dyn.x - x).max() < 1e-12 and torch.abs(v - vv).max() < 1e-12
+    assert len(dyn.iterations) == 20  # one slow solve per outer step
+    ke = 0.5 * (m[:, None] * v * v).sum() / md.ACC
+    assert abs(H[-1] - (float(ke) + 0.5 * 0.3 * float((x * x).sum()) + md.Repulsion()(x)[0])) < 1e-9 * abs(H[-1])
+    assert np.abs(H - H[0]).max() < 1e-2 * float(0.5 * (m[:, None] * v0 * v0).sum() / md.ACC)
