@@ -1,0 +1,61 @@
+"""The work counts behind the benchmark's roofline figures, against brute
+force: M2L flops per box pair, tensor-core MACs issued per tile row, near-field
+pairs and far-field box pairs of the octree; and the tolerance rule."""
+import itertools
+
+import numpy as np
+
+import bench
+import oracle
+import synth
+
+
+def test_m2l_flops_per_box_pair_counts_the_retained_terms():
+    # F_n += sum_{|m| <= p - |n|} D_{n+m} M_m: one multiply-add per (n, m) with |n| + |m| <= p
+    for p in range(1, 9):
+        mis = [t for t in itertools.product(range(p + 1), repeat=3) if sum(t) <= p]
+        pairs = sum(1 for n in mis for m in mis if sum(n) + sum(m) <= p)
+        assert bench.m2l_flops_per_box_pair(p) == 2 * pairs
+    assert bench.m2l_flops_per_box_pair(6) == 1848
+
+
+def test_tensor_core_macs_issued_per_row():
+    """Inputs in degree order in steps of 8; each step is one MMA whose N is the
+    number of outputs it can feed (|n| <= p - degree of the step's first input),
+    rounded up to 16, with K = 8."""
+    for p in range(2, 9):
+        deg = [int(d) for d in oracle.multi_indices(p).sum(1)]  # degree order, as the kernel stores them
+        nc = len(deg)
+        macs = 0
+        for k0 in range(0, nc, 8):
+            feeds = sum(1 for d in deg if d <= p - deg[k0])
+            macs += max(16, -(-feeds // 16) * 16) * 8
+        assert bench.tc_issued_macs_per_row(p) == macs
+    assert bench.tc_issued_macs_per_row(6) == 2432
+
+
+def test_tree_work_counts_pairs_by_brute_force():
+    w = synth.workload(1)
+    lo, side = oracle.root_box(w.pos)
+    depth = 3
+    near, boxes, _ = bench.tree_work(w.pos, depth, lo, side)
+    cells = oracle.leaf_cells(w.pos, depth, lo, side).astype(np.int64)
+    # ordered site pairs i != j in adjacent (or the same) leaves
+    adj = np.abs(cells[:, None, :] - cells[None, :, :]).max(axis=2) <= 1
+    assert near == int(adj.sum()) - w.n
+    # box pairs at each level >= 2: occupied target and source, not adjacent, parents adjacent
+    total = 0
+    for l in range(2, depth + 1):
+        occ = sorted({tuple(c) for c in (cells >> (depth - l)).tolist()})
+        for t in occ:
+            for s in occ:
+                d = max(abs(a - b) for a, b in zip(t, s))
+                dp = max(abs((a >> 1) - (b >> 1)) for a, b in zip(t, s))
+                total += d > 1 and dp <= 1
+    assert boxes == total
+
+
+def test_tolerance_rule():
+    assert bench.tol_for("fp64", 10 ** 6) == 1e-8
+    assert bench.tol_for("mixed", 100_000) == 1e-6
+    assert bench.tol_for("mixed", 100_001) == 3e-7
