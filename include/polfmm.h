@@ -25,6 +25,10 @@
  *   - no call traps, aborts or prints; every int-returning call returns one
  *     of the POLFMM_* status codes below.
  *   - calls on one context must not overlap; distinct contexts are independent.
+ *   - every reduction (energies, dot products of the solver, the partial sums of
+ *     the multipole-to-local pass) adds its terms in a fixed order, so the same
+ *     inputs give bitwise identical outputs on every run; there is no
+ *     non-deterministic fast path to switch off.
  */
 #ifndef POLFMM_H
 #define POLFMM_H
@@ -120,8 +124,15 @@ POLFMM_API int fmm_build(polfmm_ctx** ctx, int64_t n, const double* positions, c
  * mu = alpha E^q.  Stops when ||r||_2 / ||E^q||_2 <= tolerance, r the residual
  * of (diag(1/alpha) - T) mu = E^q, or after max_iter iterations.
  * iterations_out / residual_out (nullable) receive the count and final
- * relative residual.  Returns POLFMM_ERR_NOT_CONVERGED when the cap is hit or
- * the residual turns non-finite; the dipoles stay readable.
+ * relative residual.  Returns POLFMM_ERR_NOT_CONVERGED, with the dipoles and
+ * residual of the last good iterate readable, when
+ *   - the cap is hit;
+ *   - the residual turns non-finite;
+ *   - a conjugate direction has d.(diag(1/alpha) - T) d <= 0: the operator is
+ *     not positive definite (the polarization catastrophe of point dipoles);
+ *     that direction is not applied;
+ *   - the residual grew in 3 consecutive iterations (stagnation, or a
+ *     diverging fixed-point iteration).
  */
 POLFMM_API int fmm_solve_induced_dipoles(polfmm_ctx* ctx, double tolerance, int* iterations_out,
                               double* residual_out);
@@ -142,6 +153,19 @@ POLFMM_API int fmm_solve_induced_dipoles(polfmm_ctx* ctx, double tolerance, int*
  */
 POLFMM_API int fmm_energy_forces(polfmm_ctx* ctx, double* energy_out, double* forces, double* dU_dq,
                       double* dU_dalpha, int outputs_on_device);
+
+/*
+ * Stationary energy without the force pass: energy_out (host, 3 doubles) =
+ * [U, U^qq', U^pol] with U^qq' = 1/2 sum q Phi^q (Sec. II.A, Eq. equ:Uqq) and
+ * U^pol = -1/2 sum mu.E^q, the value of the polarization energy at the solution
+ * of the dipole equations (Sec. II.A, Eq. upol_derivatives), both times
+ * coulomb_k.  Uses the static pass of the tree and the current dipoles, summed
+ * in float64 in a fixed order.  Valid after a converged
+ * fmm_solve_induced_dipoles; for arbitrary dipoles (fmm_set_dipoles) use
+ * fmm_energy_forces, whose U^pol is the full expression.  POLFMM_ERR_STATE
+ * before any dipoles exist.
+ */
+POLFMM_API int fmm_energy(polfmm_ctx* ctx, double* energy_out);
 
 /* Copy the current induced dipoles (n x 3) out; POLFMM_ERR_STATE before any. */
 POLFMM_API int fmm_get_dipoles(polfmm_ctx* ctx, double* mu, int on_device);
@@ -199,6 +223,15 @@ POLFMM_API int fmm_profile_reset(polfmm_ctx* ctx);
 POLFMM_API int64_t fmm_launch_count(polfmm_ctx* ctx);
 
 /*
+ * Testing hook for the out-of-memory paths (the paper has no counterpart).
+ * Returns how many device or pinned-host allocations the library made since
+ * the previous call, and arms a planted failure: the fail_at-th allocation
+ * from now (0 = the next one) reports out of memory, once; fail_at < 0
+ * disarms it.  Process-wide, not thread-safe against concurrent builds.
+ */
+POLFMM_API int64_t fmm_testing_alloc_hook(int64_t fail_at);
+
+/*
  * Allocation-free tree set-up.  The paper has no counterpart: this entry point
  * exists for callers that cannot call cudaMalloc -- code whose host framework
  * owns all device memory through its own pool, or a time-critical loop that
@@ -225,7 +258,9 @@ POLFMM_API int64_t fmm_launch_count(polfmm_ctx* ctx);
  * device which loads the library holds until the process exits.  The first
  * call on a device looks up that array's device address (cudaGetSymbolAddress,
  * with that device current), so that first call should come before any stream
- * capture.  Every call shares the array and it keeps the previous call's
+ * capture.  The address is kept for the life of the process: a
+ * cudaDeviceReset unloads the module and makes it stale, so a process that
+ * resets a device must not call this entry point on that device afterwards.  Every call shares the array and it keeps the previous call's
  * contents: calls that overlap on the GPU (several streams, threads or
  * devices sharing a context) race and must be serialised by the caller.
  * Non-finite positions return POLFMM_ERR_INVALID_ARG.

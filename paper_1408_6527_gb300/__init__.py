@@ -151,6 +151,13 @@ class PolFMM:
         _lib.check(st, "fmm_energy_forces")
         return {"U": float(e[0]), "Uqq": float(e[1]), "Upol": float(e[2]), "F": F, "dUdq": Q, "dUdalpha": A}
 
+    def energy(self):
+        """Stationary energy [U, U^qq', U^pol] at the current (converged) dipoles,
+        reduced in the library (no force pass)."""
+        e = np.zeros(3)
+        _lib.check(self.lib.fmm_energy(self.h, e.ctypes.data_as(ctypes.c_void_p)), "fmm_energy")
+        return {"U": float(e[0]), "Uqq": float(e[1]), "Upol": float(e[2])}
+
     # -- accessors ----------------------------------------------------------------
     def dipoles(self):
         out, p = self._out(self.n, 3)

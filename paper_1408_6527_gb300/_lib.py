@@ -57,6 +57,7 @@ SIGNATURES = {
     "fmm_build": (I, [ctypes.POINTER(P), I64, P, P, P, I, I, ctypes.POINTER(Options), I]),
     "fmm_solve_induced_dipoles": (I, [P, D, ctypes.POINTER(I), ctypes.POINTER(D)]),
     "fmm_energy_forces": (I, [P, P, P, P, P, I]),
+    "fmm_energy": (I, [P, P]),
     "fmm_get_dipoles": (I, [P, P, I]),
     "fmm_set_dipoles": (I, [P, P, I]),
     "fmm_update_positions": (I, [P, P, I]),
@@ -70,6 +71,7 @@ SIGNATURES = {
     "fmm_profile_get": (I, [P, ctypes.c_char_p, ctypes.POINTER(D), ctypes.POINTER(I64)]),
     "fmm_profile_reset": (I, [P]),
     "fmm_launch_count": (I64, [P]),
+    "fmm_testing_alloc_hook": (I64, [I64]),
     "fmm_destroy": (None, [P]),
     "fmm_sort_sites_noalloc": (I, [I64, P, I, P, P, P, P, P, P]),
     "fmm_status_string": (ctypes.c_char_p, [I]),

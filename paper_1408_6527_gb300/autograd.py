@@ -1,8 +1,8 @@
 """Energy of charges plus induced point dipoles as a differentiable function.
 
 Forward: build the octree, run the static pass and solve the induced dipoles
-(Sec. III, stages 1 and 2); the energy comes from the stationary form
-U^pol = -1/2 sum mu.E^q, valid at the solution (Eq. upol_derivatives).
+(Sec. III, stages 1 and 2); the library reduces the energy in the stationary
+form U^pol = -1/2 sum mu.E^q, valid at the solution (Eq. upol_derivatives).
 Backward: one more FMM pass with charges and dipoles as sources (stage 3).
 Because dU^pol/dmu = 0 at the solution, the gradients need no derivative of
 the dipole iterations: dU/dx = -(q E + (grad E) mu), dU/dq = Phi,
@@ -34,8 +34,10 @@ class _PolarizableEnergy(torch.autograd.Function):
 
 
 class _PolarizableEnergyTwoPass(torch.autograd.Function):
-    """Forward keeps the context (tree, static pass, dipoles); backward runs the
-    force pass on it, so the gradient pass happens only when asked for."""
+    """Forward keeps the context (tree, static pass, dipoles) and takes the
+    stationary energy from the library; the first backward runs the force pass
+    on it, so the gradient pass happens only when asked for.  The gradients are
+    kept, so a second backward (retain_graph=True) reuses them."""
 
     @staticmethod
     def forward(ctx, pos, q, alpha, p, depth, mode, tol, max_iter, coulomb_k, root_box):
@@ -44,20 +46,21 @@ class _PolarizableEnergyTwoPass(torch.autograd.Function):
         fmm = PolFMM(pos.detach(), q.detach(), alpha.detach(), p=p, depth=depth, mode=mode, max_iter=max_iter,
                      coulomb_k=coulomb_k, root_box=root_box)
         info = fmm.solve(tol)
-        st = fmm.static_field()
-        mu = fmm.dipoles()
-        uqq = 0.5 * coulomb_k * torch.sum(q.detach() * st["phi"])
-        upol = -0.5 * coulomb_k * torch.sum(mu * st["E"])
+        U = fmm.energy()["U"]
         ctx.fmm = fmm
         ctx.info = info
-        return (uqq + upol).to(torch.float64)
+        ctx.grads = None
+        return torch.tensor(U, dtype=torch.float64, device=pos.device)
 
     @staticmethod
     def backward(ctx, gU):
-        out = ctx.fmm.energy_forces(forces=True, dq=True, dalpha=True)
-        ctx.fmm.close()
-        ctx.fmm = None
-        return gU * (-out["F"]), gU * out["dUdq"], gU * out["dUdalpha"], None, None, None, None, None, None, None
+        if ctx.grads is None:
+            out = ctx.fmm.energy_forces(forces=True, dq=True, dalpha=True)
+            ctx.fmm.close()
+            ctx.fmm = None
+            ctx.grads = (-out["F"], out["dUdq"], out["dUdalpha"])
+        gx, gq, ga = ctx.grads
+        return gU * gx, gU * gq, gU * ga, None, None, None, None, None, None, None
 
 
 def polarizable_energy(pos, q, alpha, p=6, depth=4, mode="fp64", tol=1e-8, max_iter=200, coulomb_k=1.0,

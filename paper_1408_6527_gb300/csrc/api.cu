@@ -7,6 +7,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <new>
 #include <string>
 #include <vector>
@@ -26,6 +27,38 @@ using namespace polfmm;
 // launch bookkeeping and profiling
 // ---------------------------------------------------------------------------
 namespace polfmm {
+
+// allocation counter and the planted failure of fmm_testing_alloc_hook
+static std::atomic<int64_t> g_alloc_count{0};
+static std::atomic<int64_t> g_alloc_fail_at{-1};
+
+static bool alloc_should_fail() {
+    const int64_t k = g_alloc_count.fetch_add(1);
+    int64_t at = g_alloc_fail_at.load();
+    return at >= 0 && k == at && g_alloc_fail_at.compare_exchange_strong(at, -1);
+}
+
+cudaError_t dev_alloc(void** p, size_t bytes) {
+    *p = nullptr;
+    if (alloc_should_fail()) return cudaErrorMemoryAllocation;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        cudaGetLastError();
+    }
+    return e;
+}
+
+cudaError_t host_alloc(void** p, size_t bytes) {
+    *p = nullptr;
+    if (alloc_should_fail()) return cudaErrorMemoryAllocation;
+    cudaError_t e = cudaMallocHost(p, bytes);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        cudaGetLastError();
+    }
+    return e;
+}
 
 LaunchScope::LaunchScope(polfmm_ctx* ctx, int family) : c(ctx), fam(family), slot(-1) {
     c->launches++;
@@ -122,7 +155,7 @@ int upload(const std::vector<T>& h, T** d, cudaStream_t st) {
         *d = nullptr;
         return POLFMM_OK;
     }
-    if (cudaMalloc(d, sizeof(T) * h.size()) != cudaSuccess) return POLFMM_ERR_OUT_OF_MEMORY;
+    if (dev_alloc(reinterpret_cast<void**>(d), sizeof(T) * h.size()) != cudaSuccess) return POLFMM_ERR_OUT_OF_MEMORY;
     if (cudaMemcpyAsync(*d, h.data(), sizeof(T) * h.size(), cudaMemcpyHostToDevice, st) != cudaSuccess)
         return POLFMM_ERR_CUDA;
     return cudaStreamSynchronize(st) == cudaSuccess ? POLFMM_OK : POLFMM_ERR_CUDA;
@@ -257,8 +290,7 @@ struct Alloc {
         if (!ok) return nullptr;
         void* p = nullptr;
         if (count == 0) count = 1;
-        if (cudaMalloc(&p, sizeof(T) * count) != cudaSuccess) {
-            cudaGetLastError();
+        if (dev_alloc(&p, sizeof(T) * count) != cudaSuccess) {
             ok = false;
             return nullptr;
         }
@@ -336,9 +368,10 @@ int allocate(polfmm_ctx* c) {
     c->leaf_items = A.get<int2>(c->leaf_items_cap);
     c->leaf_nitems = A.get<int>(4);
     if (!A.ok) return POLFMM_ERR_OUT_OF_MEMORY;
-    if (cudaMallocHost(&c->h_scal, sizeof(double) * (S_COUNT + 8)) != cudaSuccess) return POLFMM_ERR_OUT_OF_MEMORY;
-    if (cudaMallocHost(&c->h_counts, sizeof(int) * (kMaxDepth + 1) * 9) != cudaSuccess) return POLFMM_ERR_OUT_OF_MEMORY;
-    if (cudaMallocHost(&c->h_bbox, sizeof(double) * 8) != cudaSuccess) return POLFMM_ERR_OUT_OF_MEMORY;
+    if (host_alloc(reinterpret_cast<void**>(&c->h_scal), sizeof(double) * (S_COUNT + 8)) != cudaSuccess ||
+        host_alloc(reinterpret_cast<void**>(&c->h_counts), sizeof(int) * (kMaxDepth + 1) * 9) != cudaSuccess ||
+        host_alloc(reinterpret_cast<void**>(&c->h_bbox), sizeof(double) * 8) != cudaSuccess)
+        return POLFMM_ERR_OUT_OF_MEMORY;
     cudaMemsetAsync(c->err, 0, sizeof(int) * 4, c->stream);
     cudaMemsetAsync(c->ticket, 0, sizeof(int) * 4, c->stream);
     cudaMemsetAsync(c->scal, 0, sizeof(double) * (S_COUNT + 8), c->stream);
@@ -356,10 +389,7 @@ int ensure_lp(polfmm_ctx* c) {
     for (int l = 0; l <= c->depth; l++) {
         void* p = nullptr;
         size_t bytes = (size_t)c->m2l_chunks * c->lv[l].cap * c->ld * rsz;
-        if (cudaMalloc(&p, std::max<size_t>(bytes, 16)) != cudaSuccess) {
-            cudaGetLastError();
-            return POLFMM_ERR_OUT_OF_MEMORY;
-        }
+        if (dev_alloc(&p, std::max<size_t>(bytes, 16)) != cudaSuccess) return POLFMM_ERR_OUT_OF_MEMORY;
         X->lp_bufs.push_back(p);
         c->lv[l].Lp = p;
     }
@@ -742,38 +772,35 @@ int fmm_solve_induced_dipoles(polfmm_ctx* c, double tol, int* iters_out, double*
         if ((rc = fetch()) != POLFMM_OK) return rc;
         it = (int)c->h_scal[S_ITER];
         c->launches += c->loop_launches * it;
-        if (!(c->h_scal[S_DAD] > 0.0)) {  // operator not positive definite (polarization catastrophe)
-            res = sqrt(fabs(c->h_scal[S_RR] / bb));
+        // a direction of non-positive curvature (polarization catastrophe) was not
+        // applied: the dipoles and residual are those of the last good iterate
+        res = sqrt(fabs(c->h_scal[S_RR] / bb));
+        if (!(c->h_scal[S_DAD] > 0.0) || !isfinite(res) || c->h_scal[S_GROW] >= kStagnationIters)
             status = POLFMM_ERR_NOT_CONVERGED;
-        } else {
-            res = sqrt(c->h_scal[S_RR] / bb);
-            if (!isfinite(res)) status = POLFMM_ERR_NOT_CONVERGED;
-        }
     } else if (!jacobi) {
         res = sqrt(c->h_scal[S_RR] / bb);
         while (res > tol && it < c->opt.max_iter) {
             if ((rc = pcg_iteration(c)) != POLFMM_OK) return rc;
             it++;
             if ((rc = fetch()) != POLFMM_OK) return rc;
-            if (!(c->h_scal[S_DAD] > 0.0)) {  // operator not positive definite (polarization catastrophe)
-                res = sqrt(fabs(c->h_scal[S_RR] / bb));
-                status = POLFMM_ERR_NOT_CONVERGED;
-                break;
-            }
-            res = sqrt(c->h_scal[S_RR] / bb);
-            if (!isfinite(res)) {
+            res = sqrt(fabs(c->h_scal[S_RR] / bb));
+            if (!(c->h_scal[S_DAD] > 0.0) || !isfinite(res) || c->h_scal[S_GROW] >= kStagnationIters) {
                 status = POLFMM_ERR_NOT_CONVERGED;
                 break;
             }
         }
     } else {
         res = INFINITY;
+        int grow = 0;
         while (it < c->opt.max_iter) {
             solver_jacobi_step(c);
             it++;
             if ((rc = fetch()) != POLFMM_OK) return rc;
-            res = sqrt(c->h_scal[S_RR] / bb);
-            if (!isfinite(res)) {
+            const double r_new = sqrt(c->h_scal[S_RR] / bb);
+            grow = it > 1 && r_new > res ? grow + 1 : 0;
+            res = r_new;
+            // a fixed point whose residual keeps growing diverges (spectral radius of alpha T >= 1)
+            if (!isfinite(res) || grow >= kStagnationIters) {
                 status = POLFMM_ERR_NOT_CONVERGED;
                 break;
             }
@@ -818,6 +845,22 @@ int fmm_energy_forces(polfmm_ctx* c, double* energy_out, double* forces, double*
         energy_out[1] = uqq;
         energy_out[2] = upol;
     }
+    return POLFMM_OK;
+}
+
+int fmm_energy(polfmm_ctx* c, double* energy_out) {
+    if (!c || !energy_out) return POLFMM_ERR_INVALID_ARG;
+    if (!c->have_mu) return POLFMM_ERR_STATE;
+    energy_stationary(c);
+    cudaMemcpyAsync(c->h_scal, c->scal, sizeof(double) * S_COUNT, cudaMemcpyDeviceToHost, c->stream);
+    int rc = read_err(c);
+    if (rc != POLFMM_OK) return rc;
+    const double k = c->opt.coulomb_k;
+    const double uqq = k * c->h_scal[S_UQQ];
+    const double upol = -0.5 * k * c->h_scal[S_MUEQ];
+    energy_out[0] = uqq + upol;
+    energy_out[1] = uqq;
+    energy_out[2] = upol;
     return POLFMM_OK;
 }
 
@@ -949,6 +992,12 @@ int fmm_profile_reset(polfmm_ctx* c) {
 }
 
 int64_t fmm_launch_count(polfmm_ctx* c) { return c ? c->launches : 0; }
+
+int64_t fmm_testing_alloc_hook(int64_t fail_at) {
+    const int64_t made = g_alloc_count.exchange(0);
+    g_alloc_fail_at.store(fail_at >= 0 ? fail_at : -1);
+    return made;
+}
 
 void fmm_destroy(polfmm_ctx* c) { destroy_impl(c); }
 

@@ -1048,7 +1048,8 @@ int m2l_setup(polfmm_ctx* c) {
         if (c->tiles) cudaFree(c->tiles);
         c->tiles = nullptr;
         c->ntiles_cap = std::max(c->ntiles, 64);
-        if (cudaMalloc(&c->tiles, sizeof(M2LTile) * c->ntiles_cap) != cudaSuccess) return POLFMM_ERR_OUT_OF_MEMORY;
+        if (dev_alloc(reinterpret_cast<void**>(&c->tiles), sizeof(M2LTile) * c->ntiles_cap) != cudaSuccess)
+            return POLFMM_ERR_OUT_OF_MEMORY;
     }
     if (c->ntiles)
         if (cudaMemcpyAsync(c->tiles, t.data(), sizeof(M2LTile) * c->ntiles, cudaMemcpyHostToDevice, c->stream) !=

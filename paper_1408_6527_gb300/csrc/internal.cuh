@@ -207,6 +207,11 @@ struct polfmm_ctx {
 
 namespace polfmm {
 
+// every device or pinned-host allocation of the library goes through these two,
+// so that fmm_testing_alloc_hook can make the k-th one fail
+cudaError_t dev_alloc(void** p, size_t bytes);
+cudaError_t host_alloc(void** p, size_t bytes);
+
 // launch bookkeeping / profiling around one kernel launch
 struct LaunchScope {
     polfmm_ctx* c;
@@ -244,11 +249,16 @@ void solver_loop_setup(polfmm_ctx* c, double tol, int max_iter);
 void solver_jacobi_step(polfmm_ctx* c);
 void energy_and_gradients(polfmm_ctx* c, double* forces_caller, double* dq_caller,
                           double* dalpha_caller, bool want_f, bool want_dq, bool want_da);
+void energy_stationary(polfmm_ctx* c);
+// residual growths in a row after which a solve stops as not converged
+constexpr int kStagnationIters = 3;
 void mask_dipoles(polfmm_ctx* c, double* v);
 
 // device scalar slots
 enum Scal {
-    S_RZ = 0, S_RZ_NEW, S_DAD, S_RR, S_BB, S_UQQ, S_MUEQ, S_MUEMU, S_AMU, S_BETA, S_TOL, S_MAXIT, S_ITER, S_COUNT
+    S_RZ = 0, S_RZ_NEW, S_DAD, S_RR, S_BB, S_UQQ, S_MUEQ, S_MUEMU, S_AMU, S_BETA, S_TOL, S_MAXIT, S_ITER,
+    S_GROW,  // consecutive iterations whose residual grew (stagnation / divergence test)
+    S_COUNT
 };
 constexpr int kRedBlocks = 256;
 constexpr int kRedSlots = 8;

@@ -908,18 +908,14 @@ int m2l_tensor_prepare(polfmm_ctx* c) {
                     }
             }
         }
-        if (cudaMalloc(&S->Bimg, sizeof(float) * img.size()) != cudaSuccess) {
-            cudaGetLastError();
+        if (dev_alloc(reinterpret_cast<void**>(&S->Bimg), sizeof(float) * img.size()) != cudaSuccess)
             return POLFMM_ERR_OUT_OF_MEMORY;
-        }
         if (cudaMemcpy(S->Bimg, img.data(), sizeof(float) * img.size(), cudaMemcpyHostToDevice) != cudaSuccess)
             return POLFMM_ERR_CUDA;
         size_t rows_cap = 0;
         for (int l = 2; l <= c->depth; l++) rows_cap += c->lv[l].cap;
-        if (cudaMalloc(&S->rows, sizeof(int2) * std::max<size_t>(rows_cap, 1)) != cudaSuccess) {
-            cudaGetLastError();
+        if (dev_alloc(reinterpret_cast<void**>(&S->rows), sizeof(int2) * std::max<size_t>(rows_cap, 1)) != cudaSuccess)
             return POLFMM_ERR_OUT_OF_MEMORY;
-        }
         cudaError_t e1 = S->tmem_a ? cudaFuncSetAttribute(m2l_tca_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                           (int)S->smem)
                                    : cudaFuncSetAttribute(m2l_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -963,10 +959,8 @@ int m2l_tensor_prepare(polfmm_ctx* c) {
         if (S->tiles) cudaFree(S->tiles);
         S->tiles = nullptr;
         S->tiles_cap = std::max(S->ntiles, 16);
-        if (cudaMalloc(&S->tiles, sizeof(TcTile) * S->tiles_cap) != cudaSuccess) {
-            cudaGetLastError();
+        if (dev_alloc(reinterpret_cast<void**>(&S->tiles), sizeof(TcTile) * S->tiles_cap) != cudaSuccess)
             return POLFMM_ERR_OUT_OF_MEMORY;
-        }
     }
     if (S->ntiles &&
         cudaMemcpyAsync(S->tiles, tl.data(), sizeof(TcTile) * S->ntiles, cudaMemcpyHostToDevice, c->stream) !=

@@ -60,7 +60,8 @@ __device__ inline void store_packed(void* base, int64_t i, double x, double y, d
 
 // single-block final reduction of nslot partial rows
 // post: 0 = store sums into scal[dst[k]]; 1 = PCG direction update
-// (scal[S_BETA] = sum0 / scal[S_RZ], scal[S_RZ] = sum0, scal[S_RR] = sum1)
+// (scal[S_BETA] = sum0 / scal[S_RZ], scal[S_RZ] = sum0, scal[S_RR] = sum1);
+// 2 = store, and restart the residual-growth count of a new solve
 __global__ void reduce_final_kernel(const double* __restrict__ partial, int nslot, int s0, int s1, int s2, int s3,
                                     double* __restrict__ scal, int post) {
     __shared__ double sh[kRedThreads];
@@ -79,6 +80,7 @@ __global__ void reduce_final_kernel(const double* __restrict__ partial, int nslo
             scal[S_RR] = res[1];
         } else {
             for (int k = 0; k < nslot; k++) scal[dst[k]] = res[k];
+            if (post == 2) scal[S_GROW] = 0.0;
         }
     }
 }
@@ -161,24 +163,32 @@ __global__ void pcg_ad_kernel(int64_t n, const double* __restrict__ alpha, const
 }
 
 // step = rz / dAd; mu += step d; r -= step Ad; z = alpha r; r.z and r.r; the
-// last block stores beta = (r.z)_new / (r.z)_old, (r.z)_new and r.r.  Inside
-// the solve graph (cond != 0) it counts the iteration and keeps the loop going
-// while d.Ad > 0, the relative residual is finite and above tol, and fewer than
-// max_iter iterations are done.
+// last block stores beta = (r.z)_new / (r.z)_old, (r.z)_new and r.r, and counts
+// the iterations in a row whose residual grew.  A direction with d.Ad <= 0 (the
+// operator is not positive definite: polarization catastrophe) or a non-finite
+// d.Ad is not applied, so mu, r and z keep the last good iterate.  Inside the
+// solve graph (cond != 0) it counts the iteration and keeps the loop going while
+// d.Ad > 0, the relative residual is finite and above tol, the residual has not
+// grown kStagnationIters times in a row, and fewer than max_iter iterations are done.
 __global__ void pcg_update_kernel(int64_t n, const double* __restrict__ alpha, double* __restrict__ scal,
                                   const double* __restrict__ d, const double* __restrict__ Ad, double* __restrict__ mu,
                                   double* __restrict__ r, double* __restrict__ z, double* __restrict__ partial,
                                   int* __restrict__ ticket, cudaGraphConditionalHandle cond) {
     __shared__ double sh[kRedThreads];
-    const double step = scal[S_RZ] / scal[S_DAD];
+    const double dad = scal[S_DAD];
+    const bool ok = dad > 0.0 && isfinite(dad);
+    const double step = ok ? scal[S_RZ] / dad : 0.0;
     double rz = 0, rr = 0;
     RED_LOOP(i, 3 * n) {
         double a = alpha[i / 3];
         if (a > 0.0) {
-            mu[i] += step * d[i];
-            double ri = r[i] - step * Ad[i];
+            double ri = r[i];
+            if (ok) {
+                mu[i] += step * d[i];
+                ri -= step * Ad[i];
+                r[i] = ri;
+            }
             double zi = a * ri;
-            r[i] = ri;
             z[i] = zi;
             rz += ri * zi;
             rr += ri * ri;
@@ -194,6 +204,8 @@ __global__ void pcg_update_kernel(int64_t n, const double* __restrict__ alpha, d
         double rz_new = sum_partials(partial, 0, sh);
         double rr_all = sum_partials(partial, 1, sh);
         if (threadIdx.x == 0) {
+            const double grow = rr_all > scal[S_RR] ? scal[S_GROW] + 1.0 : 0.0;
+            scal[S_GROW] = grow;
             scal[S_BETA] = rz_new / scal[S_RZ];
             scal[S_RZ] = rz_new;
             scal[S_RR] = rr_all;
@@ -202,7 +214,8 @@ __global__ void pcg_update_kernel(int64_t n, const double* __restrict__ alpha, d
                 const double it = scal[S_ITER] + 1.0;
                 scal[S_ITER] = it;
                 const double res = sqrt(rr_all / scal[S_BB]);
-                const bool go = scal[S_DAD] > 0.0 && isfinite(res) && res > scal[S_TOL] && it < scal[S_MAXIT];
+                const bool go = ok && isfinite(res) && res > scal[S_TOL] && it < scal[S_MAXIT] &&
+                                grow < (double)kStagnationIters;
                 cudaGraphSetConditional(cond, go ? 1u : 0u);
             }
         }
@@ -333,6 +346,25 @@ __global__ void assemble_kernel(int64_t n, const int* __restrict__ perm, const d
     }
 }
 
+// stationary energy terms (Sec. II.A): partials of 1/2 q Phi^q and mu.E^q; at a
+// converged solve U^pol = -1/2 sum mu.E^q (Eq. upol_derivatives)
+__global__ void energy_stationary_kernel(int64_t n, const double* __restrict__ q, const double* __restrict__ mu,
+                                         const double* __restrict__ phiq, const double* __restrict__ Eq,
+                                         double* __restrict__ partial) {
+    __shared__ double sh[kRedThreads];
+    double uqq = 0, mueq = 0;
+    RED_LOOP(i, n) {
+        uqq += 0.5 * q[i] * phiq[i];
+        mueq += mu[3 * i] * Eq[3 * i] + mu[3 * i + 1] * Eq[3 * i + 1] + mu[3 * i + 2] * Eq[3 * i + 2];
+    }
+    uqq = block_sum(uqq, sh);
+    mueq = block_sum(mueq, sh);
+    if (threadIdx.x == 0) {
+        partial[0 * kRedBlocks + blockIdx.x] = uqq;
+        partial[1 * kRedBlocks + blockIdx.x] = mueq;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
@@ -376,7 +408,7 @@ void solver_init(polfmm_ctx* c, bool warm) {
         pcg_init_kernel<<<kRedBlocks, kRedThreads, 0, c->stream>>>(c->n, c->alpha_s, c->Eq, c->mu, c->Td, c->r,
                                                                     c->z, c->d, c->partial);
     }
-    reduce(c, 3, S_RZ, S_RR, S_BB, 0, 0, F_SOLVER);
+    reduce(c, 3, S_RZ, S_RR, S_BB, 0, 2, F_SOLVER);
     LaunchScope ls(c, F_SOLVER);
     if (c->mixed)
         pack_vec_kernel<float><<<grid_for(c->n, 256), 256, 0, c->stream>>>(c->n, c->d, c->srcB);
@@ -433,6 +465,15 @@ void energy_and_gradients(polfmm_ctx* c, double* F, double* dq, double* da, bool
             want_f ? F : nullptr, want_dq ? dq : nullptr, want_da ? da : nullptr, c->partial);
     }
     reduce(c, 4, S_UQQ, S_MUEQ, S_MUEMU, S_AMU, 0, F_ASSEMBLE);
+}
+
+void energy_stationary(polfmm_ctx* c) {
+    {
+        LaunchScope ls(c, F_ASSEMBLE);
+        energy_stationary_kernel<<<kRedBlocks, kRedThreads, 0, c->stream>>>(c->n, c->q_s, c->mu, c->phiq, c->Eq,
+                                                                              c->partial);
+    }
+    reduce(c, 2, S_UQQ, S_MUEQ, 0, 0, 0, F_ASSEMBLE);
 }
 
 }  // namespace polfmm

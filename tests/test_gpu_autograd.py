@@ -80,3 +80,17 @@ def test_autograd_gradients_match_finite_differences():
         if checked == 6:
             break
     assert checked == 6
+
+
+def test_second_backward_reuses_the_gradients():
+    """retain_graph=True: a second backward gives the same gradients (the force
+    pass runs once; its results are kept)."""
+    pos, q, alpha, root = _setup(n=200, seed=62)
+    x = torch.tensor(pos, device="cuda", requires_grad=True)
+    U = polarizable_energy(x, torch.tensor(q, device="cuda"), torch.tensor(alpha, device="cuda"), p=4, depth=3,
+                           tol=1e-12, root_box=root)
+    U.backward(retain_graph=True)
+    g1 = x.grad.clone()
+    x.grad = None
+    (2.0 * U).backward()
+    torch.testing.assert_close(x.grad, 2.0 * g1, rtol=0, atol=0)

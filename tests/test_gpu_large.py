@@ -15,6 +15,7 @@ if not torch.cuda.is_available():  # pragma: no cover
     pytest.skip("no CUDA device", allow_module_level=True)
 
 from paper_1408_6527_gb300 import PolFMM  # noqa: E402
+from siteerr import max_site_err  # noqa: E402
 
 
 def dev(a):
@@ -34,6 +35,8 @@ def test_large_static_field_fp64_matches_oracle(index, n, depth):
     ref = oracle.fmm_fields(w.pos, w.q, None, p=w.p, depth=w.depth, root=(lo, side))
     assert oracle.rel_rms(host(st["E"]), ref["E"]) < 1e-10
     assert oracle.rel_rms(host(st["phi"]), ref["phi"]) < 1e-10
+    assert max_site_err(host(st["E"]), ref["E"]) < 1e-8
+    assert max_site_err(host(st["phi"]), ref["phi"]) < 1e-8
 
 
 @pytest.mark.parametrize("index,n", [(2, None), (3, None), (5, 250000)])
@@ -51,6 +54,7 @@ def test_large_mixed_forces_within_gate(index, n):
             assert info["converged"], (mode, info)
             F[mode] = host(f.energy_forces()["F"])
     assert oracle.rel_rms(F["mixed"], F["fp64"]) < 1e-5
+    assert max_site_err(F["mixed"], F["fp64"]) < 1e-3
 
 
 def test_globule_fp64_solve_matches_oracle_at_bench_size():
@@ -68,3 +72,5 @@ def test_globule_fp64_solve_matches_oracle_at_bench_size():
     assert oracle.rel_rms(mu, ref["mu"]) < 1e-9
     assert out["U"] == pytest.approx(ref["U"], rel=1e-10)
     assert oracle.rel_rms(host(out["F"]), ref["F"]) < 1e-9
+    assert max_site_err(mu, ref["mu"]) < 1e-7
+    assert max_site_err(host(out["F"]), ref["F"]) < 1e-7

@@ -1,10 +1,12 @@
 """GPU path against the CPU oracle, through the C ABI.
 
 FP64 mode must reproduce the oracle's FMM at the same order and tree to
-round-off (1e-10 relative RMS; the arithmetic is the same truncated expansion,
-only evaluated in a different order and normalisation).  MIXED mode must stay
-within 1e-5 relative RMS force error of FP64.  Integer work (leaf cells, root
-cube) must match bit for bit.
+round-off: 1e-10 relative RMS over all sites and 1e-8 at the worst single site
+(per-site error with a floor of 1 % of the typical magnitude, so that one
+wrong leaf or tile row cannot hide in the norm; the arithmetic is the same
+truncated expansion, only evaluated in a different order and normalisation).
+MIXED mode must stay within 1e-5 relative RMS force error of FP64.  Integer
+work (leaf cells, root cube) must match bit for bit.
 """
 import numpy as np
 import pytest
@@ -19,9 +21,13 @@ if not torch.cuda.is_available():  # pragma: no cover
     pytest.skip("no CUDA device", allow_module_level=True)
 
 from paper_1408_6527_gb300 import PolFMM, PolFMMError  # noqa: E402
+from siteerr import max_site_err  # noqa: E402
 
 FP64_TOL = 1e-10
+FP64_SITE_TOL = 1e-8
 MIXED_FORCE_TOL = 1e-5
+MIXED_SITE_TOL = 1e-3
+MIXED_ENERGY_TOL = 1e-6
 
 
 def dev(a):
@@ -83,6 +89,8 @@ def test_static_field_fp64(w1, p, depth):
     st, ref = _static_case(w1.pos, w1.q, w1.alpha, p, depth)
     assert oracle.rel_rms(host(st["E"]), ref["E"]) < FP64_TOL
     assert oracle.rel_rms(host(st["phi"]), ref["phi"]) < FP64_TOL
+    assert max_site_err(host(st["E"]), ref["E"]) < FP64_SITE_TOL
+    assert max_site_err(host(st["phi"]), ref["phi"]) < FP64_SITE_TOL
 
 
 def test_static_field_fp64_ragged_small():
@@ -90,12 +98,16 @@ def test_static_field_fp64_ragged_small():
     pos, q, alpha = synth.small_random(31, 37, box=10.0)
     st, ref = _static_case(pos, q, alpha, 5, 4)
     assert oracle.rel_rms(host(st["E"]), ref["E"]) < FP64_TOL
+    assert max_site_err(host(st["E"]), ref["E"]) < FP64_SITE_TOL
+    assert max_site_err(host(st["phi"]), ref["phi"]) < FP64_SITE_TOL
 
 
 def test_static_field_fp64_globule_full_size(w2):
     st, ref = _static_case(w2.pos, w2.q, w2.alpha, w2.p, w2.depth)
     assert oracle.rel_rms(host(st["E"]), ref["E"]) < FP64_TOL
     assert oracle.rel_rms(host(st["phi"]), ref["phi"]) < FP64_TOL
+    assert max_site_err(host(st["E"]), ref["E"]) < FP64_SITE_TOL
+    assert max_site_err(host(st["phi"]), ref["phi"]) < FP64_SITE_TOL
 
 
 @pytest.mark.parametrize("p,depth", [(4, 3), (6, 4)])
@@ -107,6 +119,7 @@ def test_dipole_field_fp64(w1, p, depth):
         lo, side = f.root_box()
     ref = oracle.fmm_fields(w1.pos, None, mu, p=p, depth=depth, root=(lo, side))
     assert oracle.rel_rms(E, ref["E"]) < FP64_TOL
+    assert max_site_err(E, ref["E"]) < FP64_SITE_TOL
 
 
 def test_total_field_fp64(w1):
@@ -118,6 +131,7 @@ def test_total_field_fp64(w1):
     ref = oracle.fmm_fields(w1.pos, w1.q, mu, p=5, depth=3, root=(lo, side))
     for k in ("phi", "E", "G"):
         assert oracle.rel_rms(host(out[k]), ref[k]) < FP64_TOL, k
+        assert max_site_err(host(out[k]), ref[k]) < FP64_SITE_TOL, k
 
 
 def test_host_buffers_match_device_buffers(w1):
@@ -148,12 +162,14 @@ def test_fixed_iteration_pcg_fp64(w1, iters):
                                                  tol=0.0, max_iter=iters)
     assert it == iters
     assert oracle.rel_rms(mu, ref_mu) < 1e-9
+    assert max_site_err(mu, ref_mu) < 1e-7
     assert info["residual"] == pytest.approx(res, rel=1e-6)
 
 
 def test_converged_energy_forces_fp64(w1):
     with PolFMM(dev(w1.pos), dev(w1.q), dev(w1.alpha), p=4, depth=3) as f:
         info = f.solve(1e-12)
+        f_energy = f.energy()
         out = f.energy_forces()
         mu = host(f.dipoles())
         lo, side = f.root_box()
@@ -161,12 +177,16 @@ def test_converged_energy_forces_fp64(w1):
     ref = oracle.polarizable_energy(w1.pos, w1.q, w1.alpha, method="fmm", p=4, depth=3, root=(lo, side),
                                     tol=1e-13)
     assert oracle.rel_rms(mu, ref["mu"]) < 1e-9
+    assert f_energy["U"] == pytest.approx(ref["U"], rel=1e-10)
     assert out["U"] == pytest.approx(ref["U"], rel=1e-10)
     assert out["Uqq"] == pytest.approx(ref["Uqq"], rel=1e-10)
     assert out["Upol"] == pytest.approx(ref["Upol"], rel=1e-9)
     assert oracle.rel_rms(host(out["F"]), ref["F"]) < 1e-9
     assert oracle.rel_rms(host(out["dUdq"]), ref["dUdq"]) < 1e-9
     assert oracle.rel_rms(host(out["dUdalpha"]), ref["dUdalpha"]) < 1e-9
+    for k in ("F", "dUdq", "dUdalpha"):
+        assert max_site_err(host(out[k]), ref[k]) < 1e-7, k
+    assert max_site_err(mu, ref["mu"]) < 1e-7
 
 
 def test_against_direct_sum_and_dense_solve(w1):
@@ -198,8 +218,12 @@ def test_mixed_vs_fp64_force_error(w2):
     F64, Fmx = host(outs["fp64"][0]["F"]), host(outs["mixed"][0]["F"])
     assert oracle.rel_rms(Fmx, F64) < MIXED_FORCE_TOL
     assert oracle.rel_rms(outs["mixed"][1], outs["fp64"][1]) < 1e-5
-    # FP32 arithmetic summed over ~1e4 terms per site: a few 1e-6 relative
-    assert outs["mixed"][0]["U"] == pytest.approx(outs["fp64"][0]["U"], rel=5e-6)
+    assert max_site_err(Fmx, F64) < MIXED_SITE_TOL
+    assert max_site_err(outs["mixed"][1], outs["fp64"][1]) < MIXED_SITE_TOL
+    # U = U^qq' + U^pol: a sum of ~1e4 terms of both signs per site in FP32 whose
+    # total is about 1e-2 of the sum of magnitudes; the MIXED solve tolerance
+    # (1e-7 here) adds an error of the same order to U^pol
+    assert outs["mixed"][0]["U"] == pytest.approx(outs["fp64"][0]["U"], rel=MIXED_ENERGY_TOL)
 
 
 def test_deterministic_repeat(w1):
@@ -268,6 +292,8 @@ def test_alpha_zero_sites_carry_no_dipole(w1):
     ref = oracle.polarizable_energy(w1.pos, w1.q, alpha, method="fmm", p=4, depth=3, root=(lo, side), tol=1e-13)
     assert oracle.rel_rms(host(out["F"]), ref["F"]) < 1e-9
     assert oracle.rel_rms(host(out["dUdalpha"]), ref["dUdalpha"]) < 1e-9
+    assert max_site_err(host(out["F"]), ref["F"]) < 1e-7
+    assert max_site_err(host(out["dUdalpha"]), ref["dUdalpha"]) < 1e-7
 
 
 # ---------------------------------------------------------------------------
@@ -296,6 +322,8 @@ def test_tensor_core_m2l_matches_simt(case, w1, w2):
     assert oracle.rel_rms(out["tensor"][0], ref) < 5e-6
     assert oracle.rel_rms(out["tensor"][0], out["simt"][0]) < 5e-6
     assert oracle.rel_rms(out["tensor"][1], out["simt"][1]) < 5e-6
+    assert max_site_err(out["tensor"][0], ref) < 1e-4
+    assert max_site_err(out["tensor"][1], out["simt"][1]) < 1e-4
 
 
 def test_tensor_core_m2l_forces_within_gate(w2):
@@ -305,6 +333,7 @@ def test_tensor_core_m2l_forces_within_gate(w2):
             f.solve(1e-8 if mode == "fp64" else 1e-7)
             outs[mode] = host(f.energy_forces()["F"])
     assert oracle.rel_rms(outs["mixed"], outs["fp64"]) < MIXED_FORCE_TOL
+    assert max_site_err(outs["mixed"], outs["fp64"]) < MIXED_SITE_TOL
 
 
 def test_graph_replay_matches_direct_launches(w1):
