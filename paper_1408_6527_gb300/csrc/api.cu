@@ -346,6 +346,14 @@ int allocate(polfmm_ctx* c) {
     c->scan_tmp_cap = tree_scan_scratch(n);
     c->scan_tmp = A.get<int>(c->scan_tmp_cap);
     c->tree_cnt = A.get<int>((kMaxDepth + 1) * 9);
+    // the multipoles of all levels in one array (level l from row mrow0[l]), so
+    // that a row of any level is addressed by one index
+    int64_t mrows = 0;
+    for (int l = 0; l <= c->depth; l++) {
+        c->mrow0[l] = mrows;
+        mrows += std::min<int64_t>((int64_t)1 << (3 * l), n);
+    }
+    c->Mall = A.get<unsigned char>((size_t)mrows * c->ld * rsz);
     for (int l = 0; l <= c->depth; l++) {
         Level& B = c->lv[l];
         int64_t full = (int64_t)1 << (3 * l);
@@ -356,7 +364,7 @@ int allocate(polfmm_ctx* c) {
         B.child0 = A.get<int>(B.cap);
         B.nchild = A.get<int>(B.cap);
         B.by_class = A.get<int>(B.cap);
-        B.M = A.get<unsigned char>((size_t)B.cap * c->ld * rsz);
+        B.M = c->Mall ? static_cast<unsigned char*>(c->Mall) + (size_t)c->mrow0[l] * c->ld * rsz : nullptr;
         B.arrive = A.get<int>(B.cap);
         if (l >= 3) B.Msh = A.get<unsigned char>((size_t)B.cap * c->ld * rsz);
     }

@@ -140,6 +140,8 @@ struct polfmm_ctx {
     int leaf_items_cap = 0;       // capacity of leaf_items
     int leaf_items_grid = 0;      // launch bound of the current tree: leaves + n / leaf_targets + 1
     polfmm::Level lv[polfmm::kMaxDepth + 1];
+    void* Mall = nullptr;                      // multipoles of all levels; level l from row mrow0[l]
+    int64_t mrow0[polfmm::kMaxDepth + 1] = {0};
     polfmm::Tables tab;
     // M2L work list
     polfmm::M2LTile* tiles = nullptr;
