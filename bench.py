@@ -48,12 +48,16 @@ def tol_for(mode, n):
     if mode == "fp64":
         return TOL["fp64"]
     return TOL["mixed"] if n <= 100_000 else 3e-7
-FP32_LANES_PER_SM = 128
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
-# current kernels from one ncu capture (profiles/); None where not captured
-TRAFFIC = {("m2l", "mixed"): 7097344, ("leaf_dipole", "mixed"): None}
-NUM_SMS = 152
-SM_MAX_MHZ = 2070.0
+# current kernels, from one ncu capture of the workload named in the key (the
+# command and the figures are in profiles/); the line reports null for any
+# other kernel, workload or mode
+TRAFFIC = {
+    ("m2l", "globule", 30000, "mixed"): 5143000,          # profiles/launches_globule30k_mixed.md
+    ("leaf_dipole", "globule", 30000, "mixed"): 1052000,
+    ("p2m", "globule", 30000, "mixed"): 1150000,
+    ("l2p", "globule", 30000, "mixed"): 7226000,
+}
 
 
 def parse():
@@ -88,19 +92,33 @@ def m2l_flops_per_box_pair(p):
     return 2 * sum((s + 1) * (s + 2) // 2 * ncoef(p - s) for s in range(p + 1))
 
 
+def tc_inputs(p):
+    """Inputs that go through the tensor cores: all of them (rounded up to 8) for
+    p = 7, 8; at most the first 40 for p <= 6, whose higher-degree inputs feed so
+    few outputs that the M2L evaluates them with FP32 FMAs instead."""
+    kp = (ncoef(p) + 7) // 8 * 8
+    return kp if p > 6 else min(kp, 40)
+
+
 def tc_issued_macs_per_row(p):
     """MACs per tile row, offset and product issued by the tensor-core M2L: one
     MMA per input step of 8, whose N is the prefix of outputs that step feeds
     (|n| <= p - degree of the step's first input), rounded up to 16."""
-    nc = ncoef(p)
-    kp = (nc + 7) // 8 * 8
     deg = lambda i: next(s for s in range(p + 1) if i < ncoef(s))
     total = 0
-    for k in range(kp // 8):
+    for k in range(tc_inputs(p) // 8):
         dmax = p - deg(8 * k)
         nout = ncoef(dmax) if dmax >= 0 else 0
         total += max(16, (nout + 15) // 16 * 16) * 8
     return total
+
+
+def simt_fmas_per_row(p):
+    """FP32 FMAs per tile row and offset of the M2L's CUDA-core part: inputs from
+    tc_inputs(p) on, for every output they can feed (|n| + |m| <= p)."""
+    deg = lambda i: next(s for s in range(p + 1) if i < ncoef(s))
+    nc = ncoef(p)
+    return sum(1 for m in range(tc_inputs(p), nc) for nn in range(nc) if deg(nn) + deg(m) <= p)
 
 
 def load_peaks():
@@ -110,6 +128,71 @@ def load_peaks():
             "measured"
     except (OSError, ValueError, KeyError):
         return 6800.0, 1900.0, 1700.0, "fallback"
+
+
+def m2m_flops_per_box(p):
+    """Upward shift of one box (three one-axis convolutions, k <= n_d terms per
+    coefficient and axis, FMA = 2) plus the 2^-|n| scaling."""
+    total = 0
+    for s_ in range(p + 1):
+        for x in range(s_, -1, -1):
+            for y in range(s_ - x, -1, -1):
+                z = s_ - x - y
+                total += 2 * (x + y + z) + 1
+    return total
+
+
+def l2l_flops_per_level(p):
+    """Downward shift of one box per level: three one-axis passes, p - |n| terms
+    each (FMA = 2), plus the 2^-(|n|+1) scaling and the partial-sum add."""
+    total = 0
+    for s_ in range(p + 1):
+        total += (s_ + 1) * (s_ + 2) // 2 * (3 * 2 * (p - s_) + 2)
+    return total
+
+
+def radix_passes(depth):
+    return (3 * depth + 7) // 8
+
+
+def family_work(w, n, near_pairs, box_pairs, nbox, mixed, iterations):
+    """Algorithmic work of one launch of each kernel family (flops or bytes),
+    with the bound it is measured against.  Counted from the tree and the
+    operators, not from the kernels."""
+    p, d = w.p, w.depth
+    nc = ncoef(p)
+    rsz = 4 if mixed else 8
+    leaves = nbox[d]
+    inner = sum(nbox[l] for l in range(3, d + 1))  # boxes shifted to their parent
+    alu = "fp32" if mixed else "fp64"
+    out = {
+        # per solver pass: dipole field of the sources, 34 flops per ordered pair
+        "leaf_dipole": (near_pairs * 34, "alu", alu, "34 flops per ordered near pair (dipole -> field)"),
+        "m2l": (box_pairs * m2l_flops_per_box_pair(p), "tensor" if mixed else "alu", "tf32" if mixed else "fp64",
+                f"{m2l_flops_per_box_pair(p)} flops per box pair (sum over |n|+|m| <= p of 2)"),
+        # P2M of the dipoles (8 flops per site and coefficient) and M2M of every box below level 2
+        "p2m": (n * nc * 8 + inner * m2m_flops_per_box(p), "alu", alu,
+                "P2M 8 flops per site and coefficient + M2M per shifted box"),
+        # L2L of the leaf's ancestors from level 3 and L2P of the field (|n| <= p-1: 3 FMA + 2 mul)
+        "l2p": (n * ncoef(p - 1) * 10 + leaves * (d - 2) * l2l_flops_per_level(p), "alu", alu,
+                "L2P of E (10 flops per site and coefficient of order <= p-1) + L2L per leaf and level"),
+        # static pass: charge -> potential and field (20 flops per pair) + L2P of Phi, E
+        "leaf_static": (near_pairs * 20 + n * nc * 11 + leaves * (d - 2) * l2l_flops_per_level(p), "alu", alu,
+                        "20 flops per pair (charge -> Phi, E) + L2P + L2L"),
+        # force pass: charges and dipoles -> Phi, E, grad E (95 flops per pair) + L2P of 10 outputs
+        "leaf_full": (near_pairs * 95 + n * nc * 23 + leaves * (d - 2) * l2l_flops_per_level(p), "alu", alu,
+                      "95 flops per pair (charge + dipole -> Phi, E, grad E) + L2P + L2L"),
+        # tree: bounding box (24 B), keys (24 in, 8 out), radix passes (24 B each), the
+        # gather of positions, charges, polarizabilities and the packed copies (~120 B)
+        "tree": (n * (24 + 32 + 24 * radix_passes(d) + 120), "hbm", "hbm",
+                 f"{24 + 32 + 24 * radix_passes(d) + 120} B per site per tree build"),
+        # PCG vectors: update (reads alpha, d, Ad, mu, r; writes mu, r, z) and direction
+        # (reads z, d; writes d and its packed copy), float64
+        "solver": (n * (176 + 72 + 4 * rsz), "hbm", "hbm", f"{176 + 72 + 4 * rsz} B per site per PCG iteration"),
+        # energies and gradients: reads q, alpha, mu, Phi^q, E^q, Phi, E, grad E, perm; writes F, dU/dq, dU/dalpha
+        "assemble": (n * 196, "hbm", "hbm", "196 B per site (assembly reads and writes)"),
+    }
+    return out
 
 
 def tree_work(pos, depth, lo, side):
@@ -320,6 +403,8 @@ def run_gpu(args, rank, world, local_rank):
     total_ms, iters, launches, info, out, clocks = timed(ctx, args.mode, args.steps, args.warmup, True)
     total_ms = max_over_ranks(total_ms, dist, "cuda")
     F_main = out["F"].detach().cpu().numpy()
+    mu_main = ctx.dipoles().detach().cpu().numpy()
+    U_main = out["U"]
     lo, side = ctx.root_box()
     ctx.close()
     if rank != 0:
@@ -335,9 +420,14 @@ def run_gpu(args, rank, world, local_rank):
     ctx2 = make(other)
     t2, it2, _, info2, out2, _ = timed(ctx2, other, max(2, args.steps // 2), 1)
     F_other = out2["F"].detach().cpu().numpy()
+    mu_other = ctx2.dipoles().detach().cpu().numpy()
+    U_other = out2["U"]
     ctx2.close()
-    F64, Fmx = (F_other, F_main) if other == "fp64" else (F_main, F_other)
-    rms_err = float(np.sqrt(np.sum((Fmx - F64) ** 2) / np.sum(F64 ** 2)))
+    res = {args.mode: (U_main, F_main, mu_main), other: (U_other, F_other, mu_other)}
+    F64, Fmx = res["fp64"][1], res["mixed"][1]
+    rms_err = rel_rms(Fmx, F64)
+    errors_vs_fp64 = {"energy_rel": abs(res["mixed"][0] - res["fp64"][0]) / abs(res["fp64"][0]),
+                      "forces_rel_rms": rms_err, "dipoles_rel_rms": rel_rms(res["mixed"][2], res["fp64"][2])}
     n2 = max(2, args.steps // 2)
 
     # the paper's timing protocol: exactly 10 dipole iterations per step
@@ -347,52 +437,70 @@ def run_gpu(args, rank, world, local_rank):
     n10 = max(2, args.steps // 2)
 
     # per-kernel CUDA-event durations, recorded on the launching stream over
-    # separately profiled steps of the same workload
+    # separately profiled steps of the same workload (kernels one at a time, no
+    # graph and no near/far overlap: the shares are proportions, the sum exceeds
+    # the graph-launched step)
+    from paper_1408_6527_gb300 import measure_peak
     ctxp = make(args.mode, profile=True)
     for _ in range(2):
         step(ctxp, args.mode, pos_d)
     ctxp.profile_reset()
-    for _ in range(3):
+    nprof = 3
+    prof_iters = 0
+    for _ in range(nprof):
         flush.zero_()
-        step(ctxp, args.mode, pos_d)
+        info_p, _ = step(ctxp, args.mode, pos_d)
+        prof_iters += info_p["iterations"]
     fams = ["tree", "p2m", "m2m", "m2l", "l2l", "leaf_dipole", "l2p", "leaf_static", "leaf_full", "solver",
             "assemble"]
     prof = {f: ctxp.profile(f) for f in fams}
+    nbox = ctxp.tree_info()["boxes"]
     ctxp.close()
     prof_total = sum(v[0] for v in prof.values())
 
-    # roofline of the dominant kernel families: the near-field pass (FP32 ALU in
-    # MIXED, FP64 ALU in FP64) and the multipole-to-local pass (TF32 tensor
-    # cores in MIXED; FP64 ALU otherwise), each against its own peak
+    # roofline of every kernel family against its own measured peak
     near_pairs, box_pairs, tc_tiles = tree_work(w.pos, w.depth, lo, side)
     hbm_peak, bf16_burst, bf16_sust, peak_src = load_peaks()
     p = w.p
     mixed = args.mode == "mixed"
-    fp32_peak = NUM_SMS * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
-    tf32_peak = bf16_sust * 1.1 / 2.25
-    fams = {
-        "leaf_dipole": dict(flops=near_pairs * 34, bound="alu",
-                            peak=fp32_peak if mixed else 1.25,
-                            peak_note="FP32 FMA nominal: 152 SMs x 128 lanes x 2 x 2070 MHz" if mixed
-                            else "FP64 nominal 1.25 TFLOP/s"),
-        "m2l": dict(flops=box_pairs * m2l_flops_per_box_pair(p), bound="tensor" if mixed else "alu",
-                    peak=tf32_peak if mixed else 1.25,
-                    peak_note=(f"TF32 dense = {peak_src} sustained bf16 {bf16_sust} x nominal TF32/BF16 1.1/2.25")
-                    if mixed else "FP64 nominal 1.25 TFLOP/s"),
+    stream_ptr = torch.cuda.current_stream().cuda_stream
+    fp32_peak = measure_peak("fp32", stream_ptr)
+    fp64_peak = measure_peak("fp64", stream_ptr)
+    torch.cuda.synchronize()
+    props = torch.cuda.get_device_properties(torch.cuda.current_device())
+    peaks = {
+        "fp32": (fp32_peak, "TFLOP/s", f"measured FP32 FMA chains on all {props.multi_processor_count} SMs"),
+        "fp64": (fp64_peak, "TFLOP/s", f"measured FP64 FMA chains on all {props.multi_processor_count} SMs"),
+        # a kernel timed on its own: the burst cuBLAS figure, scaled to TF32 by the nominal ratio
+        "tf32": (bf16_burst * 1.1 / 2.25, "TFLOP/s",
+                 f"TF32 dense = {peak_src} burst bf16 {bf16_burst} x nominal TF32/BF16 1.1/2.25"),
+        "hbm": (hbm_peak, "GB/s", f"{peak_src} HBM copy"),
     }
+    work = family_work(w, n, near_pairs, box_pairs, nbox, mixed, prof_iters / nprof)
     roofs = {}
-    for fam, fi in fams.items():
-        if prof[fam][1] == 0:
+    for fam, (units, bound, pk, note) in work.items():
+        ms, nl = prof[fam]
+        if nl == 0:
             continue
-        dur_s = prof[fam][0] / prof[fam][1] / 1e3
-        achieved = fi["flops"] / dur_s / 1e12
-        r = {"kernel": fam, "bound": fi["bound"], "achieved": round(achieved, 3), "peak": round(fi["peak"], 2),
-             "unit": "TFLOP/s", "frac": round(achieved / fi["peak"], 5), "traffic": TRAFFIC.get((fam, args.mode)),
-             "peak_note": fi["peak_note"], "avg_launch_ms": round(prof[fam][0] / prof[fam][1], 4),
-             "algorithmic_flops_per_launch": int(fi["flops"]), "share_of_step": round(prof[fam][0] / prof_total, 4)}
+        dur_s = ms / nl / 1e3
+        if fam == "solver":  # one family launch per kernel: count the work per PCG iteration
+            dur_s = ms / max(prof_iters, 1) / 1e3
+        peak, unit, peak_note = peaks[pk]
+        scale = 1e12 if unit == "TFLOP/s" else 1e9
+        achieved = units / dur_s / scale
+        r = {"kernel": fam, "bound": bound, "achieved": round(achieved, 3), "peak": round(peak, 2), "unit": unit,
+             "frac": round(achieved / peak, 5),
+             "traffic": TRAFFIC.get((fam, w.name, n, args.mode)),
+             "peak_note": peak_note, "work_note": note,
+             "avg_launch_ms": round(ms / nl, 4), "launches_per_step": round(nl / nprof, 2),
+             ("algorithmic_bytes_per_unit" if bound == "hbm" else "algorithmic_flops_per_launch"): int(units),
+             "share_of_step": round(ms / prof_total, 4)}
         if fam == "m2l" and mixed:
+            # what the kernel issues: three TF32 products over the block-sparse MMA
+            # schedule on every tile row, present or not
             issued = 3 * 2 * 128 * tc_issued_macs_per_row(p) * tc_tiles * 189
             r["issued_tensor_tflops"] = round(issued / dur_s / 1e12, 3)
+            r["issued_tensor_frac"] = round(issued / dur_s / 1e12 / peaks["tf32"][0], 5)
         roofs[fam] = r
     dom = max(roofs, key=lambda f: prof[f][0]) if roofs else None
     roof = roofs.get(dom)
@@ -427,19 +535,37 @@ def run_gpu(args, rank, world, local_rank):
         "fixed_10_iterations": {"value": round(world * n * n10 / (t10 / 1e3), 1), "ms_per_step": round(t10 / n10, 4),
                                 "iterations": it10[-1]},
         "rms_force_err_mixed_vs_fp64": rms_err,
+        "errors_mixed_vs_fp64": {k: float(f"{v:.3e}") for k, v in errors_vs_fp64.items()},
         other: {"value": round(n * n2 / (t2 / 1e3), 1), "ms_per_step": round(t2 / n2, 4), "iterations": it2[-1]},
         "gpu_launches": int(launches),
-        "kernel_ms_per_step": {f: round(v[0] / 3, 4) for f, v in prof.items()},
+        "kernel_ms_per_step": {f: round(v[0] / nprof, 4) for f, v in prof.items()},
+        "kernel_ms_note": "CUDA events around each launch in separately profiled steps (kernels serialised, no "
+                          "graph, no near/far overlap): proportions, whose sum exceeds the graph-launched step",
         "kernel_share": {f: round(v[0] / prof_total, 4) for f, v in prof.items()} if prof_total > 0 else None,
         "roofline": roof, "roofline_kernels": roofs, "clocks": clocks, "e2e": e2e,
-        "tree": {"near_pairs": near_pairs, "m2l_box_pairs": box_pairs, "tc_tiles": tc_tiles},
+        "tree": {"near_pairs": near_pairs, "m2l_box_pairs": box_pairs, "tc_tiles": tc_tiles, "boxes": nbox},
+        "peaks": {k: {"value": round(v[0], 2), "unit": v[1], "source": v[2]} for k, v in peaks.items()},
     }
     if world == 1 and not args.no_cpu:
-        result["cpu_baseline"] = cpu_baseline(w, lo, side)
+        cb, ref = cpu_baseline(w, lo, side, return_result=True)
+        result["cpu_baseline"] = cb
+        # both GPU modes against the FP64 oracle on the same tree (same p, root box, depth)
+        result["errors_vs_oracle"] = {
+            mode: {"energy_rel": float(f"{abs(U - ref['U']) / abs(ref['U']):.3e}"),
+                   "forces_rel_rms": float(f"{rel_rms(F, ref['F']):.3e}"),
+                   "dipoles_rel_rms": float(f"{rel_rms(mu, ref['mu']):.3e}")}
+            for mode, (U, F, mu) in res.items()}
+        result["errors_vs_oracle"]["oracle"] = f"CPU FMM, FP64, PCG to {TOL['fp64']:g}, same tree"
     return result
 
 
-def cpu_baseline(w, lo, side, tol=None):
+def rel_rms(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.sqrt(np.sum((a - b) ** 2) / np.sum(b ** 2)))
+
+
+def cpu_baseline(w, lo, side, tol=None, return_result=False):
     """The CPU oracle as it stands on the host cores: one complete step on the
     full workload (FMM static pass, PCG with FMM matrix-vector products to the
     FP64 tolerance, force pass)."""
@@ -450,9 +576,10 @@ def cpu_baseline(w, lo, side, tol=None):
     out = oracle.polarizable_energy(w.pos, w.q, w.alpha, method="fmm", p=w.p, depth=w.depth, root=(lo, side),
                                     tol=tol, max_iter=500)
     dt = time.perf_counter() - t0
-    return {"value": round(w.n / dt, 1), "unit": "atoms/s", "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": f"one complete step of the full {w.n}-site workload (FP64 CPU FMM p={w.p} depth={w.depth}, "
-                      f"{out['iterations']} PCG iterations to {tol:g}, force pass): {dt:.2f} s"}
+    cb = {"value": round(w.n / dt, 1), "unit": "atoms/s", "cores": oracle.num_threads(), "kind": "oracle",
+          "sample": f"one complete step of the full {w.n}-site workload (FP64 CPU FMM p={w.p} depth={w.depth}, "
+                    f"{out['iterations']} PCG iterations to {tol:g}, force pass): {dt:.2f} s"}
+    return (cb, out) if return_result else cb
 
 
 def run_reference(args):

@@ -270,6 +270,16 @@ POLFMM_API int fmm_sort_sites_noalloc(int64_t n, const double* positions, int tr
                                       double* root_side, int32_t* cells, uint32_t* keys, int32_t* perm,
                                       void* cuda_stream);
 
+/*
+ * Measured peak rate of one arithmetic unit of the current device, for
+ * roofline fractions (the paper has no counterpart): what = 0 -> FP32 fused
+ * multiply-add, 1 -> FP64 fused multiply-add, in TFLOP/s (FMA = 2 flops), from
+ * the fastest of three timed launches of independent FMA chains on every SM
+ * (CUDA events on cuda_stream, NULL = legacy default stream).  Allocates and
+ * frees a few bytes of device memory.
+ */
+POLFMM_API int fmm_measure_peak(int what, void* cuda_stream, double* tflops);
+
 /* Release every device buffer of the context; NULL is a no-op. */
 POLFMM_API void fmm_destroy(polfmm_ctx* ctx);
 

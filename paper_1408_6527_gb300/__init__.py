@@ -228,4 +228,14 @@ class PolFMM:
         return int(self.lib.fmm_launch_count(self.h))
 
 
+def measure_peak(kind: str, stream=None) -> float:
+    """Measured FP32 ("fp32") or FP64 ("fp64") fused multiply-add peak of the
+    current device in TFLOP/s (for roofline fractions)."""
+    lib = _lib.load()
+    v = ctypes.c_double()
+    _lib.check(lib.fmm_measure_peak({"fp32": 0, "fp64": 1}[kind], ctypes.c_void_p(stream or 0), ctypes.byref(v)),
+               "fmm_measure_peak")
+    return v.value
+
+
 from .autograd import polarizable_energy  # noqa: E402

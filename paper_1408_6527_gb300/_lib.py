@@ -72,6 +72,7 @@ SIGNATURES = {
     "fmm_profile_reset": (I, [P]),
     "fmm_launch_count": (I64, [P]),
     "fmm_testing_alloc_hook": (I64, [I64]),
+    "fmm_measure_peak": (I, [I, P, ctypes.POINTER(D)]),
     "fmm_destroy": (None, [P]),
     "fmm_sort_sites_noalloc": (I, [I64, P, I, P, P, P, P, P, P]),
     "fmm_status_string": (ctypes.c_char_p, [I]),

@@ -27,11 +27,37 @@ def test_tensor_core_macs_issued_per_row():
         deg = [int(d) for d in oracle.multi_indices(p).sum(1)]  # degree order, as the kernel stores them
         nc = len(deg)
         macs = 0
-        for k0 in range(0, nc, 8):
+        kt = nc if p > 6 else min(nc, 40)  # p <= 6: the inputs from 40 on are FP32 FMAs
+        for k0 in range(0, kt, 8):
             feeds = sum(1 for d in deg if d <= p - deg[k0])
             macs += max(16, -(-feeds // 16) * 16) * 8
         assert bench.tc_issued_macs_per_row(p) == macs
-    assert bench.tc_issued_macs_per_row(6) == 2432
+    assert bench.tc_issued_macs_per_row(6) == 8 * (96 + 48 + 32 + 16 + 16)
+    assert bench.tc_issued_macs_per_row(8) == 8 * sum(
+        max(16, -(-sum(1 for d in [int(v) for v in oracle.multi_indices(8).sum(1)] if d <= 8 - dk) // 16) * 16)
+        for dk in [int(v) for v in oracle.multi_indices(8).sum(1)][::8])
+
+
+def test_cuda_core_part_of_the_m2l_covers_the_rest():
+    """Tensor-core inputs x their outputs + the CUDA-core FMAs = every retained
+    term |n| + |m| <= p."""
+    for p in range(1, 7):
+        mis = [t for t in itertools.product(range(p + 1), repeat=3) if sum(t) <= p]
+        deg = sorted(sum(t) for t in mis)
+        kt = min((len(mis) + 7) // 8 * 8, 40)
+        terms = sum(1 for dm in deg[:kt] for dn in deg if dn + dm <= p)
+        assert terms + bench.simt_fmas_per_row(p) == bench.m2l_flops_per_box_pair(p) // 2
+    assert bench.simt_fmas_per_row(6) == 16 * 4 + 28
+
+
+def test_shift_flop_counts():
+    """M2M: per coefficient n, three one-axis convolutions of n_x, n_y, n_z terms
+    and one scaling; L2L per level: three passes of p - |n| terms, one scaling
+    and one add."""
+    for p in range(1, 9):
+        mis = [t for t in itertools.product(range(p + 1), repeat=3) if sum(t) <= p]
+        assert bench.m2m_flops_per_box(p) == sum(2 * sum(t) + 1 for t in mis)
+        assert bench.l2l_flops_per_level(p) == sum(3 * 2 * (p - sum(t)) + 2 for t in mis)
 
 
 def test_tree_work_counts_pairs_by_brute_force():

@@ -36,12 +36,26 @@ def _ptr(t):
     return ctypes.c_void_p(t.data_ptr())
 
 
-@pytest.mark.parametrize("index,depth", [(1, 3), (2, 4), (2, 7)])
+def _positions(index):
+    if index == "max":
+        # exactly the largest size the static scratch holds: uniform sites in a cube
+        n = _lib.NOALLOC_MAX_SITES
+        rng = np.random.default_rng(7)
+        return rng.uniform(0.0, 140.0, size=(n, 3)), np.zeros(n), np.ones(n)
+    w = synth.workload(index)
+    return w.pos, w.q, w.alpha
+
+
+@pytest.mark.parametrize("index,depth", [(1, 3), (2, 4), (2, 7), ("max", 6)])
 def test_noalloc_sort_matches_allocating_path(index, depth):
     lib = _lib.load()
-    w = synth.workload(index)
-    pos = torch.as_tensor(w.pos, dtype=torch.float64, device="cuda")
-    with PolFMM(pos, torch.as_tensor(w.q, device="cuda"), torch.as_tensor(w.alpha, device="cuda"), p=2,
+    wpos, wq, walpha = _positions(index)
+
+    class w:  # noqa: N801
+        n = wpos.shape[0]
+
+    pos = torch.as_tensor(wpos, dtype=torch.float64, device="cuda")
+    with PolFMM(pos, torch.as_tensor(wq, device="cuda"), torch.as_tensor(walpha, device="cuda"), p=2,
                 depth=depth) as f:
         ref_cells = f.leaf_cells().cpu().numpy()
         ref_lo, ref_side = f.root_box()
