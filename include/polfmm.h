@@ -177,6 +177,42 @@ POLFMM_API int fmm_set_dipoles(polfmm_ctx* ctx, const double* mu, int on_device)
 /* Forget the current dipoles: the next solve starts again from mu = alpha E^q. */
 POLFMM_API int fmm_reset_dipoles(polfmm_ctx* ctx);
 
+/*
+ * Field charges (Sec. III: the set of charges q^E that generate the field
+ * polarizing the sites, which the force field may choose apart from the
+ * Coulomb charges q; Sec. II.A, E^q).  qE: n float64 in caller order.  After
+ * this call the static field that polarizes the sites is that of the q^E, the
+ * Coulomb energy U^qq' and its field stay those of the q, and
+ * fmm_energy_forces returns
+ *   U^pol = sum |mu|^2/(2 alpha) - sum mu.E^qE - 1/2 sum mu.E^mu,
+ *   F = q E^q + q^E E^mu + (grad E^qE + grad E^mu) mu,
+ *   dU/dq = Phi^q (potential of the Coulomb charges),
+ * with dU/dq^E = Phi^mu (potential of the dipoles) from
+ * fmm_field_charge_gradient.  Without this call q^E = q and dU/dq = Phi^q +
+ * Phi^mu.  Runs the field charges' static pass; kept across
+ * fmm_update_positions.  The dipoles are kept as the next solve's guess.
+ */
+POLFMM_API int fmm_set_field_charges(polfmm_ctx* ctx, const double* qE, int on_device);
+
+/*
+ * Excluded pairs (Sec. II.A: the starred sums skip a list of pairs, e.g. atoms
+ * less than two chemical bonds apart).  pairs: npairs x 2 int32 caller indices
+ * (i != j, each in [0, n); duplicates and both orders allowed); npairs = 0
+ * clears the list.  Every pair is removed from all three sums -- the Coulomb
+ * energy and potential, the static field, and the dipole field of every
+ * solver iteration and of the force pass -- by subtracting its direct terms
+ * from the FMM result over all pairs (one thread per site, partners in
+ * ascending order: deterministic).  Reruns the static passes; kept across
+ * fmm_update_positions.  fmm_static_field, fmm_dipole_field and
+ * fmm_total_field honour the list too.  POLFMM_ERR_INVALID_ARG for an index
+ * out of range or i == j.
+ */
+POLFMM_API int fmm_set_exclusions(polfmm_ctx* ctx, int64_t npairs, const int32_t* pairs, int on_device);
+
+/* dU/dq^E = Phi^mu (n, caller order) from the last fmm_energy_forces with field
+ * charges set; POLFMM_ERR_STATE before one. */
+POLFMM_API int fmm_field_charge_gradient(polfmm_ctx* ctx, double* dU_dqE, int on_device);
+
 /* New positions for the same sites: rebuild the tree and the static pass,
  * keeping the current dipoles as the next solve's starting guess. */
 POLFMM_API int fmm_update_positions(polfmm_ctx* ctx, const double* positions, int on_device);

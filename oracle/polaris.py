@@ -40,7 +40,7 @@ from __future__ import annotations
 
 import numpy as np
 
-from . import OracleError, fmm_fields
+from . import OracleError, fmm_fields, pcg_dipole_solve
 
 
 def _pairs(pos):
@@ -109,11 +109,15 @@ def _excluded_correction(pos, exclusions, w, mu=None):
     return phi, E, G
 
 
-def polaris_energy(pos, q, qE, alpha, exclusions=(), method="dense", p=8, depth=3, root=None):
+def polaris_energy(pos, q, qE, alpha, exclusions=(), method="dense", p=8, depth=3, root=None, solve="dense",
+                   tol=1e-13, max_iter=500):
     """U, its gradients and the dipoles for charges q, field charges qE,
     polarizabilities alpha and the excluded pairs. method: "dense" (pair sums)
     or "fmm" (CPU octree FMM at order p over all pairs, minus the excluded
-    pairs' direct terms)."""
+    pairs' direct terms). solve: "dense" (Cholesky of diag(1/alpha) - T, T
+    built column by column from the method's dipole field and symmetrised) or
+    "pcg" (the preconditioned conjugate gradients of ``oracle.pcg_dipole_solve``
+    on the method's dipole field as it is, to the relative residual tol)."""
     pos = np.ascontiguousarray(pos, dtype=np.float64)
     q, qE, alpha = (np.asarray(v, dtype=np.float64) for v in (q, qE, alpha))
     n = pos.shape[0]
@@ -144,10 +148,15 @@ def polaris_energy(pos, q, qE, alpha, exclusions=(), method="dense", p=8, depth=
     phi_c, E_c, _ = charges(q)
     _, E_qE, G_qE = charges(qE)
     # mu = alpha (E^qE + T mu) on the polarizable sites: dense Cholesky of
-    # diag(1/alpha) - T over the active sites, T applied through `dipoles`
+    # diag(1/alpha) - T over the active sites, T applied through `dipoles`,
+    # or PCG with that operator
     idx = np.nonzero(act)[0]
     mu = np.zeros((n, 3))
-    if idx.size:
+    if solve == "pcg":
+        mu, _, _, _ = pcg_dipole_solve(alpha, E_qE, lambda v: dipoles(v)[1], tol=tol, max_iter=max_iter)
+    elif solve != "dense":
+        raise ValueError(solve)
+    elif idx.size:
         k = idx.size
         T = np.zeros((3 * k, 3 * k))
         for c in range(3 * k):

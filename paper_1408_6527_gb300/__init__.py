@@ -175,6 +175,23 @@ class PolFMM:
         b = self._in(pos, (self.n, 3))
         _lib.check(self.lib.fmm_update_positions(self.h, b.ptr, int(self.device)), "fmm_update_positions")
 
+    def set_field_charges(self, qE):
+        """Field charges q^E (Sec. III): the charges whose field polarizes the sites."""
+        b = self._in(qE, (self.n,))
+        _lib.check(self.lib.fmm_set_field_charges(self.h, b.ptr, int(self.device)), "fmm_set_field_charges")
+
+    def set_exclusions(self, pairs):
+        """Excluded site pairs (Sec. II.A starred sums), an (m, 2) integer array of caller indices."""
+        arr = np.ascontiguousarray(np.asarray(pairs, dtype=np.int32).reshape(-1, 2))
+        _lib.check(self.lib.fmm_set_exclusions(self.h, int(arr.shape[0]), arr.ctypes.data_as(ctypes.c_void_p), 0),
+                   "fmm_set_exclusions")
+
+    def field_charge_gradient(self):
+        """dU/dq^E of the last energy_forces() with field charges set."""
+        out, p = self._out(self.n)
+        _lib.check(self.lib.fmm_field_charge_gradient(self.h, p, int(self.device)), "fmm_field_charge_gradient")
+        return out
+
     def static_field(self):
         phi, pp = self._out(self.n)
         E, pe = self._out(self.n, 3)

@@ -8,6 +8,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <utility>
 #include <new>
 #include <string>
 #include <vector>
@@ -320,7 +321,7 @@ int allocate(polfmm_ctx* c) {
     c->ploc = A.get<unsigned char>(3 * n * rsz);
     c->srcA = A.get<unsigned char>(n * source_record_bytes(c->mixed));
     c->srcB = A.get<unsigned char>(n * source_record_bytes(c->mixed));
-    c->in_buf = A.get<double>(8 * n);
+    c->in_buf = A.get<double>(9 * n);  // positions, q, alpha, mu, q^E (caller order)
     c->out_buf = A.get<double>(10 * n);
     c->phiq = A.get<double>(n);
     c->Eq = A.get<double>(3 * n);
@@ -458,6 +459,36 @@ __global__ void leaf_cells_kernel(int64_t n, const uint32_t* __restrict__ key, c
     out[3 * (int64_t)o + 2] = (int32_t)compact3(k >> 2);
 }
 
+// The field charges q^E stand in for the charges q as the sources of one pass
+// (the packed near-field records and the P2M read c->q_s and c->srcA).
+struct FieldChargeSources {
+    polfmm_ctx* c;
+    double* q;
+    void* a;
+    explicit FieldChargeSources(polfmm_ctx* ctx) : c(ctx), q(ctx->q_s), a(ctx->srcA) {
+        if (c->qE_s) {
+            c->q_s = c->qE_s;
+            c->srcA = c->srcAE;
+        }
+    }
+    ~FieldChargeSources() {
+        c->q_s = q;
+        c->srcA = a;
+    }
+};
+
+// static passes (Sec. III, first stage): potential and field of the Coulomb
+// charges q, and with field charges set those of the q^E, which polarize the
+// sites; every pass without the excluded pairs
+void static_passes(polfmm_ctx* c) {
+    fmm_pass(c, LEAF_CHARGE_PHI_E, true, nullptr, c->phiq, c->Eq, nullptr);
+    if (c->qE_s) {
+        FieldChargeSources fc(c);
+        pack_positions(c);  // (x, y, z, q^E) records
+        fmm_pass(c, LEAF_CHARGE_PHI_E, true, nullptr, c->phiqE, c->EqE, nullptr);
+    }
+}
+
 // build the tree from caller-order inputs staged in in_buf and run the static pass
 int rebuild(polfmm_ctx* c) {
     const int64_t n = c->n;
@@ -480,8 +511,10 @@ int rebuild(polfmm_ctx* c) {
         return rc;
     }
     if ((rc = ensure_lp(c)) != POLFMM_OK) return rc;
+    if (c->qE_s) gather_sites(c, c->in_buf + 8 * n, c->qE_s, 1);
+    exclusion_inv_perm(c);
     pack_positions(c);
-    fmm_pass(c, LEAF_CHARGE_PHI_E, true, nullptr, c->phiq, c->Eq, nullptr);
+    static_passes(c);
     c->pcg_graph_dirty = true;  // launch sizes of the solver iteration changed
     c->loop_dirty = true;
     return read_err(c);
@@ -827,7 +860,10 @@ int fmm_energy_forces(polfmm_ctx* c, double* energy_out, double* forces, double*
     if (!c) return POLFMM_ERR_INVALID_ARG;
     if (!c->have_mu) return POLFMM_ERR_STATE;
     const int64_t n = c->n;
-    fmm_pass(c, LEAF_FULL, true, c->mu, c->phi_t, c->E_t, c->G_t);
+    {
+        FieldChargeSources fc(c);  // sources: the field charges (or q) and the dipoles
+        fmm_pass(c, LEAF_FULL, true, c->mu, c->phi_t, c->E_t, c->G_t);
+    }
     double* F = forces;
     double* dq = dU_dq;
     double* da = dU_dalpha;
@@ -848,6 +884,7 @@ int fmm_energy_forces(polfmm_ctx* c, double* energy_out, double* forces, double*
     const double k = c->opt.coulomb_k;
     const double uqq = k * c->h_scal[S_UQQ];
     const double upol = k * (c->h_scal[S_AMU] - c->h_scal[S_MUEQ] - 0.5 * c->h_scal[S_MUEMU]);
+    c->have_dqE = c->qE_s != nullptr;
     if (energy_out) {
         energy_out[0] = uqq + upol;
         energy_out[1] = uqq;
@@ -896,6 +933,97 @@ int fmm_reset_dipoles(polfmm_ctx* c) {
     return POLFMM_OK;
 }
 
+int fmm_set_field_charges(polfmm_ctx* c, const double* qE, int on_device) {
+    if (!c || !qE) return POLFMM_ERR_INVALID_ARG;
+    const int64_t n = c->n;
+    if (!on_device && !finite_host(qE, (size_t)n)) return POLFMM_ERR_INVALID_ARG;
+    if (!c->qE_s) {
+        Alloc& A = extra_of(c)->alloc;
+        c->qE_s = A.get<double>(n);
+        c->srcAE = A.get<unsigned char>(n * source_record_bytes(c->mixed));
+        c->phiqE = A.get<double>(n);
+        c->EqE = A.get<double>(3 * n);
+        c->dqE = A.get<double>(n);
+        if (!A.ok) return POLFMM_ERR_OUT_OF_MEMORY;
+    }
+    int rc = copy_in(c, c->in_buf + 8 * n, qE, (size_t)n, on_device);
+    if (rc != POLFMM_OK) return rc;
+    gather_sites(c, c->in_buf + 8 * n, c->qE_s, 1);
+    {
+        FieldChargeSources fc(c);
+        pack_positions(c);
+        fmm_pass(c, LEAF_CHARGE_PHI_E, true, nullptr, c->phiqE, c->EqE, nullptr);
+    }
+    c->have_dqE = false;
+    return read_err(c);
+}
+
+int fmm_set_exclusions(polfmm_ctx* c, int64_t npairs, const int32_t* pairs, int on_device) {
+    if (!c || npairs < 0 || (npairs > 0 && !pairs) || npairs > (int64_t)1 << 30) return POLFMM_ERR_INVALID_ARG;
+    const int64_t n = c->n;
+    std::vector<int32_t> h((size_t)2 * npairs);
+    if (npairs > 0) {
+        if (on_device) {
+            if (cudaMemcpy(h.data(), pairs, sizeof(int32_t) * h.size(), cudaMemcpyDeviceToHost) != cudaSuccess)
+                return cuda_fail(cudaGetLastError(), "copy of the excluded pairs");
+        } else {
+            memcpy(h.data(), pairs, sizeof(int32_t) * h.size());
+        }
+    }
+    // both directions of every pair, sorted by site then partner, duplicates dropped
+    std::vector<std::pair<int, int>> e;
+    e.reserve(h.size());
+    for (int64_t k = 0; k < npairs; k++) {
+        const int32_t i = h[2 * k], j = h[2 * k + 1];
+        if (i < 0 || j < 0 || i >= n || j >= n || i == j) return POLFMM_ERR_INVALID_ARG;
+        e.emplace_back(i, j);
+        e.emplace_back(j, i);
+    }
+    std::sort(e.begin(), e.end());
+    e.erase(std::unique(e.begin(), e.end()), e.end());
+    std::vector<int> targets, ptr(1, 0), idx;
+    for (size_t k = 0; k < e.size(); k++) {
+        if (k == 0 || e[k].first != e[k - 1].first) {
+            if (k) ptr.push_back((int)k);
+            targets.push_back(e[k].first);
+        }
+        idx.push_back(e[k].second);
+    }
+    if (!e.empty()) ptr.push_back((int)e.size());
+    Alloc& A = extra_of(c)->alloc;
+    if (!c->inv_perm) c->inv_perm = A.get<int>(n);
+    if (targets.size() > c->excl_targets_cap) {
+        c->excl_targets_cap = targets.size();
+        c->excl_targets = A.get<int>(targets.size());
+        c->excl_ptr = A.get<int>(targets.size() + 1);
+    }
+    if (idx.size() > c->excl_cap) {
+        c->excl_cap = idx.size();
+        c->excl_idx = A.get<int>(idx.size());
+    }
+    if (!A.ok) return POLFMM_ERR_OUT_OF_MEMORY;
+    if (!targets.empty() &&
+        (cudaMemcpy(c->excl_targets, targets.data(), sizeof(int) * targets.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+         cudaMemcpy(c->excl_ptr, ptr.data(), sizeof(int) * ptr.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+         cudaMemcpy(c->excl_idx, idx.data(), sizeof(int) * idx.size(), cudaMemcpyHostToDevice) != cudaSuccess))
+        return cuda_fail(cudaGetLastError(), "upload of the excluded pairs");
+    c->n_excl = (int64_t)(e.size() / 2);
+    c->n_excl_targets = (int)targets.size();
+    exclusion_inv_perm(c);
+    static_passes(c);
+    c->pcg_graph_dirty = true;  // the solver pass gains (or loses) the correction kernel
+    c->loop_dirty = true;
+    c->have_dqE = false;
+    return read_err(c);
+}
+
+int fmm_field_charge_gradient(polfmm_ctx* c, double* dU_dqE, int on_device) {
+    if (!c || !dU_dqE) return POLFMM_ERR_INVALID_ARG;
+    if (!c->have_dqE) return POLFMM_ERR_STATE;
+    int rc = scatter_out(c, c->dqE, dU_dqE, 1, on_device);
+    return rc != POLFMM_OK ? rc : read_err(c);
+}
+
 int fmm_update_positions(polfmm_ctx* c, const double* positions, int on_device) {
     if (!c || !positions) return POLFMM_ERR_INVALID_ARG;
     const int64_t n = c->n;
@@ -904,6 +1032,8 @@ int fmm_update_positions(polfmm_ctx* c, const double* positions, int on_device) 
     scatter_sites(c, c->q_s, c->in_buf + 3 * n, 1);
     scatter_sites(c, c->alpha_s, c->in_buf + 4 * n, 1);
     if (c->have_mu) scatter_sites(c, c->mu, c->in_buf + 5 * n, 3);
+    if (c->qE_s) scatter_sites(c, c->qE_s, c->in_buf + 8 * n, 1);
+    c->have_dqE = false;
     int rc = copy_in(c, c->in_buf, positions, 3 * (size_t)n, on_device);
     if (rc != POLFMM_OK) return rc;
     if ((rc = rebuild(c)) != POLFMM_OK) return rc;

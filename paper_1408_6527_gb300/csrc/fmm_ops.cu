@@ -1152,6 +1152,8 @@ static bool pass_impl(polfmm_ctx* c, int mode, bool use_q, const double* mu_sort
             cudaStreamWaitEvent(c->side_stream, c->ev_fork, 0);
         }
         launch_leaf<R>(c, mode, mu_sorted, phi, E, G, mu_packed, overlap ? c->side_stream : c->stream, 0);
+        // excluded pairs off the near field, before the far field completes it
+        exclusion_correct(c, mode, nullptr, mu_sorted, nullptr, E, nullptr, overlap ? c->side_stream : c->stream);
         if (overlap) cudaEventRecord(c->ev_join, c->side_stream);
     }
     if (d >= 2) {
@@ -1191,6 +1193,7 @@ static bool pass_impl(polfmm_ctx* c, int mode, bool use_q, const double* mu_sort
         return pcg;
     }
     launch_leaf<R>(c, mode, mu_sorted, phi, E, G, mu_packed, c->stream, d >= 2 ? 1 : 0);
+    exclusion_correct(c, mode, use_q ? c->q_s : nullptr, mu_sorted, phi, E, G, c->stream);
     return false;
 }
 

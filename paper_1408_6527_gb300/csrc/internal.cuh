@@ -178,6 +178,21 @@ struct polfmm_ctx {
     int* h_counts = nullptr;      // pinned host copy of tree counts
     double* h_bbox = nullptr;     // pinned host bounding box
 
+    // field charges and excluded pairs (Sec. II.A, III); see polaris.cu
+    double* qE_s = nullptr;       // field charges q^E (sorted); null: q^E = q
+    void* srcAE = nullptr;        // packed (x, y, z, q^E) per sorted site
+    double* phiqE = nullptr;      // potential and field of the field charges (null: phiq, Eq)
+    double* EqE = nullptr;
+    double* dqE = nullptr;        // dU/dq^E of the last force pass (sorted)
+    int64_t n_excl = 0;           // excluded pairs
+    int n_excl_targets = 0;       // sites with at least one excluded partner
+    int* excl_targets = nullptr;  // their caller indices
+    int* excl_ptr = nullptr;      // [n_excl_targets + 1] offsets into excl_idx
+    int* excl_idx = nullptr;      // [2 n_excl] partners, caller indices, ascending per site
+    int* inv_perm = nullptr;      // [n] sorted index of each caller index
+    size_t excl_cap = 0, excl_targets_cap = 0;
+    bool have_dqE = false;        // dqE holds the last force pass's dU/dq^E
+
     bool have_mu = false;
     int64_t launches = 0;
     void* extra = nullptr;        // host-side bookkeeping of device allocations
@@ -255,6 +270,14 @@ void energy_stationary(polfmm_ctx* c);
 // residual growths in a row after which a solve stops as not converged
 constexpr int kStagnationIters = 3;
 void mask_dipoles(polfmm_ctx* c, double* v);
+
+// polaris.cu: subtract the excluded pairs' direct terms from the outputs of a
+// pass (leaf_mode: the pass's sources), and the caller -> sorted map they use
+void exclusion_correct(polfmm_ctx* c, int leaf_mode, const double* w_sorted, const double* mu_sorted, double* phi,
+                       double* E, double* G, cudaStream_t st);
+void exclusion_inv_perm(polfmm_ctx* c);
+// the field that polarizes the sites: that of the field charges when set
+inline const double* polarizing_field(const polfmm_ctx* c) { return c->EqE ? c->EqE : c->Eq; }
 
 // device scalar slots
 enum Scal {

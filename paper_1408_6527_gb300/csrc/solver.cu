@@ -303,15 +303,25 @@ __global__ void scatter_kernel(int64_t n, int comps, const int* __restrict__ per
     dst[(int64_t)perm[i] * comps + k] = scale * src[t];
 }
 
-// forces, dU/dq, dU/dalpha (caller order) and energy partials
-// F = q E + (grad E) mu;  dU/dq = Phi;  dU/dalpha = -|mu|^2 / (2 alpha^2)
-// (-|E|^2/2 where alpha = 0); energies: 1/2 q Phi^q, mu.E^q, mu.E^mu, |mu|^2/(2 alpha)
+// forces, dU/dq, dU/dalpha (caller order) and energy partials, at the dipoles
+// mu (Sec. II.A, Eq. upol_derivatives).  The last FMM pass had the field
+// charges q^E (= q when none are set) and the dipoles as sources: phi, E, G;
+// phiq, Eq are the potential and field of the Coulomb charges q, EqE, phiqE
+// those of the field charges (null: the same as phiq, Eq).  With E^mu = E - EqE
+// and Phi^mu = phi - phiqE:
+//   F = q Eq + q^E E^mu + (grad E) mu;  U^pol terms use E^q = EqE and E^mu;
+//   dU/dq = phiq + Phi^mu (= phi) without field charges, phiq with them, and
+//   then dU/dq^E = Phi^mu (written to dqE, sorted order);
+//   dU/dalpha = -|mu|^2 / (2 alpha^2) (-|E|^2/2 where alpha = 0);
+// energies: 1/2 q Phi^q, mu.E^q, mu.E^mu, |mu|^2/(2 alpha)
 __global__ void assemble_kernel(int64_t n, const int* __restrict__ perm, const double* __restrict__ q,
-                                const double* __restrict__ alpha, const double* __restrict__ mu,
-                                const double* __restrict__ phiq, const double* __restrict__ Eq,
-                                const double* __restrict__ phi, const double* __restrict__ E,
-                                const double* __restrict__ G, double kc, double* __restrict__ F,
-                                double* __restrict__ dq, double* __restrict__ da, double* __restrict__ partial) {
+                                const double* __restrict__ qE, const double* __restrict__ alpha,
+                                const double* __restrict__ mu, const double* __restrict__ phiq,
+                                const double* __restrict__ Eq, const double* __restrict__ phiqE,
+                                const double* __restrict__ EqE, const double* __restrict__ phi,
+                                const double* __restrict__ E, const double* __restrict__ G, double kc,
+                                double* __restrict__ F, double* __restrict__ dq, double* __restrict__ dqE,
+                                double* __restrict__ da, double* __restrict__ partial) {
     __shared__ double sh[kRedThreads];
     double uqq = 0, mueq = 0, muemu = 0, amu = 0;
     RED_LOOP(i, n) {
@@ -320,16 +330,29 @@ __global__ void assemble_kernel(int64_t n, const int* __restrict__ perm, const d
         const double e0 = E[3 * i], e1 = E[3 * i + 1], e2 = E[3 * i + 2];
         const double* g = G + 6 * i;
         const int o = perm[i];
+        const double* ep = EqE ? EqE : Eq;  // the polarizing field E^q
+        const double q0 = ep[3 * i], q1 = ep[3 * i + 1], q2 = ep[3 * i + 2];
         if (F) {
-            F[3 * (int64_t)o + 0] = kc * (qi * e0 + g[0] * m0 + g[1] * m1 + g[2] * m2);
-            F[3 * (int64_t)o + 1] = kc * (qi * e1 + g[1] * m0 + g[3] * m1 + g[4] * m2);
-            F[3 * (int64_t)o + 2] = kc * (qi * e2 + g[2] * m0 + g[4] * m1 + g[5] * m2);
+            double f0, f1, f2;
+            if (qE) {
+                const double qe = qE[i];
+                f0 = qi * Eq[3 * i] + qe * (e0 - q0);
+                f1 = qi * Eq[3 * i + 1] + qe * (e1 - q1);
+                f2 = qi * Eq[3 * i + 2] + qe * (e2 - q2);
+            } else {
+                f0 = qi * e0;
+                f1 = qi * e1;
+                f2 = qi * e2;
+            }
+            F[3 * (int64_t)o + 0] = kc * (f0 + g[0] * m0 + g[1] * m1 + g[2] * m2);
+            F[3 * (int64_t)o + 1] = kc * (f1 + g[1] * m0 + g[3] * m1 + g[4] * m2);
+            F[3 * (int64_t)o + 2] = kc * (f2 + g[2] * m0 + g[4] * m1 + g[5] * m2);
         }
-        if (dq) dq[o] = kc * phi[i];
+        if (dq) dq[o] = kc * (qE ? phiq[i] : phi[i]);
+        if (dqE) dqE[i] = kc * (phi[i] - (phiqE ? phiqE[i] : phiq[i]));
         const double mm = m0 * m0 + m1 * m1 + m2 * m2;
         if (da) da[o] = ai > 0.0 ? -kc * mm / (2.0 * ai * ai) : -0.5 * kc * (e0 * e0 + e1 * e1 + e2 * e2);
         uqq += 0.5 * qi * phiq[i];
-        const double q0 = Eq[3 * i], q1 = Eq[3 * i + 1], q2 = Eq[3 * i + 2];
         mueq += m0 * q0 + m1 * q1 + m2 * q2;
         muemu += m0 * (e0 - q0) + m1 * (e1 - q1) + m2 * (e2 - q2);
         if (ai > 0.0) amu += mm / (2.0 * ai);
@@ -346,8 +369,9 @@ __global__ void assemble_kernel(int64_t n, const int* __restrict__ perm, const d
     }
 }
 
-// stationary energy terms (Sec. II.A): partials of 1/2 q Phi^q and mu.E^q; at a
-// converged solve U^pol = -1/2 sum mu.E^q (Eq. upol_derivatives)
+// stationary energy terms (Sec. II.A): partials of 1/2 q Phi^q and mu.E^q (E^q
+// the polarizing field); at a converged solve U^pol = -1/2 sum mu.E^q (Eq.
+// upol_derivatives)
 __global__ void energy_stationary_kernel(int64_t n, const double* __restrict__ q, const double* __restrict__ mu,
                                          const double* __restrict__ phiq, const double* __restrict__ Eq,
                                          double* __restrict__ partial) {
@@ -392,12 +416,12 @@ void mask_dipoles(polfmm_ctx* c, double* v) {
 void solver_init(polfmm_ctx* c, bool warm) {
     if (!warm) {
         LaunchScope ls(c, F_SOLVER);
-        mu_init_kernel<<<grid_for(3 * c->n, 256), 256, 0, c->stream>>>(c->n, c->alpha_s, c->Eq, c->mu);
+        mu_init_kernel<<<grid_for(3 * c->n, 256), 256, 0, c->stream>>>(c->n, c->alpha_s, polarizing_field(c), c->mu);
     }
     if (c->opt.solver == POLFMM_SOLVER_JACOBI) {
         {
             LaunchScope ls(c, F_SOLVER);
-            norm_b_kernel<<<kRedBlocks, kRedThreads, 0, c->stream>>>(c->n, c->alpha_s, c->Eq, c->partial);
+            norm_b_kernel<<<kRedBlocks, kRedThreads, 0, c->stream>>>(c->n, c->alpha_s, polarizing_field(c), c->partial);
         }
         reduce(c, 1, S_BB, 0, 0, 0, 0, F_SOLVER);
         return;
@@ -405,7 +429,7 @@ void solver_init(polfmm_ctx* c, bool warm) {
     fmm_pass(c, LEAF_DIPOLE_E, false, c->mu, nullptr, c->Td, nullptr);
     {
         LaunchScope ls(c, F_SOLVER);
-        pcg_init_kernel<<<kRedBlocks, kRedThreads, 0, c->stream>>>(c->n, c->alpha_s, c->Eq, c->mu, c->Td, c->r,
+        pcg_init_kernel<<<kRedBlocks, kRedThreads, 0, c->stream>>>(c->n, c->alpha_s, polarizing_field(c), c->mu, c->Td, c->r,
                                                                     c->z, c->d, c->partial);
     }
     reduce(c, 3, S_RZ, S_RR, S_BB, 0, 2, F_SOLVER);
@@ -451,7 +475,8 @@ void solver_jacobi_step(polfmm_ctx* c) {
     fmm_pass(c, LEAF_DIPOLE_E, false, c->mu, nullptr, c->Td, nullptr);
     {
         LaunchScope ls(c, F_SOLVER);
-        jacobi_kernel<<<kRedBlocks, kRedThreads, 0, c->stream>>>(c->n, c->alpha_s, c->Eq, c->Td, c->mu, c->partial);
+        jacobi_kernel<<<kRedBlocks, kRedThreads, 0, c->stream>>>(c->n, c->alpha_s, polarizing_field(c), c->Td, c->mu,
+                                                                c->partial);
     }
     reduce(c, 1, S_RR, 0, 0, 0, 0, F_SOLVER);
 }
@@ -461,8 +486,9 @@ void energy_and_gradients(polfmm_ctx* c, double* F, double* dq, double* da, bool
     {
         LaunchScope ls(c, F_ASSEMBLE);
         assemble_kernel<<<kRedBlocks, kRedThreads, 0, c->stream>>>(
-            c->n, c->perm, c->q_s, c->alpha_s, c->mu, c->phiq, c->Eq, c->phi_t, c->E_t, c->G_t, c->opt.coulomb_k,
-            want_f ? F : nullptr, want_dq ? dq : nullptr, want_da ? da : nullptr, c->partial);
+            c->n, c->perm, c->q_s, c->qE_s, c->alpha_s, c->mu, c->phiq, c->Eq, c->phiqE, c->EqE, c->phi_t, c->E_t,
+            c->G_t, c->opt.coulomb_k, want_f ? F : nullptr, want_dq ? dq : nullptr, c->qE_s ? c->dqE : nullptr,
+            want_da ? da : nullptr, c->partial);
     }
     reduce(c, 4, S_UQQ, S_MUEQ, S_MUEMU, S_AMU, 0, F_ASSEMBLE);
 }
@@ -470,8 +496,8 @@ void energy_and_gradients(polfmm_ctx* c, double* F, double* dq, double* da, bool
 void energy_stationary(polfmm_ctx* c) {
     {
         LaunchScope ls(c, F_ASSEMBLE);
-        energy_stationary_kernel<<<kRedBlocks, kRedThreads, 0, c->stream>>>(c->n, c->q_s, c->mu, c->phiq, c->Eq,
-                                                                              c->partial);
+        energy_stationary_kernel<<<kRedBlocks, kRedThreads, 0, c->stream>>>(c->n, c->q_s, c->mu, c->phiq,
+                                                                              polarizing_field(c), c->partial);
     }
     reduce(c, 2, S_UQQ, S_MUEQ, 0, 0, 0, F_ASSEMBLE);
 }

@@ -109,3 +109,14 @@ def test_fmm_with_the_exclusion_correction_matches_the_pair_sums():
         f = polaris.polaris_energy(pos, q, qE, alpha, ex, method="fmm", p=8, depth=2, root=(lo, side))
         err[len(ex) > 0] = oracle.rel_rms(f["F"], d["F"])
     assert 0.0 < err[True] < 1.5 * err[False]
+
+
+def test_pcg_solve_reproduces_the_dense_solve():
+    """The conjugate-gradient solve of the same (exactly symmetric) dense
+    operator gives the Cholesky dipoles, energy and gradients."""
+    pos, q, qE, alpha, excl = _system()
+    a = polaris.polaris_energy(pos, q, qE, alpha, excl)
+    b = polaris.polaris_energy(pos, q, qE, alpha, excl, solve="pcg", tol=1e-14)
+    assert abs(a["U"] - b["U"]) < 1e-12 * abs(a["U"])
+    for k in ("F", "dUdq", "dUdqE", "dUdalpha", "mu"):
+        assert oracle.rel_rms(b[k], a[k]) < 1e-10, k
