@@ -307,6 +307,53 @@ POLFMM_API int fmm_sort_sites_noalloc(int64_t n, const double* positions, int tr
                                       void* cuda_stream);
 
 /*
+ * Dynamics around the FMM (Sec. IV.B runs molecular dynamics on these forces,
+ * with the long-range part on a longer time step than the short-range part).
+ * The paper's force field has short-range terms of its own, which are not part
+ * of this library; the calls below give the purely repulsive wall that keeps
+ * undamped point dipoles apart during a run, and the kicks and drifts of
+ * velocity Verlet and of the reversible multiple-time-step integrator, so that
+ * a step runs in device kernels only.  All pointers are device pointers on the
+ * stream named at creation (or given); all arrays are float64, positions,
+ * velocities and forces n x 3 row-major, masses n.
+ *
+ * fmm_wall_create: scratch for up to max_sites sites (1 <= max_sites <= 2^28;
+ * about 40 bytes per site plus a hash table of 8 bytes per bucket, with at
+ * least 2 max_sites buckets).  POLFMM_ERR_OUT_OF_MEMORY leaves *out NULL.
+ */
+typedef struct polfmm_wall polfmm_wall;
+POLFMM_API int fmm_wall_create(polfmm_wall** out, int64_t max_sites, void* cuda_stream);
+
+/*
+ * The wall U = sum over pairs i < j with r_ij < r_c = 2^(1/6) sigma of
+ * 4 eps [(sigma/r_ij)^12 - (sigma/r_ij)^6] + eps (zero and with zero slope at
+ * r_c) and its forces F_i = -dU/dx_i, in FP64.  energy: one double, written on
+ * the device (the caller reads it when it needs it); forces: n x 3,
+ * overwritten.  Pairs come from a spatial hash of cells of side r_c; every sum
+ * runs in a fixed order, so that the outputs are bitwise reproducible.
+ * POLFMM_ERR_INVALID_ARG for n > max_sites, eps < 0 or sigma <= 0.  Coincident
+ * sites give non-finite values (the FMM rejects them at fmm_build).
+ */
+POLFMM_API int fmm_wall_forces(polfmm_wall* wall, const double* positions, int64_t n, double eps, double sigma,
+                               double* energy, double* forces);
+
+/* Kinetic energy scale * sum_i 1/2 m_i |v_i|^2 into one device double (fixed
+ * summation order), on the wall's stream and scratch. */
+POLFMM_API int fmm_md_kinetic(polfmm_wall* wall, const double* velocities, const double* masses, int64_t n,
+                              double scale, double* energy);
+
+/* Kick v_i += coef * F_i / m_i (coef = the time step share times the unit
+ * conversion from force / mass to acceleration). */
+POLFMM_API int fmm_md_kick(double* velocities, const double* forces, const double* masses, double coef, int64_t n,
+                           void* cuda_stream);
+
+/* Drift x_i += dt * v_i. */
+POLFMM_API int fmm_md_drift(double* positions, const double* velocities, double dt, int64_t n, void* cuda_stream);
+
+/* Release the wall's scratch (after its stream has finished); NULL is a no-op. */
+POLFMM_API void fmm_wall_destroy(polfmm_wall* wall);
+
+/*
  * Measured peak rate of one arithmetic unit of the current device, for
  * roofline fractions (the paper has no counterpart): what = 0 -> FP32 fused
  * multiply-add, 1 -> FP64 fused multiply-add, in TFLOP/s (FMA = 2 flops), from

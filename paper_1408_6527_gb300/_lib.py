@@ -76,6 +76,12 @@ SIGNATURES = {
     "fmm_launch_count": (I64, [P]),
     "fmm_testing_alloc_hook": (I64, [I64]),
     "fmm_measure_peak": (I, [I, P, ctypes.POINTER(D)]),
+    "fmm_wall_create": (I, [ctypes.POINTER(P), I64, P]),
+    "fmm_wall_forces": (I, [P, P, I64, D, D, P, P]),
+    "fmm_md_kinetic": (I, [P, P, P, I64, D, P]),
+    "fmm_md_kick": (I, [P, P, P, D, I64, P]),
+    "fmm_md_drift": (I, [P, P, D, I64, P]),
+    "fmm_wall_destroy": (None, [P]),
     "fmm_destroy": (None, [P]),
     "fmm_sort_sites_noalloc": (I, [I64, P, I, P, P, P, P, P, P]),
     "fmm_status_string": (ctypes.c_char_p, [I]),

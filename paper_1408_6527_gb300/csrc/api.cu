@@ -16,6 +16,13 @@
 #include "internal.cuh"
 
 namespace polfmm {
+
+thread_local char g_last_error[256] = "";
+
+int cuda_fail(cudaError_t e, const char* where) {
+    snprintf(g_last_error, sizeof(g_last_error), "%s: %s (%s)", where, cudaGetErrorName(e), cudaGetErrorString(e));
+    return POLFMM_ERR_CUDA;
+}
 int fmm_ops_init_attributes(polfmm_ctx* c);
 size_t m2l_simt_smem(int ncoef, size_t rsize);
 int m2l_tensor_prepare(polfmm_ctx* c);
@@ -406,12 +413,6 @@ int ensure_lp(polfmm_ctx* c) {
     return POLFMM_OK;
 }
 
-thread_local char g_last_error[256] = "";
-
-int cuda_fail(cudaError_t e, const char* where) {
-    snprintf(g_last_error, sizeof(g_last_error), "%s: %s (%s)", where, cudaGetErrorName(e), cudaGetErrorString(e));
-    return POLFMM_ERR_CUDA;
-}
 
 int read_err(polfmm_ctx* c) {
     int h[4] = {0, 0, 0, 0};

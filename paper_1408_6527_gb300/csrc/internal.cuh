@@ -227,6 +227,8 @@ namespace polfmm {
 // every device or pinned-host allocation of the library goes through these two,
 // so that fmm_testing_alloc_hook can make the k-th one fail
 cudaError_t dev_alloc(void** p, size_t bytes);
+// records the CUDA error for fmm_last_error and returns POLFMM_ERR_CUDA
+int cuda_fail(cudaError_t e, const char* where);
 cudaError_t host_alloc(void** p, size_t bytes);
 
 // launch bookkeeping / profiling around one kernel launch

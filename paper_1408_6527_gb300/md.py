@@ -1,5 +1,5 @@
-"""Velocity-Verlet dynamics on the polarizable FMM forces, and the finite-
-difference check of the gradients (the differentiation / MD configuration).
+"""Velocity-Verlet and multiple-time-step dynamics on the polarizable FMM
+forces, and the finite-difference check of the gradients (the differentiation / MD configuration).
 
 Units: positions in Angstrom, charges in e, polarizabilities in Angstrom^3,
 masses in amu, time in fs, energies in kcal/mol (Coulomb constant
@@ -14,8 +14,9 @@ collapses within some tens of fs.  The paper's force field has short-range
 repulsion that is out of scope here, so the dynamics adds a purely repulsive
 wall (the repulsive part of a Lennard-Jones pair, shifted to zero at its
 minimum): U = 4 eps [(sigma/r)^12 - (sigma/r)^6] + eps for r < 2^(1/6) sigma,
-eps = 5 kcal/mol, sigma = 2.05 A (zero beyond 2.30 A), evaluated in FP64 with
-a cell list (torch operations on the GPU; it is not part of the FMM path).
+eps = 5 kcal/mol, sigma = 2.05 A (zero beyond 2.30 A), evaluated in FP64 by
+the library's own kernels from a spatial hash of cells (it is not part of the
+FMM path); kicks, drifts and the kinetic energy are library kernels too.
 Even so, undamped point dipoles with alpha up to 2.5 A^3 at 0.1 sites/A^3 are
 collectively near the catastrophe (largest eigenvalue of alpha^1/2 T alpha^1/2
 0.84 on the lattice) and a few fs of motion push them over it; the dynamics
@@ -27,6 +28,7 @@ while the finite-difference check uses them as they are.
 from __future__ import annotations
 
 import argparse
+import ctypes
 import json
 import time
 
@@ -38,158 +40,201 @@ KB = 0.0019872              # kcal / (mol K)
 
 
 class Repulsion:
-    """Purely repulsive wall between pairs closer than 2^(1/6) sigma (FP64)."""
+    """The purely repulsive wall between pairs closer than 2^(1/6) sigma, and
+    the kicks, drifts and kinetic energy of the integrators, in the library's
+    CUDA kernels (FP64; fmm_wall_forces, fmm_md_kick, fmm_md_drift,
+    fmm_md_kinetic).  Scratch for up to `capacity` sites, grown on demand; the
+    kernels run on the stream current at creation."""
 
-    def __init__(self, eps=5.0, sigma=2.05):
-        self.eps, self.sigma = float(eps), float(sigma)
-        self.rc = 2.0 ** (1.0 / 6.0) * self.sigma
-
-    def __call__(self, x):
+    def __init__(self, eps=5.0, sigma=2.05, capacity=0, stream=None):
         import torch
 
-        n = x.shape[0]
-        rc = self.rc
-        lo = x.min(0).values - 1e-6
-        cell = torch.floor((x - lo) / rc).long()
-        dims = cell.max(0).values + 3  # one empty layer of cells on each side
-        cell = cell + 1
-        key = cell[:, 0] + dims[0] * (cell[:, 1] + dims[1] * cell[:, 2])
-        order = torch.argsort(key)
-        skey = key[order]
-        ncell = int(dims[0] * dims[1] * dims[2])
-        count = torch.bincount(skey, minlength=ncell)
-        start = torch.cumsum(count, 0) - count
-        kmax = int(count.max())
-        # table[c, k] = k-th site of cell c, -1 past its count
-        table = torch.full((ncell, kmax), -1, dtype=torch.long, device=x.device)
-        rank = torch.arange(n, device=x.device) - start[skey]
-        table[skey, rank] = order
-        U = torch.zeros((), dtype=torch.float64, device=x.device)
-        F = torch.zeros_like(x)
-        s6 = self.sigma ** 6
-        me = torch.arange(n, device=x.device)[:, None]
-        for dz in (-1, 0, 1):
-            for dy in (-1, 0, 1):
-                for dx in (-1, 0, 1):
-                    nk = key + dx + dims[0] * (dy + dims[1] * dz)
-                    js = table[nk]                                   # [n, kmax]
-                    jj = js.clamp(min=0)
-                    r = x[:, None, :] - x[jj]                        # [n, kmax, 3]
-                    r2 = (r * r).sum(-1)
-                    valid = (js >= 0) & (jj != me) & (r2 < rc * rc)
-                    r2 = torch.where(valid, r2, torch.ones_like(r2))
-                    t6 = s6 * r2 ** -3                               # (sigma / r)^6
-                    e = torch.where(valid, 4.0 * self.eps * (t6 * t6 - t6) + self.eps, torch.zeros_like(r2))
-                    U = U + 0.5 * e.sum()
-                    fmag = torch.where(valid, 4.0 * self.eps * (12.0 * t6 * t6 - 6.0 * t6) / r2, torch.zeros_like(r2))
-                    F = F + (fmag[..., None] * r).sum(1)
-        return float(U), F
+        from . import _lib
 
+        self.lib = _lib.load()
+        self.eps, self.sigma = float(eps), float(sigma)
+        self.rc = 2.0 ** (1.0 / 6.0) * self.sigma
+        self.stream = stream if stream is not None else torch.cuda.current_stream().cuda_stream
+        self.h, self.cap = None, 0
+        if capacity > 0:
+            self._reserve(capacity)
 
-def respa(x, v, acc_slow, acc_fast, slow, fast, dt, inner):
-    """One outer step of the reversible multiple-time-step integrator (r-RESPA):
-    a half kick of the slow acceleration over the outer step inner * dt,
-    `inner` velocity-Verlet steps of dt under the fast acceleration, and the
-    closing slow half kick. slow(x) and fast(x) return accelerations; the
-    accelerations at the current x are passed in and the new ones returned:
-    (x, v, acc_slow, acc_fast). With inner = 1 this is velocity Verlet under
-    the sum of the two."""
-    h = 0.5 * inner * dt
-    v = v + h * acc_slow
-    for _ in range(inner):
-        v = v + 0.5 * dt * acc_fast
-        x = x + dt * v
-        acc_fast = fast(x)
-        v = v + 0.5 * dt * acc_fast
-    acc_slow = slow(x)
-    v = v + h * acc_slow
-    return x, v, acc_slow, acc_fast
+    def _reserve(self, n):
+        from . import _lib
+
+        if self.h is not None and n <= self.cap:
+            return
+        self.close()
+        h = ctypes.c_void_p()
+        _lib.check(self.lib.fmm_wall_create(ctypes.byref(h), max(int(n), 1), ctypes.c_void_p(self.stream)),
+                   "fmm_wall_create")
+        self.h, self.cap = h, max(int(n), 1)
+
+    @staticmethod
+    def _ptr(t):
+        return ctypes.c_void_p(t.data_ptr())
+
+    @staticmethod
+    def _check_f8(*ts):
+        import torch
+
+        for t in ts:
+            if t.dtype != torch.float64 or not t.is_cuda or not t.is_contiguous():
+                raise ValueError("dynamics arrays must be contiguous float64 CUDA tensors")
+
+    def __call__(self, x):
+        """(U, F): U a 0-d device tensor (kcal/mol), F = -dU/dx (n x 3)."""
+        import torch
+
+        from . import _lib
+
+        x = torch.as_tensor(x, dtype=torch.float64, device="cuda").contiguous()
+        n = int(x.shape[0])
+        self._reserve(n)
+        U = torch.empty((), dtype=torch.float64, device="cuda")
+        F = torch.empty_like(x)
+        _lib.check(self.lib.fmm_wall_forces(self.h, self._ptr(x), n, self.eps, self.sigma, self._ptr(U),
+                                            self._ptr(F)), "fmm_wall_forces")
+        return U, F
+
+    wall = __call__
+
+    def kick(self, v, F, m, coef):
+        """v += coef * F / m, in place."""
+        from . import _lib
+
+        self._check_f8(v, F, m)
+        _lib.check(self.lib.fmm_md_kick(self._ptr(v), self._ptr(F), self._ptr(m), float(coef), int(v.shape[0]),
+                                        ctypes.c_void_p(self.stream)), "fmm_md_kick")
+
+    def drift(self, x, v, dt):
+        """x += dt * v, in place."""
+        from . import _lib
+
+        self._check_f8(x, v)
+        _lib.check(self.lib.fmm_md_drift(self._ptr(x), self._ptr(v), float(dt), int(x.shape[0]),
+                                         ctypes.c_void_p(self.stream)), "fmm_md_drift")
+
+    def kinetic(self, v, m, scale):
+        """scale * sum 1/2 m |v|^2 as a 0-d device tensor."""
+        import torch
+
+        from . import _lib
+
+        self._check_f8(v, m)
+        self._reserve(int(v.shape[0]))
+        out = torch.empty((), dtype=torch.float64, device="cuda")
+        _lib.check(self.lib.fmm_md_kinetic(self.h, self._ptr(v), self._ptr(m), int(v.shape[0]), float(scale),
+                                           self._ptr(out)), "fmm_md_kinetic")
+        return out
+
+    def close(self):
+        if self.h is not None:
+            self.lib.fmm_wall_destroy(self.h)
+            self.h, self.cap = None, 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # pragma: no cover
+            pass
 
 
 class Dynamics:
-    """Velocity Verlet with FMM electrostatics + polarization and the wall;
-    with inner > 1 the multiple-time-step form (the FMM forces every inner
-    steps, the wall every step)."""
+    """Molecular dynamics on FMM electrostatics + polarization (the slow force)
+    and the wall (the fast force).  A step is velocity Verlet (inner = 1), or
+    one outer step of the reversible multiple-time-step integrator (r-RESPA,
+    Sec. IV.B runs the long-range forces on a longer step): a half kick of the
+    FMM force over the outer step inner * dt, `inner` velocity-Verlet steps of
+    dt under the wall, and the closing FMM half kick.  Velocity Verlet applies
+    its kicks force by force in the order the multiple-time-step form does
+    (opening: FMM then wall; closing: wall then FMM), so that one inner step
+    gives the same bits as velocity Verlet.  `ops` provides wall(x),
+    kick(v, F, m, coef), drift(x, v, dt) and kinetic(v, m, scale): by default
+    the library's CUDA kernels (Repulsion)."""
 
-    def __init__(self, pos, q, alpha, masses, p=6, depth=5, mode="fp64", tol=1e-8, repulsion=None):
+    def __init__(self, pos, q, alpha, masses, p=6, depth=5, mode="fp64", tol=1e-8, ops=None):
         import torch
 
         from . import PolFMM
 
-        self.x = torch.as_tensor(pos, dtype=torch.float64, device="cuda").clone()
+        self.x = torch.as_tensor(pos, dtype=torch.float64, device="cuda").clone().contiguous()
         self.q = torch.as_tensor(q, dtype=torch.float64, device="cuda")
         self.alpha = torch.as_tensor(alpha, dtype=torch.float64, device="cuda")
-        self.m = torch.as_tensor(masses, dtype=torch.float64, device="cuda")
+        self.m = torch.as_tensor(masses, dtype=torch.float64, device="cuda").contiguous()
         self.tol = tol
-        self.rep = repulsion or Repulsion()
+        self.ops = ops or Repulsion(capacity=self.x.shape[0])
         self.fmm = PolFMM(self.x, self.q, self.alpha, p=p, depth=depth, mode=mode, coulomb_k=COULOMB,
                           max_iter=500)
         self.iterations = []
-        self.U, self.F = self._forces(first=True)
+        self.start()
 
-    def _forces(self, first=False):
-        if not first:
-            self.fmm.update_positions(self.x)  # keeps the dipoles as the start of the next solve
-        info = self.fmm.solve(self.tol)
-        self.iterations.append(info["iterations"])
-        out = self.fmm.energy_forces(forces=True, dq=False, dalpha=False)
-        ur, fr = self.rep(self.x)
-        return out["U"] + ur, out["F"] + fr
+    def start(self):
+        """Forces at the current positions (the first step's opening kicks use them)."""
+        self.Us, self.Fs = self._slow(update=False)
+        self.Uw, self.Fw = self.ops.wall(self.x)
 
-    def kinetic(self, v):
-        return float(0.5 * (self.m[:, None] * v * v).sum() / ACC)
-
-    def _slow(self):
-        """FMM electrostatics and polarization at self.x: (U, F)."""
-        self.fmm.update_positions(self.x)
+    def _slow(self, update=True):
+        """FMM electrostatics and polarization at self.x: (U, F); the solve starts
+        from the previous dipoles."""
+        if update:
+            self.fmm.update_positions(self.x)
         info = self.fmm.solve(self.tol)
         self.iterations.append(info["iterations"])
         out = self.fmm.energy_forces(forces=True, dq=False, dalpha=False)
         return out["U"], out["F"]
 
-    def run(self, v, steps, dt=1.0, inner=1):
+    def kinetic(self, v):
+        return float(self.ops.kinetic(v, self.m, 1.0 / ACC))
+
+    def total(self, v):
+        """Kinetic + FMM + wall energy (kcal/mol)."""
+        return self.kinetic(v) + float(self.Us) + float(self.Uw)
+
+    def _verlet_step(self, v, dt):
+        c = 0.5 * dt * ACC
+        self.ops.kick(v, self.Fs, self.m, c)
+        self.ops.kick(v, self.Fw, self.m, c)
+        self.ops.drift(self.x, v, dt)
+        self.Uw, self.Fw = self.ops.wall(self.x)
+        self.Us, self.Fs = self._slow()
+        self.ops.kick(v, self.Fw, self.m, c)
+        self.ops.kick(v, self.Fs, self.m, c)
+
+    def _respa_step(self, v, dt, inner):
+        c_out = 0.5 * inner * dt * ACC
+        c = 0.5 * dt * ACC
+        self.ops.kick(v, self.Fs, self.m, c_out)
+        for _ in range(inner):
+            self.ops.kick(v, self.Fw, self.m, c)
+            self.ops.drift(self.x, v, dt)
+            self.Uw, self.Fw = self.ops.wall(self.x)
+            self.ops.kick(v, self.Fw, self.m, c)
+        self.Us, self.Fs = self._slow()
+        self.ops.kick(v, self.Fs, self.m, c_out)
+
+    def run(self, v, steps, dt=1.0, inner=1, multistep=None):
         """Returns the total energy before and after each step (kcal/mol) and the
-        final velocities. With inner > 1 a step is one outer step of inner * dt:
-        the wall is integrated at dt and the FMM forces at inner * dt (r-RESPA)."""
-        if inner > 1:
-            return self._run_respa(v, steps, dt, inner)
-        H = [self.kinetic(v) + self.U]
-        a = self.F / self.m[:, None] * ACC
+        final velocities (a new tensor; v itself is not changed).  A step is
+        velocity Verlet at dt when inner == 1 (unless multistep=True), else one
+        multiple-time-step outer step of inner * dt."""
+        import torch
+
+        multistep = inner > 1 if multistep is None else bool(multistep)
+        v = torch.as_tensor(v, dtype=torch.float64, device=self.x.device).clone().contiguous()
+        H = [self.total(v)]
         for _ in range(steps):
-            v = v + 0.5 * dt * a
-            self.x = self.x + dt * v
-            self.U, self.F = self._forces()
-            a = self.F / self.m[:, None] * ACC
-            v = v + 0.5 * dt * a
-            H.append(self.kinetic(v) + self.U)
-        return np.array(H), v
-
-    def _run_respa(self, v, steps, dt, inner):
-        inv_m = ACC / self.m[:, None]
-        ur, fr = self.rep(self.x)
-        us, fs = self.U - ur, self.F - fr  # the first forces hold both parts
-        state = {"ur": ur, "us": us}
-
-        def fast(x):
-            state["ur"], f = self.rep(x)
-            return f * inv_m
-
-        def slow(x):
-            self.x = x
-            state["us"], f = self._slow()
-            return f * inv_m
-
-        H = [self.kinetic(v) + us + ur]
-        a_s, a_f = fs * inv_m, fr * inv_m
-        for _ in range(steps):
-            self.x, v, a_s, a_f = respa(self.x, v, a_s, a_f, slow, fast, dt, inner)
-            H.append(self.kinetic(v) + state["us"] + state["ur"])
-        self.U = state["us"] + state["ur"]
-        self.F = (a_s + a_f) / inv_m
+            if multistep:
+                self._respa_step(v, dt, inner)
+            else:
+                self._verlet_step(v, dt)
+            H.append(self.total(v))
         return np.array(H), v
 
     def close(self):
         self.fmm.close()
+        if hasattr(self.ops, "close"):
+            self.ops.close()
 
 
 def maxwell_velocities(masses, temperature, seed):
