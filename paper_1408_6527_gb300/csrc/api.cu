@@ -383,6 +383,14 @@ int allocate(polfmm_ctx* c) {
     c->leaf_items_cap = (int)std::min<int64_t>((int64_t)c->lv[c->depth].cap + n / kLeafTargetsMin + 1, 2 * n + 1);
     c->leaf_items = A.get<int2>(c->leaf_items_cap);
     c->leaf_nitems = A.get<int>(4);
+    if (c->mixed) {
+        // sum over leaves of ceil(count / 2) <= (n + leaves) / 2 <= n records
+        c->near_pairs = A.get<float>(12 * (size_t)n);
+        c->near_pbase = A.get<int>(c->lv[c->depth].cap + 1);
+        c->near_slot = A.get<int>(n);
+        c->near_items = A.get<NearItem>(2 * (size_t)c->leaf_items_cap);
+        c->near_nitems = A.get<int>(4);
+    }
     if (!A.ok) return POLFMM_ERR_OUT_OF_MEMORY;
     if (host_alloc(reinterpret_cast<void**>(&c->h_scal), sizeof(double) * (S_COUNT + 8)) != cudaSuccess ||
         host_alloc(reinterpret_cast<void**>(&c->h_counts), sizeof(int) * (kMaxDepth + 1) * 9) != cudaSuccess ||
@@ -424,6 +432,10 @@ int read_err(polfmm_ctx* c) {
     if (h[0] & 2) return POLFMM_ERR_COINCIDENT;
     if (h[0] & 4) {
         snprintf(g_last_error, sizeof(g_last_error), "a bounded wait of the tensor-core M2L kernel timed out");
+        return POLFMM_ERR_CUDA;
+    }
+    if (h[0] & 8) {
+        snprintf(g_last_error, sizeof(g_last_error), "a bounded wait of the near-field kernel timed out");
         return POLFMM_ERR_CUDA;
     }
     return POLFMM_OK;
@@ -515,6 +527,7 @@ int rebuild(polfmm_ctx* c) {
     if (c->qE_s) gather_sites(c, c->in_buf + 8 * n, c->qE_s, 1);
     exclusion_inv_perm(c);
     pack_positions(c);
+    if ((rc = near_tables(c)) != POLFMM_OK) return rc;
     static_passes(c);
     c->pcg_graph_dirty = true;  // launch sizes of the solver iteration changed
     c->loop_dirty = true;

@@ -837,6 +837,292 @@ __global__ void __launch_bounds__(kLeafThreads) leaf_kernel(
     }
 }
 
+// ---------------------------------------------------------------------------
+// FP32 near field of the dipole solve: E_i = sum_j [3 (mu_j.r) r / r^5 - mu_j / r^3]
+// over the sites j != i of the 27 adjacent leaves (Sec. II.A, the field of the
+// induced dipoles; the far field is added after the multipole passes).
+//
+// The sources are pair records in global memory (near_pairs: positions
+// relative to their own leaf centre, written once per tree; dipoles, written
+// once per pass), so that a leaf's sources are one contiguous range.  Each
+// work item (a leaf and up to kNearTargets of its sites) has a 240-byte record
+// with the 27 ranges of its adjacent leaves, its own leaf first.
+//
+// One block per item.  Staging: thread t copies records t, t + 256, ... of
+// the item's concatenated ranges (three 16-byte loads and stores each),
+// adding the neighbour leaf's offset to the positions.  Thread (w, s) owns targets 2w and 2w + 1 and every
+// slices-th record: four pairs per step in packed f32x2 arithmetic, the three
+// 16-byte loads of a record serving both targets; only the own leaf's
+// records, which come first, test for the self pair.  The slices are added in
+// a fixed order.
+// ---------------------------------------------------------------------------
+constexpr int kNearThreads = 256;
+constexpr int kNearBlocksPerSM = 3;
+constexpr int kNearPairCap = 1024;  // pair records per chunk (2,048 sources, 48 KB)
+constexpr int kNearTargets = 64;    // targets per near-field item
+static_assert(kLeafTargetsF32 <= 2 * kNearTargets, "a leaf item makes at most two near-field items");
+
+struct NearSmem {
+    float4 pairs[kNearPairCap * 3];
+    float part[3][2 * kNearThreads];
+    float shift[27][3];
+    int segx[28];    // item-relative first record of segment r; segx[27] = records of the item
+    int segsrc[27];  // first pair record of segment r in near_pairs
+    int nt, s0t;
+};
+static_assert(kNearBlocksPerSM * (sizeof(NearSmem) + 1024) <= 228 * 1024, "three blocks fit on one SM");
+
+constexpr size_t near_dipole_smem_bytes() { return sizeof(NearSmem); }
+
+// E += r^-3 [nu - 3 (nu.r) r / r^2] for the two sources of record pp, nu = -mu
+// the stored (negated) dipole: the field 3 (mu.r) r / r^5 - mu / r^3 with one
+// accumulator per component
+template <bool SELF>
+__device__ __forceinline__ void near_step(const ulonglong2* __restrict__ sp, int pp, const F2 (&X)[2][3],
+                                          F2 (&E)[2][3]) {
+    const ulonglong2 A = sp[3 * pp], B = sp[3 * pp + 1], C = sp[3 * pp + 2];
+    const F2 M3 = f2_pack(-3.f, -3.f);
+#pragma unroll
+    for (int u = 0; u < 2; u++) {
+        const F2 rx = f2_sub(X[u][0], A.x), ry = f2_sub(X[u][1], A.y), rz = f2_sub(X[u][2], B.x);
+        const F2 r2 = f2_fma(rz, rz, f2_fma(ry, ry, f2_mul(rx, rx)));
+        float r2a, r2b;
+        f2_unpack(r2, r2a, r2b);
+        const F2 ri = SELF ? f2_pack(rsqrt_pos(r2a), rsqrt_pos(r2b)) : f2_pack(rsqrtf(r2a), rsqrtf(r2b));
+        const F2 ri2 = f2_mul(ri, ri);
+        const F2 ri3 = f2_mul(ri, ri2);
+        const F2 nr = f2_fma(C.y, rz, f2_fma(C.x, ry, f2_mul(B.y, rx)));  // nu.r
+        const F2 a = f2_mul(nr, f2_mul(ri2, M3));                          // -3 (nu.r) / r^2
+        E[u][0] = f2_fma(ri3, f2_fma(a, rx, B.y), E[u][0]);
+        E[u][1] = f2_fma(ri3, f2_fma(a, ry, C.x), E[u][1]);
+        E[u][2] = f2_fma(ri3, f2_fma(a, rz, C.y), E[u][2]);
+    }
+}
+
+__global__ void __launch_bounds__(kNearThreads, kNearBlocksPerSM) near_dipole_f32_kernel(
+    const NearItem* __restrict__ items, const int* __restrict__ nitems, const float4* __restrict__ P,
+    const Q4<float>* __restrict__ srcA, float h, double* __restrict__ out_E) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    NearSmem& S = *reinterpret_cast<NearSmem*>(smem_raw);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if ((int)blockIdx.x >= *nitems) return;
+    const NearItem& R = items[blockIdx.x];
+    if (tid < 27) {
+        // segment r: the own leaf (offset 0), then the other 26 in a fixed order
+        const int o = tid == 0 ? 13 : (tid <= 13 ? tid - 1 : tid);
+        S.shift[tid][0] = float(o % 3 - 1) * h;
+        S.shift[tid][1] = float((o / 3) % 3 - 1) * h;
+        S.shift[tid][2] = float(o / 9 - 1) * h;
+    }
+    if (warp == 0) {
+        const int2 e = lane < 27 ? R.seg[lane] : make_int2(0, 0);
+        int incl = e.y;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        if (lane < 27) {
+            S.segx[lane] = incl - e.y;
+            S.segsrc[lane] = e.x;
+        }
+        if (lane == 26) S.segx[27] = incl;
+        if (lane == 0) {
+            S.nt = R.nt;
+            S.s0t = R.s0 + R.t_lo;
+        }
+    }
+    __syncthreads();
+    const int nt = S.nt, s0t = S.s0t, total = S.segx[27];
+    const int ntp = (nt + 1) >> 1;
+    const int slices = kNearThreads / ntp;
+    const int w = tid % ntp, s = tid / ntp;
+    const bool active = s < slices;
+    F2 X[2][3];
+#pragma unroll
+    for (int v = 0; v < 2; v++) {
+        // a missing second target repeats the first (its sums are dropped)
+        const Q4<float> t = srcA[s0t + min(2 * w + v, nt - 1)];
+        X[v][0] = f2_pack(t.x, t.x);
+        X[v][1] = f2_pack(t.y, t.y);
+        X[v][2] = f2_pack(t.z, t.z);
+    }
+    F2 E[2][3];
+#pragma unroll
+    for (int v = 0; v < 2; v++)
+#pragma unroll
+        for (int k = 0; k < 3; k++) E[v][k] = 0ull;
+    const ulonglong2* sp = reinterpret_cast<const ulonglong2*>(S.pairs);
+    for (int lo = 0; lo < total; lo += kNearPairCap) {
+        const int m = min(total - lo, kNearPairCap);
+        if (lo > 0) __syncthreads();  // the previous chunk is consumed
+        // record k of the chunk: segment r with segx[r] <= lo + k < segx[r + 1]
+        // (a search instead of a loop over segments, so that every thread
+        // issues its loads at once)
+        for (int k = tid; k < m; k += kNearThreads) {
+            const int g = lo + k;
+            int r = 0;
+#pragma unroll
+            for (int step = 16; step > 0; step >>= 1)
+                if (r + step < 27 && S.segx[r + step] <= g) r += step;
+            const float4* src = P + 3 * ((int64_t)S.segsrc[r] + (g - S.segx[r]));
+            float4 p0 = src[0], p1 = src[1];
+            const float4 p2 = src[2];
+            const float sx = S.shift[r][0], sy = S.shift[r][1], sz = S.shift[r][2];
+            p0.x += sx;
+            p0.y += sx;
+            p0.z += sy;
+            p0.w += sy;
+            p1.x += sz;
+            p1.y += sz;
+            float4* d = &S.pairs[3 * k];
+            d[0] = p0;
+            d[1] = p1;
+            d[2] = p2;
+        }
+        __syncthreads();
+        if (active) {
+            const int own_end = min(max(S.segx[1] - lo, 0), m);
+            int pp = s;
+            for (; pp < own_end; pp += slices) near_step<true>(sp, pp, X, E);
+            for (; pp < m; pp += slices) near_step<false>(sp, pp, X, E);
+        }
+    }
+    // fixed-order reduction over slices: target t, slice s at part[.][s * 2 ntp + t]
+    if (active) {
+#pragma unroll
+        for (int v = 0; v < 2; v++)
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+                float e0, e1;
+                f2_unpack(E[v][k], e0, e1);
+                S.part[k][s * 2 * ntp + 2 * w + v] = e0 + e1;
+            }
+    }
+    __syncthreads();
+    if (tid < nt) {
+        const int64_t ii = s0t + tid;
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            float acc = 0.f;
+            for (int q = 0; q < slices; q++) acc += S.part[k][q * 2 * ntp + tid];
+            out_E[3 * ii + k] = (double)acc;
+        }
+    }
+}
+
+// per tree (MIXED): records of ceil(count / 2) per leaf, first record of each leaf
+__global__ void near_pair_count_kernel(int nleaf, const int* __restrict__ lcount, int* __restrict__ npair) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < nleaf) npair[b] = (lcount[b] + 1) >> 1;
+}
+
+// per tree: the positions of the pair records (dipoles zero until a pass packs
+// them), the far padding source of odd leaves, and the record slot of each site
+__global__ void near_records_kernel(int nleaf, const int* __restrict__ lstart, const int* __restrict__ lcount,
+                                    const int* __restrict__ pbase, const Q4<float>* __restrict__ srcA,
+                                    float* __restrict__ P, int* __restrict__ slot) {
+    const int b = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+    if (b >= nleaf) return;
+    const int s0 = lstart[b], cnt = lcount[b], np = (cnt + 1) >> 1, pb = pbase[b];
+    for (int k = lane; k < np; k += 32) {
+        const int i0 = s0 + 2 * k;
+        const bool two = 2 * k + 1 < cnt;
+        const Q4<float> a = srcA[i0];
+        const Q4<float> c = two ? srcA[i0 + 1] : Q4<float>{kFarPad, kFarPad, kFarPad, 0.f};
+        float4* q = reinterpret_cast<float4*>(P + 12 * (int64_t)(pb + k));
+        q[0] = make_float4(a.x, c.x, a.y, c.y);
+        q[1] = make_float4(a.z, c.z, 0.f, 0.f);
+        q[2] = make_float4(0.f, 0.f, 0.f, 0.f);
+        slot[i0] = 2 * (pb + k);
+        if (two) slot[i0 + 1] = 2 * (pb + k) + 1;
+    }
+}
+
+// per tree: near-field items per leaf item (ceil(targets / 32)), 0 past the list
+__global__ void near_item_count_kernel(const int2* __restrict__ litems, const int* __restrict__ nitems, int bound,
+                                       const int* __restrict__ lcount, int* __restrict__ cnt) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= bound) return;
+    int c = 0;
+    if (i < *nitems) {
+        const int nt = min(lcount[litems[i].x] - litems[i].y, kLeafTargetsF32);
+        c = (nt + kNearTargets - 1) / kNearTargets;
+    }
+    cnt[i] = c;
+}
+
+// per tree: the work-item records, in the order of the leaf items (heaviest
+// first): own leaf first, then the other 26 adjacent leaves in a fixed order;
+// absent leaves are empty ranges
+__global__ void near_items_kernel(const int2* __restrict__ litems, const int* __restrict__ nitems,
+                                  const int* __restrict__ first, int depth, const int* __restrict__ lkey,
+                                  const int* __restrict__ lmap, const int* __restrict__ lstart,
+                                  const int* __restrict__ lcount, const int* __restrict__ pbase,
+                                  NearItem* __restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= *nitems) return;
+    const int b = litems[i].x, t0 = litems[i].y;
+    const int nt_all = min(lcount[b] - t0, kLeafTargetsF32);
+    int2 seg[27];
+    const uint32_t key = (uint32_t)lkey[b];
+    const int nside = 1 << depth;
+    const int bx = (int)compact3(key), by = (int)compact3(key >> 1), bz = (int)compact3(key >> 2);
+    for (int r = 0; r < 27; r++) {
+        const int o = r == 0 ? 13 : (r <= 13 ? r - 1 : r);
+        const int ax = bx + o % 3 - 1, ay = by + (o / 3) % 3 - 1, az = bz + o / 9 - 1;
+        int ns = -1;
+        if (ax >= 0 && ay >= 0 && az >= 0 && ax < nside && ay < nside && az < nside) ns = lmap[morton3(ax, ay, az)];
+        seg[r] = ns >= 0 ? make_int2(pbase[ns], (lcount[ns] + 1) >> 1) : make_int2(0, 0);
+    }
+    int o = first[i];
+    for (int t = 0; t < nt_all; t += kNearTargets, o++) {
+        NearItem& R = out[o];
+        R.b = b;
+        R.s0 = lstart[b];
+        R.t_lo = t0 + t;
+        R.nt = min(nt_all - t, kNearTargets);
+        R.pad[0] = R.pad[1] = 0;
+        for (int r = 0; r < 27; r++) R.seg[r] = seg[r];
+    }
+}
+
+// per pass: the dipoles into the pair records (negated: the kernel's form)
+__global__ void near_pack_mu_kernel(int64_t n, const double* __restrict__ mu, const int* __restrict__ slot,
+                                    float* __restrict__ P) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int sl = slot[i];
+    float* q = P + 12 * (int64_t)(sl >> 1) + (sl & 1);
+    q[6] = -(float)mu[3 * i];
+    q[8] = -(float)mu[3 * i + 1];
+    q[10] = -(float)mu[3 * i + 2];
+}
+
+int near_tables(polfmm_ctx* c) {
+    if (!c->mixed) return POLFMM_OK;
+    Level& L = c->lv[c->depth];
+    const int nl = L.nbox;
+    {
+        LaunchScope ls(c, F_TREE);
+        near_pair_count_kernel<<<grid_for(nl, 256), 256, 0, c->stream>>>(nl, c->lcount, c->flags);
+    }
+    scan_exclusive(c, c->flags, c->near_pbase, nl, nullptr);
+    LaunchScope ls(c, F_TREE);
+    near_records_kernel<<<grid_for((int64_t)nl * 32, 256), 256, 0, c->stream>>>(
+        nl, c->lstart, c->lcount, c->near_pbase, reinterpret_cast<const Q4<float>*>(c->srcA), c->near_pairs,
+        c->near_slot);
+    // every leaf item has a target of its own: at most n items
+    const int bound = (int)std::min<int64_t>(c->leaf_items_grid, c->n);
+    near_item_count_kernel<<<grid_for(bound, 256), 256, 0, c->stream>>>(c->leaf_items, c->leaf_nitems, bound,
+                                                                         c->lcount, c->flags);
+    scan_exclusive(c, c->flags, c->val_a, bound, c->near_nitems);
+    near_items_kernel<<<grid_for(bound, 128), 128, 0, c->stream>>>(c->leaf_items, c->leaf_nitems, c->val_a,
+                                                                   c->depth, L.key, L.map, c->lstart, c->lcount,
+                                                                   c->near_pbase, c->near_items);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? POLFMM_OK : cuda_fail(e, "near-field tables");
+}
+
 // far field of the solver pass, added to the near field already in out_E:
 // E += -(1/h^2) sum_{|n| <= p-1} u^n/n! f_{n+e_d}, u = (x - z) / h (Sec. II.B).
 // With pf.Ad set (PCG), the kernel also forms Ad = d/alpha - E of its sites
@@ -1083,6 +1369,20 @@ static void launch_leaf(polfmm_ctx* c, int mode, const double* mu_sorted, double
     const Tables& T = c->tab;
     Q4<R>* A = reinterpret_cast<Q4<R>*>(c->srcA);
     Q4<R>* B = reinterpret_cast<Q4<R>*>(c->srcB);
+    if (mode == LEAF_DIPOLE_E && sizeof(R) == 4 && !far) {
+        // FP32 dipole near field from the pair records
+        if (!mu_packed) {
+            LaunchScope ls(c, F_P2M);
+            near_pack_mu_kernel<<<grid_for(c->n, 256), 256, 0, st>>>(c->n, mu_sorted, c->near_slot, c->near_pairs);
+        }
+        LaunchScope ls(c, F_LEAF_DIPOLE);
+        // one block per item; at most two items per leaf item (their count is on the device)
+        const int grid = 2 * c->leaf_items_grid;
+        near_dipole_f32_kernel<<<grid, kNearThreads, near_dipole_smem_bytes(), st>>>(
+            c->near_items, c->near_nitems, reinterpret_cast<const float4*>(c->near_pairs),
+            reinterpret_cast<const Q4<float>*>(c->srcA), float(h), E);
+        return;
+    }
     if (mode != LEAF_CHARGE_PHI_E && !mu_packed) {
         LaunchScope ls(c, F_P2M);
         pack_dipoles_kernel<R><<<grid_for(c->n, 256), 256, 0, st>>>(c->n, mu_sorted, B);
@@ -1235,6 +1535,9 @@ int fmm_ops_init_attributes(polfmm_ctx*) {
     LEAF_ATTR(double, LEAF_CHARGE_PHI_E)
     LEAF_ATTR(double, LEAF_FULL)
 #undef LEAF_ATTR
+    if (cudaFuncSetAttribute(near_dipole_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)near_dipole_smem_bytes()) != cudaSuccess)
+        return POLFMM_ERR_CUDA;
     return POLFMM_OK;
 }
 

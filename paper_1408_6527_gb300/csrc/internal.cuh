@@ -72,6 +72,17 @@ struct Tables {
 };
 
 // one tile of same-level, same-octant-class target boxes for the M2L kernel
+// FP32 near field of the dipole solve, one work item: its leaf b, the leaf's
+// first sorted site s0, the item's first target t_lo (relative to s0) and its
+// target count, and the 27 source segments (first pair record, records) of
+// the adjacent leaves, the leaf itself first (240 bytes, one bulk copy)
+struct NearItem {
+    int b, s0, t_lo, nt;
+    int2 seg[27];
+    int pad[2];
+};
+static_assert(sizeof(NearItem) == 240, "NearItem is copied as 15 x 16 bytes");
+
 struct M2LTile {
     int level;
     int cls;
@@ -137,6 +148,15 @@ struct polfmm_ctx {
     int* leaf_order = nullptr;    // leaves by descending near-field work
     int2* leaf_items = nullptr;   // near-field blocks: (leaf, first target), heaviest leaves first
     int* leaf_nitems = nullptr;   // device count of leaf_items
+    // MIXED: sources of the dipole near field as pair records of 12 floats
+    // (x0 x1 y0 y1 | z0 z1 nx0 nx1 | ny0 ny1 nz0 nz1, nu = -mu), each leaf padded to an
+    // even count with a far, dipole-free source; positions once per tree,
+    // dipoles once per pass
+    float* near_pairs = nullptr;
+    int* near_pbase = nullptr;     // first pair record of each leaf
+    int* near_slot = nullptr;      // pair slot (2 record + half) of each sorted site
+    polfmm::NearItem* near_items = nullptr;  // up to 2 per leaf item (32 targets each)
+    int* near_nitems = nullptr;               // device count of near_items
     int leaf_items_cap = 0;       // capacity of leaf_items
     int leaf_items_grid = 0;      // launch bound of the current tree: leaves + n / leaf_targets + 1
     polfmm::Level lv[polfmm::kMaxDepth + 1];
@@ -257,6 +277,8 @@ bool fmm_pass(polfmm_ctx* c, int mode, bool use_q, const double* mu_sorted, doub
               double* G, bool mu_packed = false, bool pcg = false);
 int m2l_setup(polfmm_ctx* c);
 void pack_positions(polfmm_ctx* c);
+// MIXED: per-tree tables of the FP32 dipole near field (pair records, work items)
+int near_tables(polfmm_ctx* c);
 size_t source_record_bytes(bool mixed);
 
 // solver.cu

@@ -49,13 +49,24 @@ __device__ inline double sum_partials(const double* __restrict__ partial, int ro
 }
 
 // packed (mu_x, mu_y, mu_z, 0) record of site i for the near-field kernels
+// the near-field source copy of a dipole-like vector: FP64 (x, y, z, 0)
+// records per site; FP32 into the site's slot of the pair records
 template <typename R>
-__device__ inline void store_packed(void* base, int64_t i, double x, double y, double z) {
-    R* p = reinterpret_cast<R*>(base) + 4 * i;
-    p[0] = R(x);
-    p[1] = R(y);
-    p[2] = R(z);
-    p[3] = R(0);
+__device__ inline void store_packed(void* base, const int* __restrict__ slot, int64_t i, double x, double y,
+                                    double z) {
+    if constexpr (sizeof(R) == 4) {
+        const int sl = slot[i];
+        float* q = reinterpret_cast<float*>(base) + 12 * (int64_t)(sl >> 1) + (sl & 1);
+        q[6] = -(float)x;  // the pair records hold the negated dipole
+        q[8] = -(float)y;
+        q[10] = -(float)z;
+    } else {
+        R* p = reinterpret_cast<R*>(base) + 4 * i;
+        p[0] = R(x);
+        p[1] = R(y);
+        p[2] = R(z);
+        p[3] = R(0);
+    }
 }
 
 // single-block final reduction of nslot partial rows
@@ -232,7 +243,7 @@ __global__ void loop_setup_kernel(double* __restrict__ scal, double tol, double 
 // d = z + beta d, and its packed copy for the next near-field pass
 template <typename R>
 __global__ void pcg_direction_kernel(int64_t n, const double* __restrict__ scal, const double* __restrict__ z,
-                                     double* __restrict__ d, void* __restrict__ packed) {
+                                     double* __restrict__ d, void* __restrict__ packed, const int* __restrict__ slot) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
     const double beta = scal[S_BETA];
@@ -241,15 +252,16 @@ __global__ void pcg_direction_kernel(int64_t n, const double* __restrict__ scal,
         v[k] = z[3 * i + k] + beta * d[3 * i + k];
         d[3 * i + k] = v[k];
     }
-    store_packed<R>(packed, i, v[0], v[1], v[2]);
+    store_packed<R>(packed, slot, i, v[0], v[1], v[2]);
 }
 
 // packed copy of d after the PCG start (d = z)
 template <typename R>
-__global__ void pack_vec_kernel(int64_t n, const double* __restrict__ v, void* __restrict__ packed) {
+__global__ void pack_vec_kernel(int64_t n, const double* __restrict__ v, void* __restrict__ packed,
+                                const int* __restrict__ slot) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
-    store_packed<R>(packed, i, v[3 * i], v[3 * i + 1], v[3 * i + 2]);
+    store_packed<R>(packed, slot, i, v[3 * i], v[3 * i + 1], v[3 * i + 2]);
 }
 
 // Jacobi fixed point: r = E^q + T mu - mu/alpha (residual at the current mu),
@@ -435,9 +447,9 @@ void solver_init(polfmm_ctx* c, bool warm) {
     reduce(c, 3, S_RZ, S_RR, S_BB, 0, 2, F_SOLVER);
     LaunchScope ls(c, F_SOLVER);
     if (c->mixed)
-        pack_vec_kernel<float><<<grid_for(c->n, 256), 256, 0, c->stream>>>(c->n, c->d, c->srcB);
+        pack_vec_kernel<float><<<grid_for(c->n, 256), 256, 0, c->stream>>>(c->n, c->d, c->near_pairs, c->near_slot);
     else
-        pack_vec_kernel<double><<<grid_for(c->n, 256), 256, 0, c->stream>>>(c->n, c->d, c->srcB);
+        pack_vec_kernel<double><<<grid_for(c->n, 256), 256, 0, c->stream>>>(c->n, c->d, c->srcB, nullptr);
 }
 
 // one PCG iteration: T d by the FMM (d already packed for the near field;
@@ -459,10 +471,10 @@ void solver_pcg_step(polfmm_ctx* c) {
         LaunchScope ls(c, F_SOLVER);
         if (c->mixed)
             pcg_direction_kernel<float><<<grid_for(c->n, 256), 256, 0, c->stream>>>(c->n, c->scal, c->z, c->d,
-                                                                                    c->srcB);
+                                                                                    c->near_pairs, c->near_slot);
         else
             pcg_direction_kernel<double><<<grid_for(c->n, 256), 256, 0, c->stream>>>(c->n, c->scal, c->z, c->d,
-                                                                                     c->srcB);
+                                                                                     c->srcB, nullptr);
     }
 }
 
