@@ -858,7 +858,7 @@ __global__ void __launch_bounds__(kLeafThreads) leaf_kernel(
 // ---------------------------------------------------------------------------
 constexpr int kNearThreads = 256;
 constexpr int kNearBlocksPerSM = 3;
-constexpr int kNearPairCap = 1024;  // pair records per chunk (2,048 sources, 48 KB)
+constexpr int kNearPairCap = 512;  // pair records per chunk (1,024 sources, 24 KB)
 constexpr int kNearTargets = 64;    // targets per near-field item
 static_assert(kLeafTargetsF32 <= 2 * kNearTargets, "a leaf item makes at most two near-field items");
 
