@@ -57,6 +57,7 @@ def _load():
             cd = ctypes.c_double
             lib.orc_direct.argtypes = [i64, P, P, P, i64, P, P, P, P]
             lib.orc_fmm.argtypes = [i64, P, P, P, ci, ci, P, cd, P, P, P]
+            lib.orc_fmm_ex.argtypes = [i64, P, P, P, ci, ci, P, cd, P, P, P, ci]
             lib.orc_derivatives.argtypes = [ci, P, P]
             lib.orc_multi_indices.argtypes = [ci, P]
             lib.orc_p2m.argtypes = [ci, P, i64, P, P, P, P]
@@ -153,9 +154,12 @@ def leaf_cells(pos, depth, lo, side):
     return cells
 
 
-def fmm_fields(pos, q=None, mu=None, p=4, depth=3, root=None):
+def fmm_fields(pos, q=None, mu=None, p=4, depth=3, root=None, fp32_top=-1):
     """Phi, E, G at every site by the CPU FMM at order p on a uniform octree of
-    the given depth; root = (lo, side) or None for the default root cube."""
+    the given depth; root = (lo, side) or None for the default root cube.
+    fp32_top >= 2: the multipole shifts into levels 2..fp32_top and the local
+    shifts out of them in single precision (a measurement of what single
+    precision at the top of the tree costs); -1: all FP64."""
     pos = _f64(pos, (-1, 3))
     n = pos.shape[0]
     q = _f64(q)
@@ -165,8 +169,8 @@ def fmm_fields(pos, q=None, mu=None, p=4, depth=3, root=None):
     G = np.zeros((n, 6))
     lo = None if root is None else _f64(root[0])
     side = 0.0 if root is None else float(root[1])
-    _check(_load().orc_fmm(n, _ptr(pos), _ptr(q), _ptr(mu), int(p), int(depth), _ptr(lo), side,
-                           _ptr(phi), _ptr(E), _ptr(G)))
+    _check(_load().orc_fmm_ex(n, _ptr(pos), _ptr(q), _ptr(mu), int(p), int(depth), _ptr(lo), side,
+                              _ptr(phi), _ptr(E), _ptr(G), int(fp32_top)))
     return {"phi": phi, "E": E, "G": G}
 
 

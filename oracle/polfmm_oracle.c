@@ -22,6 +22,11 @@
  *                    parents adjacent", per-pair derivative evaluation, and
  *                    near-field direct sums over the 27 adjacent leaves
  *                    (Sec. II.B and Sec. III, Phi = Phi^direct + Phi^fmm).
+ *   orc_fmm_ex       orc_fmm with a measurement knob: the multipole shifts
+ *                    into levels 2..fp32_top and the local shifts out of
+ *                    them done in single precision (arithmetic and stored
+ *                    result), everything else in FP64; it measures what
+ *                    single precision at the top of the tree costs.
  *
  * Conventions: positions AoS (n x 3); the field gradient G = grad E is
  * stored as (xx, xy, xz, yy, yz, zz); Coulomb constant 1; r_ij = x_i - x_j.
@@ -214,6 +219,22 @@ static void m2m_accum(const orc_mi* t, const double s[3], const double* Min, dou
     }
 }
 
+/* m2m_accum in single precision: terms, sum and the stored result rounded to
+ * float (the measurement knob of orc_fmm_ex). */
+static void m2m_accum_f32(const orc_mi* t, const double s[3], const double* Min, double* Mout) {
+    for (int i = 0; i < t->ncoef; i++) {
+        const int* n = t->n[i];
+        float acc = 0.0f;
+        for (int kx = 0; kx <= n[0]; kx++)
+            for (int ky = 0; ky <= n[1]; ky++)
+                for (int kz = 0; kz <= n[2]; kz++) {
+                    int k[3] = {kx, ky, kz};
+                    acc += (float)(mi_pow(s, k) / mi_fact(k)) * (float)Min[mi_at(t, n[0] - kx, n[1] - ky, n[2] - kz)];
+                }
+        Mout[i] = (double)((float)Mout[i] + acc);
+    }
+}
+
 int orc_m2m(int p, const double s[3], const double* Min, double* Mout) {
     orc_mi t;
     if (p < 0 || p > ORC_MAXP || mi_init(&t, p)) return ORC_EINVAL;
@@ -264,6 +285,21 @@ static void l2l_accum(const orc_mi* t, const double s[3], const double* Fin, dou
             acc += mi_pow(s, k) / mi_fact(k) * Fin[mi_at(t, n[0] + k[0], n[1] + k[1], n[2] + k[2])];
         }
         Fout[i] += acc;
+    }
+}
+
+/* l2l_accum in single precision (the measurement knob of orc_fmm_ex). */
+static void l2l_accum_f32(const orc_mi* t, const double s[3], const double* Fin, double* Fout) {
+    for (int i = 0; i < t->ncoef; i++) {
+        const int* n = t->n[i];
+        int sn = n[0] + n[1] + n[2];
+        float acc = 0.0f;
+        for (int j = 0; j < t->ncoef; j++) {
+            const int* k = t->n[j];
+            if (k[0] + k[1] + k[2] > t->p - sn) continue;
+            acc += (float)(mi_pow(s, k) / mi_fact(k)) * (float)Fin[mi_at(t, n[0] + k[0], n[1] + k[1], n[2] + k[2])];
+        }
+        Fout[i] = (double)((float)Fout[i] + acc);
     }
 }
 
@@ -464,8 +500,8 @@ static inline int64_t lin3(int nside, int i, int j, int k) {
  * leaves interact directly.  Each multipole-to-local derivative tensor is
  * evaluated per pair by the recurrence above.
  */
-int orc_fmm(int64_t n, const double* x, const double* q, const double* mu, int p, int depth,
-            const double* root_lo, double root_side, double* phi, double* E, double* G) {
+int orc_fmm_ex(int64_t n, const double* x, const double* q, const double* mu, int p, int depth,
+               const double* root_lo, double root_side, double* phi, double* E, double* G, int fp32_top) {
     if (n < 1 || p < 1 || p > ORC_MAXP || depth < 1 || depth > 8) return ORC_EINVAL;
     orc_mi t;
     if (mi_init(&t, p)) return ORC_ENOMEM;
@@ -568,7 +604,10 @@ int orc_fmm(int64_t n, const double* x, const double* q, const double* mu, int p
                 double zc[3];
                 BOX_CENTRE(l + 1, cs, zc);
                 double s[3] = {zp[0] - zc[0], zp[1] - zc[1], zp[2] - zc[2]};
-                m2m_accum(&t, s, C->M + (int64_t)cs * nc, P->M + b * nc);
+                if (l <= fp32_top)
+                    m2m_accum_f32(&t, s, C->M + (int64_t)cs * nc, P->M + b * nc);
+                else
+                    m2m_accum(&t, s, C->M + (int64_t)cs * nc, P->M + b * nc);
             }
         }
     }
@@ -613,7 +652,10 @@ int orc_fmm(int64_t n, const double* x, const double* q, const double* mu, int p
             BOX_CENTRE(l, b, zc);
             BOX_CENTRE(l - 1, ps, zp);
             double s[3] = {zc[0] - zp[0], zc[1] - zp[1], zc[2] - zp[2]};
-            l2l_accum(&t, s, P->F + (int64_t)ps * nc, C->F + b * nc);
+            if (l - 1 <= fp32_top)
+                l2l_accum_f32(&t, s, P->F + (int64_t)ps * nc, C->F + b * nc);
+            else
+                l2l_accum(&t, s, P->F + (int64_t)ps * nc, C->F + b * nc);
         }
     }
     /* L2P + near field over the 27 adjacent leaves */
@@ -671,6 +713,11 @@ int orc_fmm(int64_t n, const double* x, const double* q, const double* mu, int p
     free(cells);
     mi_free(&t);
     return status;
+}
+
+int orc_fmm(int64_t n, const double* x, const double* q, const double* mu, int p, int depth,
+            const double* root_lo, double root_side, double* phi, double* E, double* G) {
+    return orc_fmm_ex(n, x, q, mu, p, depth, root_lo, root_side, phi, E, G, -1);
 }
 
 int orc_num_threads(void) {
