@@ -323,6 +323,7 @@ int allocate(polfmm_ctx* c) {
     c->pos_s = A.get<double>(3 * n);
     c->q_s = A.get<double>(n);
     c->alpha_s = A.get<double>(n);
+    c->inv_alpha_s = A.get<double>(n);
     c->perm = A.get<int>(n);
     c->key_s = A.get<uint32_t>(n);
     c->ploc = A.get<unsigned char>(3 * n * rsz);

@@ -1132,7 +1132,7 @@ constexpr int kL2PThreads = 128;
 constexpr int kPowStride = 3 * kMaxP + 1;  // odd: the per-thread rows hit distinct banks
 
 struct PcgFuse {
-    const double* alpha;
+    const double* inv_alpha;  // 1 / alpha, 0 where alpha = 0
     const double* d;
     double* Ad;
     double* partial;  // [nleaf]
@@ -1188,7 +1188,7 @@ __global__ void __launch_bounds__(kL2PThreads) l2p_field_add_kernel(
         const int64_t i = s0 + tid;
         for (int k = 0; k < 3; k++) pre[k] = out_E[3 * i + k];
         if (pf.Ad) {
-            pre[3] = pf.alpha[i];
+            pre[3] = pf.inv_alpha[i];
             for (int k = 0; k < 3; k++) pre[4 + k] = pf.d[3 * i + k];
         }
     }
@@ -1240,7 +1240,7 @@ __global__ void __launch_bounds__(kL2PThreads) l2p_field_add_kernel(
             if (tg > 0) {
                 for (int k = 0; k < 3; k++) pre[k] = out_E[3 * (int64_t)i + k];
                 if (pf.Ad) {
-                    pre[3] = pf.alpha[i];
+                    pre[3] = pf.inv_alpha[i];
                     for (int k = 0; k < 3; k++) pre[4 + k] = pf.d[3 * (int64_t)i + k];
                 }
             }
@@ -1250,10 +1250,10 @@ __global__ void __launch_bounds__(kL2PThreads) l2p_field_add_kernel(
             e[2] = pre[2] + (double)(e2 * s2);
             for (int k = 0; k < 3; k++) out_E[3 * (int64_t)i + k] = e[k];
             if (pf.Ad) {
-                const double a = pre[3];
+                const double ia = pre[3];
                 for (int k = 0; k < 3; k++) {
                     const double dk = pre[4 + k];
-                    const double v = a > 0.0 ? dk / a - e[k] : 0.0;
+                    const double v = ia > 0.0 ? dk * ia - e[k] : 0.0;
                     pf.Ad[3 * (int64_t)i + k] = v;
                     dot += dk * v;
                 }
@@ -1485,7 +1485,7 @@ static bool pass_impl(polfmm_ctx* c, int mode, bool use_q, const double* mu_sort
         const size_t smem = l2p_smem_bytes<R>(c->ld, d);
         PcgFuse pf{};
         if (pcg)
-            pf = PcgFuse{c->alpha_s, c->d,      c->Ad, c->leaf_partial,
+            pf = PcgFuse{c->inv_alpha_s, c->d,      c->Ad, c->leaf_partial,
                          c->scal,    c->ticket, c->capturing_loop ? c->loop_cond : 0};
         l2p_field_add_kernel<R><<<Lf.nbox, kL2PThreads, smem, c->stream>>>(
             Lf.nbox, c->lstart, c->lcount, reinterpret_cast<const Q4<R>*>(c->srcA), down_ptrs(c), c->ld, c->ncoef,

@@ -137,6 +137,7 @@ struct polfmm_ctx {
     double* pos_s = nullptr;
     double* q_s = nullptr;
     double* alpha_s = nullptr;
+    double* inv_alpha_s = nullptr;  // 1 / alpha (0 where alpha = 0), sorted
     int* perm = nullptr;
     uint32_t* key_s = nullptr;
     void* ploc = nullptr;

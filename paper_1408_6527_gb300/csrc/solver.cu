@@ -150,15 +150,15 @@ __global__ void pcg_init_kernel(int64_t n, const double* __restrict__ alpha, con
 // Ad = d/alpha - T d; d.Ad (partials, then the last block stores the sum).
 // Inside the solve graph (cond != 0) it also clears the loop condition, which
 // only the last kernel of the iteration sets again.
-__global__ void pcg_ad_kernel(int64_t n, const double* __restrict__ alpha, const double* __restrict__ d,
+__global__ void pcg_ad_kernel(int64_t n, const double* __restrict__ inv_alpha, const double* __restrict__ d,
                               const double* __restrict__ Td, double* __restrict__ Ad, double* __restrict__ partial,
                               double* __restrict__ scal, int* __restrict__ ticket, cudaGraphConditionalHandle cond) {
     __shared__ double sh[kRedThreads];
     if (cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(cond, 0u);
     double s = 0;
     RED_LOOP(i, 3 * n) {
-        double a = alpha[i / 3];
-        double v = a > 0.0 ? d[i] / a - Td[i] : 0.0;
+        const double ia = inv_alpha[i / 3];
+        const double v = ia > 0.0 ? d[i] * ia - Td[i] : 0.0;
         Ad[i] = v;
         s += d[i] * v;
     }
@@ -186,9 +186,13 @@ __global__ void pcg_update_kernel(int64_t n, const double* __restrict__ alpha, d
                                   double* __restrict__ r, double* __restrict__ z, double* __restrict__ partial,
                                   int* __restrict__ ticket, cudaGraphConditionalHandle cond) {
     __shared__ double sh[kRedThreads];
+    __shared__ double step_sh;
     const double dad = scal[S_DAD];
     const bool ok = dad > 0.0 && isfinite(dad);
-    const double step = ok ? scal[S_RZ] / dad : 0.0;
+    // one FP64 division per block, not per thread (FP64 is a narrow unit here)
+    if (threadIdx.x == 0) step_sh = ok ? scal[S_RZ] / dad : 0.0;
+    __syncthreads();
+    const double step = step_sh;
     double rz = 0, rr = 0;
     RED_LOOP(i, 3 * n) {
         double a = alpha[i / 3];
@@ -459,7 +463,7 @@ void solver_pcg_step(polfmm_ctx* c) {
     const cudaGraphConditionalHandle cond = c->capturing_loop ? c->loop_cond : 0;
     if (!fmm_pass(c, LEAF_DIPOLE_E, false, c->d, nullptr, c->Td, nullptr, true, true)) {
         LaunchScope ls(c, F_SOLVER);
-        pcg_ad_kernel<<<kRedBlocks, kRedThreads, 0, c->stream>>>(c->n, c->alpha_s, c->d, c->Td, c->Ad, c->partial,
+        pcg_ad_kernel<<<kRedBlocks, kRedThreads, 0, c->stream>>>(c->n, c->inv_alpha_s, c->d, c->Td, c->Ad, c->partial,
                                                                   c->scal, c->ticket, cond);
     }
     {

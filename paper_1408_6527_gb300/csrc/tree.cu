@@ -288,8 +288,8 @@ template <typename R>
 __global__ void gather_sorted_kernel(int64_t n, const int* __restrict__ perm, const uint32_t* __restrict__ key,
                                      const double* __restrict__ x, const double* __restrict__ q,
                                      const double* __restrict__ a, double* __restrict__ xs, double* __restrict__ qs,
-                                     double* __restrict__ as, R* __restrict__ ploc, double lo0, double lo1,
-                                     double lo2, double h, int* __restrict__ err) {
+                                     double* __restrict__ as, double* __restrict__ ias, R* __restrict__ ploc,
+                                     double lo0, double lo1, double lo2, double h, int* __restrict__ err) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
     int j = perm[i];
@@ -306,6 +306,7 @@ __global__ void gather_sorted_kernel(int64_t n, const int* __restrict__ perm, co
     if (!isfinite(qq) || !isfinite(aa) || aa < 0.0) atomicOr(err, 1);
     qs[i] = qq;
     as[i] = aa;
+    ias[i] = aa > 0.0 ? 1.0 / aa : 0.0;  // the solver multiplies by 1/alpha (FP64 division is slow here)
 }
 
 // ---------------------------------------------------------------------------
@@ -472,11 +473,11 @@ int tree_tables(polfmm_ctx* c, const double* x_in, const double* q_in, const dou
         LaunchScope ls(c, F_TREE);
         if (c->mixed)
             gather_sorted_kernel<float><<<grid_for(n, 256), 256, 0, st>>>(
-                n, c->perm, c->key_s, x_in, q_in, a_in, c->pos_s, c->q_s, c->alpha_s, (float*)c->ploc, c->lo[0],
+                n, c->perm, c->key_s, x_in, q_in, a_in, c->pos_s, c->q_s, c->alpha_s, c->inv_alpha_s, (float*)c->ploc, c->lo[0],
                 c->lo[1], c->lo[2], h, c->err);
         else
             gather_sorted_kernel<double><<<grid_for(n, 256), 256, 0, st>>>(
-                n, c->perm, c->key_s, x_in, q_in, a_in, c->pos_s, c->q_s, c->alpha_s, (double*)c->ploc, c->lo[0],
+                n, c->perm, c->key_s, x_in, q_in, a_in, c->pos_s, c->q_s, c->alpha_s, c->inv_alpha_s, (double*)c->ploc, c->lo[0],
                 c->lo[1], c->lo[2], h, c->err);
     }
     // device counters: [kMaxDepth + 1] box counts, then [kMaxDepth + 1][8] class counts
