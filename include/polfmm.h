@@ -86,10 +86,18 @@ typedef struct {
     void* cuda_stream;   /* cudaStream_t for all work; NULL = the legacy default stream */
     int no_graphs;       /* 1: launch every solver iteration kernel by kernel instead of replaying a
                             CUDA graph of one iteration (graphs are also off while profiling) */
+    double dipole_dl;    /* 0 (default): a point dipole enters the multipoles analytically (the
+                            limit of Sec. II.C).  > 0: as the pair of charges +-q^mu at
+                            x +- dl mu/|mu|, q^mu = |mu| / (2 dl) (Sec. II.C, mu = 2 |q^mu| dl);
+                            the near-field pairs and the field at the sites keep the explicit
+                            dipole.  FP64 mode only (in FP32 the pair's multipole cancels
+                            catastrophically); dl must not exceed a quarter of the leaf side:
+                            POLFMM_ERR_INVALID_ARG otherwise, at fmm_build or at a rebuild. */
 } polfmm_options;
 
 /* Fill *opt with the defaults: FP64, PCG, max_iter 100, coulomb_k 1, bounding
- * root cube, automatic M2L choice, no profiling, default stream. */
+ * root cube, automatic M2L choice, no profiling, default stream, analytic
+ * point-dipole multipoles (dipole_dl = 0). */
 POLFMM_API void fmm_default_options(polfmm_options* opt);
 
 /*

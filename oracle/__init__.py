@@ -57,7 +57,7 @@ def _load():
             cd = ctypes.c_double
             lib.orc_direct.argtypes = [i64, P, P, P, i64, P, P, P, P]
             lib.orc_fmm.argtypes = [i64, P, P, P, ci, ci, P, cd, P, P, P]
-            lib.orc_fmm_ex.argtypes = [i64, P, P, P, ci, ci, P, cd, P, P, P, ci]
+            lib.orc_fmm_ex.argtypes = [i64, P, P, P, ci, ci, P, cd, P, P, P, ci, cd]
             lib.orc_derivatives.argtypes = [ci, P, P]
             lib.orc_multi_indices.argtypes = [ci, P]
             lib.orc_p2m.argtypes = [ci, P, i64, P, P, P, P]
@@ -154,12 +154,14 @@ def leaf_cells(pos, depth, lo, side):
     return cells
 
 
-def fmm_fields(pos, q=None, mu=None, p=4, depth=3, root=None, fp32_top=-1):
+def fmm_fields(pos, q=None, mu=None, p=4, depth=3, root=None, fp32_top=-1, dipole_dl=0.0):
     """Phi, E, G at every site by the CPU FMM at order p on a uniform octree of
     the given depth; root = (lo, side) or None for the default root cube.
     fp32_top >= 2: the multipole shifts into levels 2..fp32_top and the local
     shifts out of them in single precision (a measurement of what single
-    precision at the top of the tree costs); -1: all FP64."""
+    precision at the top of the tree costs); -1: all FP64.  dipole_dl > 0: the
+    dipoles enter the multipoles as the +-q^mu pairs of Sec. II.C at that
+    separation (the near field keeps the explicit dipoles); 0: analytically."""
     pos = _f64(pos, (-1, 3))
     n = pos.shape[0]
     q = _f64(q)
@@ -170,7 +172,7 @@ def fmm_fields(pos, q=None, mu=None, p=4, depth=3, root=None, fp32_top=-1):
     lo = None if root is None else _f64(root[0])
     side = 0.0 if root is None else float(root[1])
     _check(_load().orc_fmm_ex(n, _ptr(pos), _ptr(q), _ptr(mu), int(p), int(depth), _ptr(lo), side,
-                              _ptr(phi), _ptr(E), _ptr(G), int(fp32_top)))
+                              _ptr(phi), _ptr(E), _ptr(G), int(fp32_top), float(dipole_dl)))
     return {"phi": phi, "E": E, "G": G}
 
 
@@ -338,11 +340,12 @@ def gradients(q, alpha, mu, tot):
 
 
 def polarizable_energy(pos, q, alpha, method="direct", p=4, depth=3, root=None, tol=1e-12,
-                       max_iter=500, solve="pcg", mu0=None, coulomb_k=1.0):
+                       max_iter=500, solve="pcg", mu0=None, coulomb_k=1.0, dipole_dl=0.0):
     """Whole path on the CPU: static field, induced dipoles, energy and gradients.
 
     method: "direct" (O(N^2) sums) or "fmm" (CPU FMM at order p and depth).
-    solve: "pcg" (PCG as in pcg_dipole_solve), "dense" (Cholesky; direct only)."""
+    solve: "pcg" (PCG as in pcg_dipole_solve), "dense" (Cholesky; direct only).
+    dipole_dl (fmm): the dipoles' multipoles from +-q pairs (Sec. II.C)."""
     pos = _f64(pos, (-1, 3))
     q = _f64(q)
     alpha = _f64(alpha)
@@ -350,7 +353,7 @@ def polarizable_energy(pos, q, alpha, method="direct", p=4, depth=3, root=None, 
     if method == "direct":
         field = lambda qq, mm: direct_fields(pos, qq, mm)
     elif method == "fmm":
-        field = lambda qq, mm: fmm_fields(pos, qq, mm, p=p, depth=depth, root=root)
+        field = lambda qq, mm: fmm_fields(pos, qq, mm, p=p, depth=depth, root=root, dipole_dl=dipole_dl)
     else:
         raise ValueError(method)
     st = field(q, None)

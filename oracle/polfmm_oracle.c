@@ -22,11 +22,14 @@
  *                    parents adjacent", per-pair derivative evaluation, and
  *                    near-field direct sums over the 27 adjacent leaves
  *                    (Sec. II.B and Sec. III, Phi = Phi^direct + Phi^fmm).
- *   orc_fmm_ex       orc_fmm with a measurement knob: the multipole shifts
- *                    into levels 2..fp32_top and the local shifts out of
- *                    them done in single precision (arithmetic and stored
- *                    result), everything else in FP64; it measures what
- *                    single precision at the top of the tree costs.
+ *   orc_fmm_ex       orc_fmm with two options: the dipoles' multipoles from
+ *                    the +-q^mu pairs of Sec. II.C at separation dipole_dl
+ *                    (0: the analytic point dipole), and a measurement knob
+ *                    that does the multipole shifts into levels 2..fp32_top
+ *                    and the local shifts out of them in single precision
+ *                    (arithmetic and stored result), everything else in FP64,
+ *                    to measure what single precision at the top of the
+ *                    tree costs.
  *
  * Conventions: positions AoS (n x 3); the field gradient G = grad E is
  * stored as (xx, xy, xz, yy, yz, zz); Coulomb constant 1; r_ij = x_i - x_j.
@@ -501,8 +504,9 @@ static inline int64_t lin3(int nside, int i, int j, int k) {
  * evaluated per pair by the recurrence above.
  */
 int orc_fmm_ex(int64_t n, const double* x, const double* q, const double* mu, int p, int depth,
-               const double* root_lo, double root_side, double* phi, double* E, double* G, int fp32_top) {
-    if (n < 1 || p < 1 || p > ORC_MAXP || depth < 1 || depth > 8) return ORC_EINVAL;
+               const double* root_lo, double root_side, double* phi, double* E, double* G, int fp32_top,
+               double dipole_dl) {
+    if (n < 1 || p < 1 || p > ORC_MAXP || depth < 1 || depth > 8 || !(dipole_dl >= 0.0)) return ORC_EINVAL;
     orc_mi t;
     if (mi_init(&t, p)) return ORC_ENOMEM;
     const int nc = t.ncoef;
@@ -584,7 +588,21 @@ int orc_fmm_ex(int64_t n, const double* x, const double* q, const double* mu, in
         BOX_CENTRE(depth, b, z);
         for (int64_t k = start[b]; k < start[b + 1]; k++) {
             int64_t a = order[k];
-            p2m_accum(&t, z, 1, x + 3 * a, q ? q + a : NULL, mu ? mu + 3 * a : NULL, L->M + b * nc);
+            if (mu && dipole_dl > 0.0) {
+                /* the dipole as the charges +-q^mu at x +- dl mu/|mu|, q^mu = |mu|/(2 dl) (Sec. II.C) */
+                if (q) p2m_accum(&t, z, 1, x + 3 * a, q + a, NULL, L->M + b * nc);
+                const double* m = mu + 3 * a;
+                double nm = sqrt(m[0] * m[0] + m[1] * m[1] + m[2] * m[2]);
+                if (nm > 0.0) {
+                    for (int sgn = -1; sgn <= 1; sgn += 2) {
+                        double y[3], qq = sgn * nm / (2.0 * dipole_dl);
+                        for (int d = 0; d < 3; d++) y[d] = x[3 * a + d] + sgn * dipole_dl * m[d] / nm;
+                        p2m_accum(&t, z, 1, y, &qq, NULL, L->M + b * nc);
+                    }
+                }
+            } else {
+                p2m_accum(&t, z, 1, x + 3 * a, q ? q + a : NULL, mu ? mu + 3 * a : NULL, L->M + b * nc);
+            }
         }
     }
     /* M2M up to level 2 */
@@ -717,7 +735,7 @@ int orc_fmm_ex(int64_t n, const double* x, const double* q, const double* mu, in
 
 int orc_fmm(int64_t n, const double* x, const double* q, const double* mu, int p, int depth,
             const double* root_lo, double root_side, double* phi, double* E, double* G) {
-    return orc_fmm_ex(n, x, q, mu, p, depth, root_lo, root_side, phi, E, G, -1);
+    return orc_fmm_ex(n, x, q, mu, p, depth, root_lo, root_side, phi, E, G, -1, 0.0);
 }
 
 int orc_num_threads(void) {

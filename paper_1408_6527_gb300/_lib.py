@@ -41,6 +41,7 @@ class Options(ctypes.Structure):
         ("profile", ctypes.c_int),
         ("cuda_stream", ctypes.c_void_p),
         ("no_graphs", ctypes.c_int),
+        ("dipole_dl", ctypes.c_double),
     ]
 
 

@@ -516,6 +516,8 @@ int rebuild(polfmm_ctx* c) {
     } else if ((rc = tree_root_box(c, x_in, c->partial, c->h_bbox)) != POLFMM_OK) {
         return rc;
     }
+    // the pair +-dl mu/|mu| stays well inside its leaf's expansion
+    if (c->opt.dipole_dl > 0.25 * c->side / (double)(1 << c->depth)) return POLFMM_ERR_INVALID_ARG;
     if ((rc = tree_build(c, x_in)) != POLFMM_OK) return rc;
     if ((rc = tree_tables(c, x_in, q_in, a_in)) != POLFMM_OK) return rc;
     if ((rc = read_err(c)) != POLFMM_OK) return rc;
@@ -733,6 +735,9 @@ int fmm_build(polfmm_ctx** out, int64_t n, const double* positions, const double
     if (o.mode != POLFMM_FP64 && o.mode != POLFMM_MIXED) return POLFMM_ERR_INVALID_ARG;
     if (o.solver != POLFMM_SOLVER_PCG && o.solver != POLFMM_SOLVER_JACOBI) return POLFMM_ERR_INVALID_ARG;
     if (o.max_iter < 0) return POLFMM_ERR_INVALID_ARG;
+    // the +-q pair form of the dipoles: FP64 only, finite, non-negative
+    if (!(o.dipole_dl >= 0.0) || !isfinite(o.dipole_dl) || (o.dipole_dl > 0.0 && o.mode != POLFMM_FP64))
+        return POLFMM_ERR_INVALID_ARG;
     if (!(o.coulomb_k == o.coulomb_k) || !isfinite(o.coulomb_k)) return POLFMM_ERR_INVALID_ARG;
     if (o.use_root_box && (!(o.root_side > 0.0) || !isfinite(o.root_side) || !finite_host(o.root_lo, 3)))
         return POLFMM_ERR_INVALID_ARG;

@@ -109,7 +109,8 @@ template <typename R>
 __global__ void __launch_bounds__(kUpThreads) upward_kernel(
     int nleaf, int depth, const int* __restrict__ lstart, const int* __restrict__ lcount,
     const R* __restrict__ ploc, const double* __restrict__ q, const double* __restrict__ mu, UpPtrs up, int ld,
-    int ncoef, int p, const int* __restrict__ mi, const R* __restrict__ w4, const R* __restrict__ rinv, R inv_h) {
+    int ncoef, int p, const int* __restrict__ mi, const R* __restrict__ w4, const R* __restrict__ rinv, R inv_h,
+    double dl) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     R* S = reinterpret_cast<R*>(smem_raw);         // [8][ncoef] slice partials of P2M, then shift rows
     R* Mrow = S + 8 * ncoef;                        // [ncoef] multipole of the current box
@@ -142,16 +143,32 @@ __global__ void __launch_bounds__(kUpThreads) upward_kernel(
         ny[k] = (pk >> 8) & 0xff;
         nz[k] = (pk >> 16) & 0xff;
     }
+    // P2M entries: one per site; with dipoles as +-q pairs (dl > 0, Sec. II.C)
+    // three per site: the charge at x, +q^mu at x + dl mu/|mu|, -q^mu at x - dl mu/|mu|
     const int s0 = lstart[b], cnt = lcount[b];
-    for (int k0 = 0; k0 < cnt; k0 += kP2MChunk) {
-        const int m = min(kP2MChunk, cnt - k0);
+    const int per = (mu && dl > 0.0) ? 3 : 1;
+    for (int k0 = 0; k0 < cnt * per; k0 += kP2MChunk) {
+        const int m = min(kP2MChunk, cnt * per - k0);
         __syncthreads();
         if (tid < m) {
-            const int i = s0 + k0 + tid;
-            const R qi = q ? R(q[i]) : R(0);
+            const int e = k0 + tid;
+            const int i = s0 + e / per, which = e % per;
+            R qi = which == 0 && q ? R(q[i]) : R(0);
+            R off[3] = {R(0), R(0), R(0)};
+            if (which > 0) {
+                const double mx = mu[3 * i], my = mu[3 * i + 1], mz = mu[3 * i + 2];
+                const double nm = sqrt(mx * mx + my * my + mz * mz);
+                if (nm > 0.0) {
+                    const double sgn = which == 1 ? 1.0 : -1.0;
+                    qi = R(sgn * nm / (2.0 * dl));
+                    off[0] = R(sgn * dl * mx / nm);
+                    off[1] = R(sgn * dl * my / nm);
+                    off[2] = R(sgn * dl * mz / nm);
+                }
+            }
             for (int a = 0; a < 3; a++) {
-                const R v = -ploc[3 * i + a] * inv_h;
-                const R ma = mu ? R(mu[3 * i + a]) * inv_h : R(0);
+                const R v = -(ploc[3 * i + a] + off[a]) * inv_h;
+                const R ma = mu && per == 1 ? R(mu[3 * i + a]) * inv_h : R(0);
                 R t = R(1), prev = R(0);
                 for (int k = 0; k <= p; k++) {
                     if (k > 0) t = t * v * RI[k];
@@ -1463,7 +1480,8 @@ static bool pass_impl(polfmm_ctx* c, int mode, bool use_q, const double* mu_sort
             R inv_h = R((double)(1 << d) / c->side);
             upward_kernel<R><<<Lf.nbox, kUpThreads, upward_smem_bytes<R>(c->ncoef), c->stream>>>(
                 Lf.nbox, d, c->lstart, c->lcount, (const R*)c->ploc, use_q ? c->q_s : nullptr, mu_sorted,
-                up_ptrs(c), c->ld, c->ncoef, c->p, T.mi, pick<R>(T.w4, T.w4f), pick<R>(T.rinv, T.rinvf), inv_h);
+                up_ptrs(c), c->ld, c->ncoef, c->p, T.mi, pick<R>(T.w4, T.w4f), pick<R>(T.rinv, T.rinvf), inv_h,
+                c->opt.dipole_dl);
         }
         // M2L, all levels >= 2 in one launch
         if (m2l_tensor_enabled(c)) {
