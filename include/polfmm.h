@@ -221,6 +221,28 @@ POLFMM_API int fmm_set_exclusions(polfmm_ctx* ctx, int64_t npairs, const int32_t
  * charges set; POLFMM_ERR_STATE before one. */
 POLFMM_API int fmm_field_charge_gradient(polfmm_ctx* ctx, double* dU_dqE, int on_device);
 
+/*
+ * Thole damping of the dipole-dipole interaction (Sec. II.A names Thole's
+ * model as part of the force field without printing it; the form is Thole's
+ * exponential model as used by the AMOEBA force field: B. T. Thole, Chem.
+ * Phys. 59, 341 (1981); P. Ren and J. W. Ponder, J. Phys. Chem. B 107, 5933
+ * (2003)).  Between two polarizable sites the field of a dipole,
+ * 3 (mu.r) r / r^5 - mu / r^3, becomes
+ *   lambda5 3 (mu.r) r / r^5 - lambda3 mu / r^3,  u = r / (alpha_i alpha_j)^(1/6),
+ *   lambda3 = 1 - exp(-a u^3),  lambda5 = 1 - (1 + a u^3) exp(-a u^3).
+ * Charge-dipole terms and pairs with a non-polarizable site stay undamped;
+ * excluded pairs stay excluded.  The damping changes the dipole solve, the
+ * energy, the forces (the derivatives of lambda3 and lambda5 included) and
+ * dU/dalpha; fmm_static_field, fmm_dipole_field and fmm_total_field keep
+ * returning the undamped FMM fields.  The pairs with a u^3 < 40 (beyond,
+ * exp(-a u^3) < 5e-18) are listed per tree with a spatial hash and corrected
+ * with direct pair terms (damped minus undamped), in the mode's precision in
+ * the solve and in FP64 for energy and gradients.  a = 0 switches it off;
+ * a < 0 or non-finite: POLFMM_ERR_INVALID_ARG.  Kept across
+ * fmm_update_positions; the next solve starts from the current dipoles.
+ */
+POLFMM_API int fmm_set_thole(polfmm_ctx* ctx, double a);
+
 /* New positions for the same sites: rebuild the tree and the static pass,
  * keeping the current dipoles as the next solve's starting guess. */
 POLFMM_API int fmm_update_positions(polfmm_ctx* ctx, const double* positions, int on_device);

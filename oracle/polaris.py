@@ -31,6 +31,17 @@ Readings:
   "separated by less than two chemical bonds") names a common choice, not a
   rule.
 - A pair that is excluded is excluded from all three sums.
+- Thole damping of the dipole tensor (Sec. II.A cites Thole's model without
+  printing it): the exponential model of B. T. Thole, Chem. Phys. 59, 341
+  (1981), in the form of P. Ren and J. W. Ponder, J. Phys. Chem. B 107, 5933
+  (2003). Between two dipoles the field 3 (mu.r) r / r^5 - mu / r^3 becomes
+  lambda5 3 (mu.r) r / r^5 - lambda3 mu / r^3, with u = r / (alpha_i alpha_j)^(1/6),
+  lambda3 = 1 - exp(-a u^3), lambda5 = 1 - (1 + a u^3) exp(-a u^3); a pair with
+  a non-polarizable site is not damped. Charge-dipole terms stay undamped.
+  The dipole-dipole part of the forces and of dU/dalpha then carries the
+  derivatives of lambda3 and lambda5:
+      F_i  += sum_j grad_i (mu_i . T^d_ij mu_j),
+      dU/dalpha_i += -sum_j mu_i . (d T^d_ij / d alpha_i) mu_j.
 
 ``dense`` evaluates the pair sums directly. ``fmm`` takes the CPU octree FMM's
 fields over all pairs and subtracts the excluded pairs' direct terms, which
@@ -87,6 +98,54 @@ def _dipole_fields(r, ri, mask, mu):
     return phi, E, G
 
 
+def thole_factors(r, ri, alpha, a, mask):
+    """lambda3, lambda5 of every pair and their derivatives with respect to r
+    and to u (the damping is 1 where alpha_i alpha_j = 0 or the pair is masked)."""
+    rr = 1.0 / ri
+    s = np.cbrt(np.sqrt(np.outer(alpha, alpha)))  # (alpha_i alpha_j)^(1/6)
+    on = mask & (s > 0)
+    u = np.where(on, rr / np.where(on, s, 1.0), np.inf)
+    au3 = a * u ** 3
+    ex = np.where(on, np.exp(-np.where(on, au3, 0.0)), 0.0)
+    au3 = np.where(on, au3, 0.0)
+    l3 = 1.0 - ex
+    l5 = 1.0 - (1.0 + au3) * ex
+    uf = np.where(on, u, 0.0)
+    d3u = 3.0 * a * uf ** 2 * ex
+    d5u = 3.0 * a * a * uf ** 5 * ex
+    sf = np.where(on, s, 1.0)
+    return {"l3": l3, "l5": l5, "d3r": d3u / sf, "d5r": d5u / sf, "d3u": d3u, "d5u": d5u, "u": uf}
+
+
+def _dipole_field_damped(r, ri, mask, mu, th):
+    """E_i = sum_j lambda5 3 (mu_j.r) r / r^5 - lambda3 mu_j / r^3 (Thole)."""
+    ri3 = ri ** 3 * mask
+    ri5 = ri3 * ri * ri
+    mr = np.einsum("ijk,jk->ij", r, mu)
+    return 3.0 * np.einsum("ij,ijk->ik", th["l5"] * mr * ri5, r) - (th["l3"] * ri3) @ mu
+
+
+def _dipole_pair_gradients(r, ri, mask, mu, alpha, th):
+    """sum_j grad_i (mu_i . T^d_ij mu_j) and sum_j mu_i . (d T^d_ij / d alpha_i) mu_j
+    with T^d_ij mu_j the damped field of dipole j at i."""
+    ri1 = ri * mask
+    ri3 = ri1 ** 3
+    ri5 = ri3 * ri1 * ri1
+    ri7 = ri5 * ri1 * ri1
+    A = mu @ mu.T                                   # mu_i . mu_j
+    Bi = np.einsum("ijk,ik->ij", r, mu)             # mu_i . r_ij
+    Bj = np.einsum("ijk,jk->ij", r, mu)             # mu_j . r_ij
+    l3, l5, d3r, d5r = th["l3"], th["l5"], th["d3r"], th["d5r"]
+    # coefficient of r_ij, and of mu_i / mu_j
+    cr = 3.0 * Bi * Bj * (d5r * ri1 * ri5 - 5.0 * l5 * ri7) - A * (d3r * ri1 * ri3 - 3.0 * l3 * ri5)
+    F = (np.einsum("ij,ijk->ik", cr, r) + 3.0 * np.einsum("ij,ik->ik", l5 * ri5 * Bj, mu)
+         + 3.0 * (l5 * ri5 * Bi) @ mu)
+    act = alpha > 0
+    dadu = np.where(act[:, None], -th["u"] / (6.0 * np.where(act, alpha, 1.0))[:, None], 0.0)
+    dA = ((3.0 * Bi * Bj * ri5 * th["d5u"] - A * ri3 * th["d3u"]) * dadu).sum(1)
+    return F, dA
+
+
 def _excluded_correction(pos, exclusions, w, mu=None):
     """Direct terms of the excluded pairs (both directions): Phi, E, G of charges
     w, or of dipoles mu when given, at every site; what an FMM over all pairs
@@ -110,14 +169,16 @@ def _excluded_correction(pos, exclusions, w, mu=None):
 
 
 def polaris_energy(pos, q, qE, alpha, exclusions=(), method="dense", p=8, depth=3, root=None, solve="dense",
-                   tol=1e-13, max_iter=500):
+                   tol=1e-13, max_iter=500, thole=0.0):
     """U, its gradients and the dipoles for charges q, field charges qE,
     polarizabilities alpha and the excluded pairs. method: "dense" (pair sums)
     or "fmm" (CPU octree FMM at order p over all pairs, minus the excluded
     pairs' direct terms). solve: "dense" (Cholesky of diag(1/alpha) - T, T
     built column by column from the method's dipole field and symmetrised) or
     "pcg" (the preconditioned conjugate gradients of ``oracle.pcg_dipole_solve``
-    on the method's dipole field as it is, to the relative residual tol)."""
+    on the method's dipole field as it is, to the relative residual tol).
+    thole > 0: Thole damping of the dipole-dipole tensor with that a (the
+    damped minus undamped terms as pair sums over the non-excluded pairs)."""
     pos = np.ascontiguousarray(pos, dtype=np.float64)
     q, qE, alpha = (np.asarray(v, dtype=np.float64) for v in (q, qE, alpha))
     n = pos.shape[0]
@@ -144,6 +205,17 @@ def polaris_energy(pos, q, qE, alpha, exclusions=(), method="dense", p=8, depth=
             return f["phi"] - c[0], f["E"] - c[1], f["G"] - c[2]
     else:
         raise ValueError(method)
+    th = thole_factors(r, ri, alpha, float(thole), mask) if thole > 0 else None
+
+    def dipole_field_dd(mu):
+        """the field of the dipoles as the dipoles feel it (damped when thole > 0)"""
+        E = dipoles(mu)[1]
+        if th is not None:
+            E = E + _dipole_field_damped(r, ri, mask, mu, th) - _dipoles_undamped_E(mu)
+        return E
+
+    def _dipoles_undamped_E(mu):
+        return _dipole_fields(r, ri, mask, mu)[1]
 
     phi_c, E_c, _ = charges(q)
     _, E_qE, G_qE = charges(qE)
@@ -153,7 +225,7 @@ def polaris_energy(pos, q, qE, alpha, exclusions=(), method="dense", p=8, depth=
     idx = np.nonzero(act)[0]
     mu = np.zeros((n, 3))
     if solve == "pcg":
-        mu, _, _, _ = pcg_dipole_solve(alpha, E_qE, lambda v: dipoles(v)[1], tol=tol, max_iter=max_iter)
+        mu, _, _, _ = pcg_dipole_solve(alpha, E_qE, dipole_field_dd, tol=tol, max_iter=max_iter)
     elif solve != "dense":
         raise ValueError(solve)
     elif idx.size:
@@ -162,7 +234,7 @@ def polaris_energy(pos, q, qE, alpha, exclusions=(), method="dense", p=8, depth=
         for c in range(3 * k):
             e = np.zeros((n, 3))
             e[idx[c // 3], c % 3] = 1.0
-            T[:, c] = dipoles(e)[1][idx].ravel()
+            T[:, c] = dipole_field_dd(e)[idx].ravel()
         T = 0.5 * (T + T.T)
         A = np.diag(np.repeat(1.0 / alpha[idx], 3)) - T
         try:
@@ -172,17 +244,27 @@ def polaris_energy(pos, q, qE, alpha, exclusions=(), method="dense", p=8, depth=
         y = np.linalg.solve(L, E_qE[idx].ravel())
         mu[idx] = np.linalg.solve(L.T, y).reshape(-1, 3)
     phi_m, E_m, G_m = dipoles(mu)
+    E_dd = dipole_field_dd(mu)
 
     m2 = (mu * mu).sum(1)
     safe = np.where(act, alpha, 1.0)
     Uqq = 0.5 * float((q * phi_c).sum())
-    Upol = float(0.5 * np.where(act, m2 / safe, 0.0).sum() - (mu * E_qE).sum() - 0.5 * (mu * E_m).sum())
-    G = G_qE + G_m
-    Gm = np.stack([G[:, 0] * mu[:, 0] + G[:, 1] * mu[:, 1] + G[:, 2] * mu[:, 2],
-                   G[:, 1] * mu[:, 0] + G[:, 3] * mu[:, 1] + G[:, 4] * mu[:, 2],
-                   G[:, 2] * mu[:, 0] + G[:, 4] * mu[:, 1] + G[:, 5] * mu[:, 2]], 1)
-    F = q[:, None] * E_c + qE[:, None] * E_m + Gm
+    Upol = float(0.5 * np.where(act, m2 / safe, 0.0).sum() - (mu * E_qE).sum() - 0.5 * (mu * E_dd).sum())
+
+    def gmu(G):
+        return np.stack([G[:, 0] * mu[:, 0] + G[:, 1] * mu[:, 1] + G[:, 2] * mu[:, 2],
+                         G[:, 1] * mu[:, 0] + G[:, 3] * mu[:, 1] + G[:, 4] * mu[:, 2],
+                         G[:, 2] * mu[:, 0] + G[:, 4] * mu[:, 1] + G[:, 5] * mu[:, 2]], 1)
+
+    F = q[:, None] * E_c + qE[:, None] * E_m + gmu(G_qE) + gmu(G_m)
+    dUda = np.where(act, -m2 / (2.0 * safe * safe), -0.5 * ((E_qE + E_m) ** 2).sum(1))
+    if th is not None:
+        # dipole-dipole terms with the damping and its derivatives, in place of
+        # the undamped (grad E^mu) mu
+        th0 = {k: (np.ones_like(v) if k in ("l3", "l5") else np.zeros_like(v)) for k, v in th.items()}
+        Fd, dAd = _dipole_pair_gradients(r, ri, mask, mu, alpha, th)
+        Fu, _ = _dipole_pair_gradients(r, ri, mask, mu, alpha, th0)
+        F = F + Fd - Fu
+        dUda = dUda - dAd
     return {"U": Uqq + Upol, "Uqq": Uqq, "Upol": Upol, "Upol_stationary": -0.5 * float((mu * E_qE).sum()),
-            "F": F, "dUdq": phi_c, "dUdqE": phi_m,
-            "dUdalpha": np.where(act, -m2 / (2.0 * safe * safe), -0.5 * ((E_qE + E_m) ** 2).sum(1)),
-            "mu": mu}
+            "F": F, "dUdq": phi_c, "dUdqE": phi_m, "dUdalpha": dUda, "mu": mu}

@@ -187,6 +187,10 @@ class PolFMM:
         _lib.check(self.lib.fmm_set_exclusions(self.h, int(arr.shape[0]), arr.ctypes.data_as(ctypes.c_void_p), 0),
                    "fmm_set_exclusions")
 
+    def set_thole(self, a):
+        """Thole damping of the dipole-dipole interaction with parameter a (0 = off)."""
+        _lib.check(self.lib.fmm_set_thole(self.h, float(a)), "fmm_set_thole")
+
     def field_charge_gradient(self):
         """dU/dq^E of the last energy_forces() with field charges set."""
         out, p = self._out(self.n)

@@ -65,6 +65,7 @@ SIGNATURES = {
     "fmm_set_field_charges": (I, [P, P, I]),
     "fmm_set_exclusions": (I, [P, I64, P, I]),
     "fmm_field_charge_gradient": (I, [P, P, I]),
+    "fmm_set_thole": (I, [P, D]),
     "fmm_reset_dipoles": (I, [P]),
     "fmm_static_field": (I, [P, P, P, I]),
     "fmm_dipole_field": (I, [P, P, P, I]),

@@ -531,6 +531,7 @@ int rebuild(polfmm_ctx* c) {
     exclusion_inv_perm(c);
     pack_positions(c);
     if ((rc = near_tables(c)) != POLFMM_OK) return rc;
+    if ((rc = thole_pairs(c)) != POLFMM_OK) return rc;
     static_passes(c);
     c->pcg_graph_dirty = true;  // launch sizes of the solver iteration changed
     c->loop_dirty = true;
@@ -680,6 +681,7 @@ void destroy_impl(polfmm_ctx* c) {
     m2l_tensor_release(c);
     free_tables(c->tab);
     if (c->tiles) cudaFree(c->tiles);
+    if (c->th_idx) cudaFree(c->th_idx);
     if (c->h_scal) cudaFreeHost(c->h_scal);
     if (c->h_counts) cudaFreeHost(c->h_counts);
     if (c->h_bbox) cudaFreeHost(c->h_bbox);
@@ -1021,7 +1023,15 @@ int fmm_set_exclusions(polfmm_ctx* c, int64_t npairs, const int32_t* pairs, int 
         c->excl_cap = idx.size();
         c->excl_idx = A.get<int>(idx.size());
     }
+    if (!c->excl_row) c->excl_row = A.get<int>(n);
     if (!A.ok) return POLFMM_ERR_OUT_OF_MEMORY;
+    {
+        // caller index -> row of the target list (the Thole pair list skips excluded pairs)
+        std::vector<int> row((size_t)n, -1);
+        for (size_t t = 0; t < targets.size(); t++) row[targets[t]] = (int)t;
+        if (cudaMemcpy(c->excl_row, row.data(), sizeof(int) * row.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+            return cuda_fail(cudaGetLastError(), "upload of the excluded pairs");
+    }
     if (!targets.empty() &&
         (cudaMemcpy(c->excl_targets, targets.data(), sizeof(int) * targets.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
          cudaMemcpy(c->excl_ptr, ptr.data(), sizeof(int) * ptr.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
@@ -1030,10 +1040,44 @@ int fmm_set_exclusions(polfmm_ctx* c, int64_t npairs, const int32_t* pairs, int 
     c->n_excl = (int64_t)(e.size() / 2);
     c->n_excl_targets = (int)targets.size();
     exclusion_inv_perm(c);
+    int rc = thole_pairs(c);
+    if (rc != POLFMM_OK) return rc;
     static_passes(c);
     c->pcg_graph_dirty = true;  // the solver pass gains (or loses) the correction kernel
     c->loop_dirty = true;
     c->have_dqE = false;
+    return read_err(c);
+}
+
+int fmm_set_thole(polfmm_ctx* c, double a) {
+    if (!c || !(a >= 0.0) || !isfinite(a)) return POLFMM_ERR_INVALID_ARG;
+    if (a > 0.0 && !c->a16) {
+        const int64_t n = c->n;
+        int nb = 1024;  // a power of two <= max(n, 4096): the tree's scan scratch holds it
+        while ((int64_t)nb * 2 <= std::max<int64_t>(n, 4096)) nb *= 2;
+        Alloc& A = extra_of(c)->alloc;
+        c->th_nb = nb;
+        c->a16 = A.get<double>(n);
+        c->th_bucket = A.get<int>(nb + 1);
+        c->th_count = A.get<int>(nb);
+        c->th_member = A.get<int>(n);
+        c->th_cell = A.get<int4>(n);
+        c->th_cnt = A.get<int>(n + 64);
+        c->th_ptr = A.get<int>(n + 1);
+        c->th_max = A.get<double>(2);
+        c->thE = A.get<double>(3 * n);
+        c->thF = A.get<double>(3 * n);
+        c->thdA = A.get<double>(n);
+        if (!A.ok) {
+            c->a16 = nullptr;
+            return POLFMM_ERR_OUT_OF_MEMORY;
+        }
+    }
+    c->thole_a = a;
+    int rc = thole_pairs(c);
+    if (rc != POLFMM_OK) return rc;
+    c->pcg_graph_dirty = true;  // the solver pass gains (or loses) the correction kernel
+    c->loop_dirty = true;
     return read_err(c);
 }
 

@@ -1471,6 +1471,7 @@ static bool pass_impl(polfmm_ctx* c, int mode, bool use_q, const double* mu_sort
         launch_leaf<R>(c, mode, mu_sorted, phi, E, G, mu_packed, overlap ? c->side_stream : c->stream, 0);
         // excluded pairs off the near field, before the far field completes it
         exclusion_correct(c, mode, nullptr, mu_sorted, nullptr, E, nullptr, overlap ? c->side_stream : c->stream);
+        thole_field(c, mu_sorted, E, overlap ? c->side_stream : c->stream);
         if (overlap) cudaEventRecord(c->ev_join, c->side_stream);
     }
     if (d >= 2) {
@@ -1512,6 +1513,7 @@ static bool pass_impl(polfmm_ctx* c, int mode, bool use_q, const double* mu_sort
     }
     launch_leaf<R>(c, mode, mu_sorted, phi, E, G, mu_packed, c->stream, d >= 2 ? 1 : 0);
     exclusion_correct(c, mode, use_q ? c->q_s : nullptr, mu_sorted, phi, E, G, c->stream);
+    if (mode == LEAF_DIPOLE_E) thole_field(c, mu_sorted, E, c->stream);
     return false;
 }
 

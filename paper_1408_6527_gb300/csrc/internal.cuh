@@ -212,6 +212,25 @@ struct polfmm_ctx {
     int* excl_idx = nullptr;      // [2 n_excl] partners, caller indices, ascending per site
     int* inv_perm = nullptr;      // [n] sorted index of each caller index
     size_t excl_cap = 0, excl_targets_cap = 0;
+    int* excl_row = nullptr;      // [n] caller index -> row of excl_targets, -1 if none
+    // Thole damping: parameter (0 = off), the damped pairs of the current tree
+    // (CSR over sorted sites, partners in sorted order), alpha^(1/6) per sorted
+    // site, the hash scratch, and the force-pass corrections (sorted order)
+    double thole_a = 0.0;
+    int* th_ptr = nullptr;        // [n + 1]
+    int* th_idx = nullptr;        // [th_cap]
+    int64_t th_cap = 0, th_npairs = 0;
+    double* a16 = nullptr;        // [n]
+    int* th_bucket = nullptr;     // [th_nb + 1] bucket starts
+    int* th_count = nullptr;      // [th_nb] bucket counts
+    int* th_member = nullptr;     // [n] sites grouped by bucket
+    int4* th_cell = nullptr;      // [n] cell coordinates and bucket
+    int* th_cnt = nullptr;        // [n + 64] pairs per site
+    double* th_max = nullptr;     // device max of alpha^(1/6)
+    int th_nb = 0;
+    double* thE = nullptr;        // [3n] damped minus undamped dipole field
+    double* thF = nullptr;        // [3n] damped minus undamped dipole-dipole force
+    double* thdA = nullptr;       // [n] damping part of dU/dalpha
     bool have_dqE = false;        // dqE holds the last force pass's dU/dq^E
 
     bool have_mu = false;
@@ -301,6 +320,12 @@ void mask_dipoles(polfmm_ctx* c, double* v);
 void exclusion_correct(polfmm_ctx* c, int leaf_mode, const double* w_sorted, const double* mu_sorted, double* phi,
                        double* E, double* G, cudaStream_t st);
 void exclusion_inv_perm(polfmm_ctx* c);
+// Thole damping (polaris.cu): the pair list of the current tree, the solve's
+// field correction (E += (T^damp - T) mu, after the near field), and the
+// force-pass corrections into thE, thF, thdA
+int thole_pairs(polfmm_ctx* c);
+void thole_field(polfmm_ctx* c, const double* mu_sorted, double* E, cudaStream_t st);
+void thole_forces(polfmm_ctx* c);
 // the field that polarizes the sites: that of the field charges when set
 inline const double* polarizing_field(const polfmm_ctx* c) { return c->EqE ? c->EqE : c->Eq; }
 

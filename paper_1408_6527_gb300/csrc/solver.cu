@@ -335,7 +335,9 @@ __global__ void assemble_kernel(int64_t n, const int* __restrict__ perm, const d
                                 const double* __restrict__ mu, const double* __restrict__ phiq,
                                 const double* __restrict__ Eq, const double* __restrict__ phiqE,
                                 const double* __restrict__ EqE, const double* __restrict__ phi,
-                                const double* __restrict__ E, const double* __restrict__ G, double kc,
+                                const double* __restrict__ E, const double* __restrict__ G,
+                                const double* __restrict__ thE, const double* __restrict__ thF,
+                                const double* __restrict__ thdA, double kc,
                                 double* __restrict__ F, double* __restrict__ dq, double* __restrict__ dqE,
                                 double* __restrict__ da, double* __restrict__ partial) {
     __shared__ double sh[kRedThreads];
@@ -360,6 +362,11 @@ __global__ void assemble_kernel(int64_t n, const int* __restrict__ perm, const d
                 f1 = qi * e1;
                 f2 = qi * e2;
             }
+            if (thF) {  // Thole: the damped minus undamped dipole-dipole force
+                f0 += thF[3 * i];
+                f1 += thF[3 * i + 1];
+                f2 += thF[3 * i + 2];
+            }
             F[3 * (int64_t)o + 0] = kc * (f0 + g[0] * m0 + g[1] * m1 + g[2] * m2);
             F[3 * (int64_t)o + 1] = kc * (f1 + g[1] * m0 + g[3] * m1 + g[4] * m2);
             F[3 * (int64_t)o + 2] = kc * (f2 + g[2] * m0 + g[4] * m1 + g[5] * m2);
@@ -367,10 +374,13 @@ __global__ void assemble_kernel(int64_t n, const int* __restrict__ perm, const d
         if (dq) dq[o] = kc * (qE ? phiq[i] : phi[i]);
         if (dqE) dqE[i] = kc * (phi[i] - (phiqE ? phiqE[i] : phiq[i]));
         const double mm = m0 * m0 + m1 * m1 + m2 * m2;
-        if (da) da[o] = ai > 0.0 ? -kc * mm / (2.0 * ai * ai) : -0.5 * kc * (e0 * e0 + e1 * e1 + e2 * e2);
+        if (da)
+            da[o] = ai > 0.0 ? kc * (-mm / (2.0 * ai * ai) + (thdA ? thdA[i] : 0.0))
+                             : -0.5 * kc * (e0 * e0 + e1 * e1 + e2 * e2);
         uqq += 0.5 * qi * phiq[i];
         mueq += m0 * q0 + m1 * q1 + m2 * q2;
         muemu += m0 * (e0 - q0) + m1 * (e1 - q1) + m2 * (e2 - q2);
+        if (thE) muemu += m0 * thE[3 * i] + m1 * thE[3 * i + 1] + m2 * thE[3 * i + 2];  // the damped E^mu
         if (ai > 0.0) amu += mm / (2.0 * ai);
     }
     uqq = block_sum(uqq, sh);
@@ -499,12 +509,15 @@ void solver_jacobi_step(polfmm_ctx* c) {
 
 void energy_and_gradients(polfmm_ctx* c, double* F, double* dq, double* da, bool want_f, bool want_dq,
                           bool want_da) {
+    const bool th = c->th_npairs > 0;
+    if (th) thole_forces(c);
     {
         LaunchScope ls(c, F_ASSEMBLE);
         assemble_kernel<<<kRedBlocks, kRedThreads, 0, c->stream>>>(
             c->n, c->perm, c->q_s, c->qE_s, c->alpha_s, c->mu, c->phiq, c->Eq, c->phiqE, c->EqE, c->phi_t, c->E_t,
-            c->G_t, c->opt.coulomb_k, want_f ? F : nullptr, want_dq ? dq : nullptr, c->qE_s ? c->dqE : nullptr,
-            want_da ? da : nullptr, c->partial);
+            c->G_t, th ? c->thE : nullptr, th ? c->thF : nullptr, th ? c->thdA : nullptr, c->opt.coulomb_k,
+            want_f ? F : nullptr, want_dq ? dq : nullptr, c->qE_s ? c->dqE : nullptr, want_da ? da : nullptr,
+            c->partial);
     }
     reduce(c, 4, S_UQQ, S_MUEQ, S_MUEMU, S_AMU, 0, F_ASSEMBLE);
 }

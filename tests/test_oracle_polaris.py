@@ -120,3 +120,70 @@ def test_pcg_solve_reproduces_the_dense_solve():
     assert abs(a["U"] - b["U"]) < 1e-12 * abs(a["U"])
     for k in ("F", "dUdq", "dUdqE", "dUdalpha", "mu"):
         assert oracle.rel_rms(b[k], a[k]) < 1e-10, k
+
+
+# ---------------------------------------------------------------------------
+# Thole damping of the dipole-dipole tensor (reading: Thole's exponential model
+# as used by AMOEBA; the paper cites Thole without printing the form)
+# ---------------------------------------------------------------------------
+
+def test_thole_factors_closed_form_and_limits():
+    pos = np.array([[0.0, 0.0, 0.0], [1.5, 0.0, 0.0], [40.0, 0.0, 0.0]])
+    alpha = np.array([1.0, 8.0, 1.0])
+    r, ri = polaris._pairs(pos)
+    th = polaris.thole_factors(r, ri, alpha, 0.39, polaris._mask(3, []))
+    u = 1.5 / (1.0 * 8.0) ** (1 / 6)
+    au3 = 0.39 * u ** 3
+    assert th["l3"][0, 1] == pytest.approx(1 - np.exp(-au3), rel=1e-14)
+    assert th["l5"][0, 1] == pytest.approx(1 - (1 + au3) * np.exp(-au3), rel=1e-14)
+    # far apart: undamped to FP64; symmetric in i, j
+    assert th["l3"][0, 2] == 1.0 and th["l5"][0, 2] == 1.0
+    np.testing.assert_array_equal(th["l3"], th["l3"].T)
+    # a site without polarizability is never damped
+    th0 = polaris.thole_factors(r, ri, np.array([0.0, 8.0, 1.0]), 0.39, polaris._mask(3, []))
+    assert th0["l3"][0, 1] == 1.0 and th0["l5"][0, 1] == 1.0 and th0["d3r"][0, 1] == 0.0
+
+
+def test_thole_damping_gradients_are_finite_differences_of_the_energy():
+    pos, q, qE, alpha, excl = _system()
+    a = 0.39
+    ref = polaris.polaris_energy(pos, q, qE, alpha, excl, thole=a)
+    und = polaris.polaris_energy(pos, q, qE, alpha, excl)
+    assert abs(ref["U"] - und["U"]) > 1e-5 * abs(und["U"])  # the damping acts on this system
+    U = lambda **kw: polaris.polaris_energy(**{"pos": pos, "q": q, "qE": qE, "alpha": alpha,
+                                               "exclusions": excl, "thole": a, **kw})["U"]
+    rng = np.random.default_rng(10)
+    h = 1e-5
+    for i in rng.choice(np.nonzero(alpha > 0)[0], 4, replace=False):
+        for d in range(3):
+            xp, xm = pos.copy(), pos.copy()
+            xp[i, d] += h
+            xm[i, d] -= h
+            fd = -(U(pos=xp) - U(pos=xm)) / (2 * h)
+            assert abs(fd - ref["F"][i, d]) < 1e-6 * np.abs(ref["F"]).max()
+        ap, am = alpha.copy(), alpha.copy()
+        ap[i] += h
+        am[i] -= h
+        fd = (U(alpha=ap) - U(alpha=am)) / (2 * h)
+        assert abs(fd - ref["dUdalpha"][i]) < 1e-6 * np.abs(ref["dUdalpha"]).max()
+    # Newton's third law survives the damping
+    assert np.abs(ref["F"].sum(0)).max() < 1e-10 * np.abs(ref["F"]).max()
+
+
+def test_thole_fmm_correction_matches_the_damped_pair_sums():
+    """FMM over all pairs plus the damped-minus-undamped pair terms: exact when
+    every pair is in the near field (depth 1), and with a far field (depth 2)
+    no less accurate than the same FMM without damping."""
+    pos, q, qE, alpha, excl = _system(n=120, seed=5)
+    lo, side = oracle.root_box(pos)
+    a = polaris.polaris_energy(pos, q, qE, alpha, excl, thole=0.39)
+    b = polaris.polaris_energy(pos, q, qE, alpha, excl, method="fmm", p=8, depth=1, root=(lo, side), thole=0.39)
+    assert abs(a["U"] - b["U"]) < 1e-13 * abs(a["U"])
+    for k in ("F", "dUdalpha", "mu"):
+        assert oracle.rel_rms(b[k], a[k]) < 1e-12, k
+    err = {}
+    for th in (0.0, 0.39):
+        d = polaris.polaris_energy(pos, q, qE, alpha, excl, thole=th)
+        f = polaris.polaris_energy(pos, q, qE, alpha, excl, method="fmm", p=8, depth=2, root=(lo, side), thole=th)
+        err[th] = oracle.rel_rms(f["F"], d["F"])
+    assert 0.0 < err[0.39] < 1.5 * err[0.0]
