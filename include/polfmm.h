@@ -236,12 +236,23 @@ POLFMM_API int fmm_field_charge_gradient(polfmm_ctx* ctx, double* dU_dqE, int on
  * dU/dalpha; fmm_static_field, fmm_dipole_field and fmm_total_field keep
  * returning the undamped FMM fields.  The pairs with a u^3 < 40 (beyond,
  * exp(-a u^3) < 5e-18) are listed per tree with a spatial hash and corrected
- * with direct pair terms (damped minus undamped), in the mode's precision in
- * the solve and in FP64 for energy and gradients.  a = 0 switches it off;
+ * with direct pair terms (damped minus undamped), in the mode's precision
+ * (FP32 in MIXED).  a = 0 switches it off;
  * a < 0 or non-finite: POLFMM_ERR_INVALID_ARG.  Kept across
  * fmm_update_positions; the next solve starts from the current dipoles.
  */
 POLFMM_API int fmm_set_thole(polfmm_ctx* ctx, double a);
+
+/*
+ * Start of the next dipole solve after fmm_update_positions (a dipole
+ * predictor for molecular dynamics, Sec. IV.B warm-starts each step's solve
+ * from earlier dipoles): order 0 (default) starts from the last dipoles;
+ * order 1 extrapolates linearly from the last two updates,
+ * mu_start = 2 mu(t) - mu(t - dt), once two updates have been seen.
+ * fmm_set_dipoles and fmm_reset_dipoles restart the history.  Other orders:
+ * POLFMM_ERR_INVALID_ARG.
+ */
+POLFMM_API int fmm_set_dipole_predictor(polfmm_ctx* ctx, int order);
 
 /* New positions for the same sites: rebuild the tree and the static pass,
  * keeping the current dipoles as the next solve's starting guess. */
@@ -376,6 +387,11 @@ POLFMM_API int fmm_md_kinetic(polfmm_wall* wall, const double* velocities, const
  * conversion from force / mass to acceleration). */
 POLFMM_API int fmm_md_kick(double* velocities, const double* forces, const double* masses, double coef, int64_t n,
                            void* cuda_stream);
+
+/* Total momentum sum_i m_i v_i (three device doubles, fixed summation order),
+ * on the wall's stream and scratch. */
+POLFMM_API int fmm_md_momentum(polfmm_wall* wall, const double* velocities, const double* masses, int64_t n,
+                               double* momentum);
 
 /* Drift x_i += dt * v_i. */
 POLFMM_API int fmm_md_drift(double* positions, const double* velocities, double dt, int64_t n, void* cuda_stream);

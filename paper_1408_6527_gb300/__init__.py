@@ -187,6 +187,11 @@ class PolFMM:
         _lib.check(self.lib.fmm_set_exclusions(self.h, int(arr.shape[0]), arr.ctypes.data_as(ctypes.c_void_p), 0),
                    "fmm_set_exclusions")
 
+    def set_dipole_predictor(self, order):
+        """Start of the next solve after update_positions: 0 = last dipoles,
+        1 = linear extrapolation from the last two."""
+        _lib.check(self.lib.fmm_set_dipole_predictor(self.h, int(order)), "fmm_set_dipole_predictor")
+
     def set_thole(self, a):
         """Thole damping of the dipole-dipole interaction with parameter a (0 = off)."""
         _lib.check(self.lib.fmm_set_thole(self.h, float(a)), "fmm_set_thole")

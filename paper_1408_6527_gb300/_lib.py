@@ -66,6 +66,7 @@ SIGNATURES = {
     "fmm_set_exclusions": (I, [P, I64, P, I]),
     "fmm_field_charge_gradient": (I, [P, P, I]),
     "fmm_set_thole": (I, [P, D]),
+    "fmm_set_dipole_predictor": (I, [P, I]),
     "fmm_reset_dipoles": (I, [P]),
     "fmm_static_field": (I, [P, P, P, I]),
     "fmm_dipole_field": (I, [P, P, P, I]),
@@ -81,6 +82,7 @@ SIGNATURES = {
     "fmm_wall_create": (I, [ctypes.POINTER(P), I64, P]),
     "fmm_wall_forces": (I, [P, P, I64, D, D, P, P]),
     "fmm_md_kinetic": (I, [P, P, P, I64, D, P]),
+    "fmm_md_momentum": (I, [P, P, P, I64, P]),
     "fmm_md_kick": (I, [P, P, P, D, I64, P]),
     "fmm_md_drift": (I, [P, P, D, I64, P]),
     "fmm_wall_destroy": (None, [P]),

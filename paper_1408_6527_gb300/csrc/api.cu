@@ -23,6 +23,14 @@ int cuda_fail(cudaError_t e, const char* where) {
     snprintf(g_last_error, sizeof(g_last_error), "%s: %s (%s)", where, cudaGetErrorName(e), cudaGetErrorString(e));
     return POLFMM_ERR_CUDA;
 }
+// linear dipole prediction: cur <- 2 cur - hist, hist <- old cur
+__global__ void extrapolate_kernel(int64_t n3, double* __restrict__ cur, double* __restrict__ hist) {
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= n3) return;
+    const double v = cur[k];
+    cur[k] = 2.0 * v - hist[k];
+    hist[k] = v;
+}
 int fmm_ops_init_attributes(polfmm_ctx* c);
 size_t m2l_simt_smem(int ncoef, size_t rsize);
 int m2l_tensor_prepare(polfmm_ctx* c);
@@ -682,6 +690,8 @@ void destroy_impl(polfmm_ctx* c) {
     free_tables(c->tab);
     if (c->tiles) cudaFree(c->tiles);
     if (c->th_idx) cudaFree(c->th_idx);
+    if (c->th_r) cudaFree(c->th_r);
+    if (c->th_t3) cudaFree(c->th_t3);
     if (c->h_scal) cudaFreeHost(c->h_scal);
     if (c->h_counts) cudaFreeHost(c->h_counts);
     if (c->h_bbox) cudaFreeHost(c->h_bbox);
@@ -946,12 +956,14 @@ int fmm_set_dipoles(polfmm_ctx* c, const double* mu, int on_device) {
     gather_sites(c, c->in_buf + 5 * c->n, c->mu, 3);
     mask_dipoles(c, c->mu);
     c->have_mu = true;
+    c->have_hist = false;  // the predictor's history restarts
     return read_err(c);
 }
 
 int fmm_reset_dipoles(polfmm_ctx* c) {
     if (!c) return POLFMM_ERR_INVALID_ARG;
     c->have_mu = false;
+    c->have_hist = false;
     return POLFMM_OK;
 }
 
@@ -1049,6 +1061,21 @@ int fmm_set_exclusions(polfmm_ctx* c, int64_t npairs, const int32_t* pairs, int 
     return read_err(c);
 }
 
+int fmm_set_dipole_predictor(polfmm_ctx* c, int order) {
+    if (!c || order < 0 || order > 1) return POLFMM_ERR_INVALID_ARG;
+    if (order == 1 && !c->mu_hist) {
+        Alloc& A = extra_of(c)->alloc;
+        c->mu_hist = A.get<double>(3 * c->n);
+        if (!A.ok) {
+            c->mu_hist = nullptr;
+            return POLFMM_ERR_OUT_OF_MEMORY;
+        }
+    }
+    c->predictor = order;
+    c->have_hist = false;
+    return POLFMM_OK;
+}
+
 int fmm_set_thole(polfmm_ctx* c, double a) {
     if (!c || !(a >= 0.0) || !isfinite(a)) return POLFMM_ERR_INVALID_ARG;
     if (a > 0.0 && !c->a16) {
@@ -1058,6 +1085,7 @@ int fmm_set_thole(polfmm_ctx* c, double a) {
         Alloc& A = extra_of(c)->alloc;
         c->th_nb = nb;
         c->a16 = A.get<double>(n);
+        c->th_xa = A.get<float4>(n);
         c->th_bucket = A.get<int>(nb + 1);
         c->th_count = A.get<int>(nb);
         c->th_member = A.get<int>(n);
@@ -1095,7 +1123,19 @@ int fmm_update_positions(polfmm_ctx* c, const double* positions, int on_device) 
     // current q, alpha and dipoles back to caller order, then the new positions
     scatter_sites(c, c->q_s, c->in_buf + 3 * n, 1);
     scatter_sites(c, c->alpha_s, c->in_buf + 4 * n, 1);
-    if (c->have_mu) scatter_sites(c, c->mu, c->in_buf + 5 * n, 3);
+    if (c->have_mu) {
+        scatter_sites(c, c->mu, c->in_buf + 5 * n, 3);
+        if (c->predictor == 1) {
+            if (c->have_hist) {
+                LaunchScope ls(c, F_SOLVER);
+                extrapolate_kernel<<<grid_for(3 * n, 256), 256, 0, c->stream>>>(3 * n, c->in_buf + 5 * n, c->mu_hist);
+            } else {
+                cudaMemcpyAsync(c->mu_hist, c->in_buf + 5 * n, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice,
+                                c->stream);
+                c->have_hist = true;
+            }
+        }
+    }
     if (c->qE_s) scatter_sites(c, c->qE_s, c->in_buf + 8 * n, 1);
     c->have_dqE = false;
     int rc = copy_in(c, c->in_buf, positions, 3 * (size_t)n, on_device);

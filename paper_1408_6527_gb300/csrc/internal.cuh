@@ -217,10 +217,16 @@ struct polfmm_ctx {
     // (CSR over sorted sites, partners in sorted order), alpha^(1/6) per sorted
     // site, the hash scratch, and the force-pass corrections (sorted order)
     double thole_a = 0.0;
+    int predictor = 0;            // dipole predictor order for fmm_update_positions
+    double* mu_hist = nullptr;    // [3n] caller order: the dipoles of the update before
+    bool have_hist = false;
     int* th_ptr = nullptr;        // [n + 1]
     int* th_idx = nullptr;        // [th_cap]
     int64_t th_cap = 0, th_npairs = 0;
     double* a16 = nullptr;        // [n]
+    float4* th_xa = nullptr;      // [n] position and alpha^(1/6) in FP32 (the pair search)
+    float4* th_r = nullptr;       // [th_cap] MIXED: r_ij and 3 (lambda5 - 1) / r^5 per pair
+    float* th_t3 = nullptr;       // [th_cap] MIXED: (lambda3 - 1) / r^3 per pair
     int* th_bucket = nullptr;     // [th_nb + 1] bucket starts
     int* th_count = nullptr;      // [th_nb] bucket counts
     int* th_member = nullptr;     // [n] sites grouped by bucket

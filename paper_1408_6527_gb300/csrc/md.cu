@@ -335,6 +335,30 @@ extern "C" POLFMM_API int fmm_md_drift(double* positions, const double* velociti
     return e == cudaSuccess ? POLFMM_OK : cuda_fail(e, "drift kernel launch");
 }
 
+// site i's momentum component k, m_i v_ik
+__global__ void momentum_site_kernel(const double* __restrict__ v, const double* __restrict__ m, int64_t n, int k,
+                                     double* __restrict__ e) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    e[i] = m[i] * v[3 * i + k];
+}
+
+extern "C" POLFMM_API int fmm_md_momentum(polfmm_wall* w, const double* velocities, const double* masses, int64_t n,
+                                          double* momentum) {
+    if (!w || n < 0 || n > w->cap || !momentum || (n > 0 && (!velocities || !masses))) return POLFMM_ERR_INVALID_ARG;
+    cudaStream_t st = w->stream;
+    if (n == 0) {
+        cudaError_t e = cudaMemsetAsync(momentum, 0, 3 * sizeof(double), st);
+        return e == cudaSuccess ? POLFMM_OK : cuda_fail(e, "momentum memset");
+    }
+    for (int k = 0; k < 3; k++) {
+        momentum_site_kernel<<<grid_for(n, 256), 256, 0, st>>>(velocities, masses, n, k, w->e_site);
+        int rc = sum_to(st, w->e_site, n, 1.0, w->part, momentum + k);
+        if (rc != POLFMM_OK) return rc;
+    }
+    return POLFMM_OK;
+}
+
 extern "C" POLFMM_API int fmm_md_kinetic(polfmm_wall* w, const double* velocities, const double* masses, int64_t n,
                                          double scale, double* energy) {
     if (!w || n < 0 || n > w->cap || !energy || (n > 0 && (!velocities || !masses))) return POLFMM_ERR_INVALID_ARG;

@@ -128,6 +128,19 @@ class Repulsion:
                                            self._ptr(out)), "fmm_md_kinetic")
         return out
 
+    def momentum(self, v, m):
+        """Total momentum sum m v as a device tensor of three."""
+        import torch
+
+        from . import _lib
+
+        self._check_f8(v, m)
+        self._reserve(int(v.shape[0]))
+        out = torch.empty(3, dtype=torch.float64, device="cuda")
+        _lib.check(self.lib.fmm_md_momentum(self.h, self._ptr(v), self._ptr(m), int(v.shape[0]), self._ptr(out)),
+                   "fmm_md_momentum")
+        return out
+
     def close(self):
         if self.h is not None:
             self.lib.fmm_wall_destroy(self.h)
@@ -153,7 +166,7 @@ class Dynamics:
     kick(v, F, m, coef), drift(x, v, dt) and kinetic(v, m, scale): by default
     the library's CUDA kernels (Repulsion)."""
 
-    def __init__(self, pos, q, alpha, masses, p=6, depth=5, mode="fp64", tol=1e-8, ops=None):
+    def __init__(self, pos, q, alpha, masses, p=6, depth=5, mode="fp64", tol=1e-8, ops=None, predictor=0):
         import torch
 
         from . import PolFMM
@@ -166,7 +179,10 @@ class Dynamics:
         self.ops = ops or Repulsion(capacity=self.x.shape[0])
         self.fmm = PolFMM(self.x, self.q, self.alpha, p=p, depth=depth, mode=mode, coulomb_k=COULOMB,
                           max_iter=500)
+        if predictor:
+            self.fmm.set_dipole_predictor(predictor)
         self.iterations = []
+        self.momenta = []
         self.start()
 
     def start(self):
@@ -213,22 +229,27 @@ class Dynamics:
         self.Us, self.Fs = self._slow()
         self.ops.kick(v, self.Fs, self.m, c_out)
 
-    def run(self, v, steps, dt=1.0, inner=1, multistep=None):
+    def run(self, v, steps, dt=1.0, inner=1, multistep=None, track_momentum=False):
         """Returns the total energy before and after each step (kcal/mol) and the
         final velocities (a new tensor; v itself is not changed).  A step is
         velocity Verlet at dt when inner == 1 (unless multistep=True), else one
-        multiple-time-step outer step of inner * dt."""
+        multiple-time-step outer step of inner * dt.  track_momentum: the total
+        momentum after each step goes to self.momenta."""
         import torch
 
         multistep = inner > 1 if multistep is None else bool(multistep)
         v = torch.as_tensor(v, dtype=torch.float64, device=self.x.device).clone().contiguous()
         H = [self.total(v)]
+        if track_momentum:
+            self.momenta.append(self.ops.momentum(v, self.m).cpu().numpy())
         for _ in range(steps):
             if multistep:
                 self._respa_step(v, dt, inner)
             else:
                 self._verlet_step(v, dt)
             H.append(self.total(v))
+            if track_momentum:
+                self.momenta.append(self.ops.momentum(v, self.m).cpu().numpy())
         return np.array(H), v
 
     def close(self):
@@ -307,6 +328,8 @@ def main(argv=None):
     ap.add_argument("--temperature", type=float, default=300.0)
     ap.add_argument("--fd-sites", type=int, default=64)
     ap.add_argument("--alpha-scale", type=float, default=0.5)
+    ap.add_argument("--predictor", type=int, default=0, choices=[0, 1],
+                    help="start of each solve: 0 = last dipoles, 1 = linear extrapolation from the last two")
     ap.add_argument("--seed", type=int, default=7)
     args = ap.parse_args(argv)
     w = synth.workload(4, n=args.sites)
@@ -317,18 +340,19 @@ def main(argv=None):
                          "dt_fs": args.dt, "inner_steps": args.inner, "temperature_K": args.temperature,
                          "masses_amu": "U(1, 16)",
                          "repulsion": "repulsive Lennard-Jones wall, eps 5 kcal/mol, sigma 2.05 A, zero beyond 2.30 A",
-                         "alpha_scale_dynamics": args.alpha_scale}}
+                         "alpha_scale_dynamics": args.alpha_scale, "dipole_predictor": args.predictor}}
     if args.fd_sites > 0:
         t0 = time.perf_counter()
         result["fd_check"] = {"sites": args.fd_sites, "h": 1e-5,
                               "max_rel_diff": fd_check(w.pos, w.q, w.alpha, w.p, w.depth, args.fd_sites),
                               "seconds": round(time.perf_counter() - t0, 1)}
     for mode, tol in (("fp64", 1e-8), ("mixed", 1e-6)):
-        dyn = Dynamics(w.pos, w.q, args.alpha_scale * w.alpha, masses, p=w.p, depth=w.depth, mode=mode, tol=tol)
+        dyn = Dynamics(w.pos, w.q, args.alpha_scale * w.alpha, masses, p=w.p, depth=w.depth, mode=mode, tol=tol,
+                       predictor=args.predictor)
         v = torch.as_tensor(v0, dtype=torch.float64, device="cuda")
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        H, v = dyn.run(v, args.steps, args.dt, args.inner)
+        H, v = dyn.run(v, args.steps, args.dt, args.inner, track_momentum=True)
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
         ke0 = float(0.5 * (masses[:, None] * v0 * v0).sum() / ACC)
@@ -338,6 +362,9 @@ def main(argv=None):
                         "max_dev_of_ke0": float(np.abs(H - H[0]).max() / ke0),
                         "mean_iterations": float(np.mean(dyn.iterations[1:])) if len(dyn.iterations) > 1 else None,
                         "ms_per_step": round(1e3 * dt / max(1, args.steps), 2),
+                        # centre-of-mass momentum: largest |P(t) - P(0)| over sum m |v(0)|
+                        "momentum_drift": float(np.abs(np.array(dyn.momenta) - dyn.momenta[0]).max()
+                                                / (masses * np.linalg.norm(v0, axis=1)).sum()),
                         "finite": bool(np.all(np.isfinite(H)))}
         dyn.close()
     print(json.dumps(result))

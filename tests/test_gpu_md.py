@@ -191,3 +191,51 @@ def test_autograd_matches_finite_differences_at_the_100k_globule():
     assert worst["x"] < 1e-5, worst
     assert worst["q"] < 1e-5, worst
     assert worst["alpha"] < 1e-5, worst
+
+
+def test_momentum_kernel():
+    rng = np.random.default_rng(8)
+    n = 3001
+    v, m = rng.standard_normal((n, 3)), rng.uniform(1.0, 16.0, n)
+    ops = md.Repulsion(capacity=n)
+    P = ops.momentum(_dev(v), _dev(m)).cpu().numpy()
+    ref = (m[:, None] * v).sum(0)
+    assert np.abs(P - ref).max() <= 1e-12 * np.abs(m[:, None] * v).sum()
+
+
+def test_linear_dipole_predictor_starts_from_the_extrapolation():
+    w, masses, v0 = _system()
+    from paper_1408_6527_gb300 import PolFMM
+
+    x = _dev(w.pos)
+    with PolFMM(x, _dev(w.q), _dev(0.5 * w.alpha), p=w.p, depth=w.depth, coulomb_k=md.COULOMB) as f:
+        f.set_dipole_predictor(1)
+        f.solve(1e-10)
+        mus = [f.dipoles().cpu().numpy()]
+        for k in range(2):
+            x = x + 0.01 * _dev(v0)
+            f.update_positions(x)
+            start = f.dipoles().cpu().numpy()
+            if k == 0:  # one update seen: the last dipoles
+                np.testing.assert_array_equal(start, mus[-1])
+            else:       # two: 2 mu(t) - mu(t - dt), bit for bit
+                np.testing.assert_array_equal(start, 2.0 * mus[-1] - mus[-2])
+            f.solve(1e-10)
+            mus.append(f.dipoles().cpu().numpy())
+
+
+def test_predictor_saves_iterations_and_momentum_is_conserved():
+    w, masses, v0 = _system()
+    res = {}
+    for pred in (0, 1):
+        dyn = md.Dynamics(w.pos, w.q, 0.5 * w.alpha, masses, p=w.p, depth=w.depth, mode="fp64", tol=1e-8,
+                          predictor=pred)
+        H, _ = dyn.run(_dev(v0), 30, dt=0.5, track_momentum=True)
+        P = np.array(dyn.momenta)
+        scale = (masses * np.linalg.norm(v0, axis=1)).sum()
+        res[pred] = (float(np.mean(dyn.iterations[3:])), float(np.abs(P - P[0]).max() / scale),
+                     float(np.abs(H - H[0]).max()))
+        dyn.close()
+    print("mean iterations (no predictor, linear predictor), momentum drift, energy excursion:", res)
+    assert res[1][0] < res[0][0]
+    assert res[0][1] < 1e-3 and res[1][1] < 1e-3
