@@ -348,6 +348,32 @@ POLFMM_API int fmm_sort_sites_noalloc(int64_t n, const double* positions, int tr
                                       void* cuda_stream);
 
 /*
+ * The paper's own tree and walk (Sec. III), in FP64: potential, field and
+ * field gradient at every site from charges and point dipoles, by an FMM on
+ * an adaptive kd-tree.  A cell's particles split across the longest dimension
+ * of their box, at their geometric centre along it, until a cell holds at most
+ * n_bucket particles (8 in the paper); every cell expands about the centre of
+ * its particles, with r_enc the distance to the farthest corner of its box
+ * (padded by `pad` Angstrom on every side below three particles).  A mutual
+ * dual-tree walk from (root, root) sums a pair directly when it holds fewer
+ * than n_direct particles (about 64 in the paper) or both cells are leaves,
+ * through multipoles when theta |z_A - z_B| > r_enc,A + r_enc,B (Eq. mac), and
+ * otherwise splits the cell with the larger r_enc (a self pair pushes its
+ * three child combinations).  Expansions keep |n| + |m| <= order_p (1..7);
+ * dipole_dl > 0 builds the dipoles' multipoles from the +-q pairs of Sec.
+ * II.C.  charges, dipoles and any output may be NULL.  stats (nullable)
+ * receives 5 counts: cells, leaves, levels, multipole pairs, direct pairs.
+ * Deterministic; allocates and frees its own device memory; synchronises
+ * cuda_stream.  Each site's own term is excluded (Sec. II.A).  0 <= theta < 1
+ * (0: every pair direct),
+ * n_bucket >= 1: POLFMM_ERR_INVALID_ARG otherwise.
+ */
+POLFMM_API int fmm_kdtree_fields(int64_t n, const double* positions, const double* charges, const double* dipoles,
+                                 int order_p, double theta, int n_bucket, int n_direct, double pad, double dipole_dl,
+                                 double* phi, double* E, double* G, int64_t* stats, void* cuda_stream,
+                                 int on_device);
+
+/*
  * Dynamics around the FMM (Sec. IV.B runs molecular dynamics on these forces,
  * with the long-range part on a longer time step than the short-range part).
  * The paper's force field has short-range terms of its own, which are not part

@@ -255,6 +255,37 @@ class PolFMM:
         return int(self.lib.fmm_launch_count(self.h))
 
 
+def kdtree_fields(pos, q=None, mu=None, p=5, theta=0.5, n_bucket=8, n_direct=64, pad=1e-3, dipole_dl=0.0,
+                  stream=None):
+    """Phi, E, G at every site by the adaptive kd-tree FMM of Sec. III on the
+    GPU (FP64, fmm_kdtree_fields), and the walk's counts."""
+    lib = _lib.load()
+    device = _is_torch(pos) and pos.is_cuda
+    n = int(pos.shape[0])
+    if stream is None and device:
+        import torch
+
+        stream = torch.cuda.current_stream().cuda_stream
+    bx = _Buf(pos, device, shape=(n, 3))
+    bq = _Buf(q, device, shape=(n,)) if q is not None else None
+    bm = _Buf(mu, device, shape=(n, 3)) if mu is not None else None
+    if device:
+        import torch
+
+        outs = [torch.empty(s, dtype=torch.float64, device="cuda") for s in ((n,), (n, 3), (n, 6))]
+        ptrs = [ctypes.c_void_p(t.data_ptr()) for t in outs]
+    else:
+        outs = [np.empty(s) for s in ((n,), (n, 3), (n, 6))]
+        ptrs = [a.ctypes.data_as(ctypes.c_void_p) for a in outs]
+    stats = np.zeros(5, dtype=np.int64)
+    _lib.check(lib.fmm_kdtree_fields(n, bx.ptr, bq.ptr if bq else None, bm.ptr if bm else None, int(p), float(theta),
+                                     int(n_bucket), int(n_direct), float(pad), float(dipole_dl), *ptrs,
+                                     stats.ctypes.data_as(ctypes.c_void_p), ctypes.c_void_p(stream or 0),
+                                     int(device)), "fmm_kdtree_fields")
+    return {"phi": outs[0], "E": outs[1], "G": outs[2],
+            "stats": dict(zip(("cells", "leaves", "levels", "multipole_pairs", "direct_pairs"), stats.tolist()))}
+
+
 def measure_peak(kind: str, stream=None) -> float:
     """Measured FP32 ("fp32") or FP64 ("fp64") fused multiply-add peak of the
     current device in TFLOP/s (for roofline fractions)."""

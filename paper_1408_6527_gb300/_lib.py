@@ -79,6 +79,7 @@ SIGNATURES = {
     "fmm_launch_count": (I64, [P]),
     "fmm_testing_alloc_hook": (I64, [I64]),
     "fmm_measure_peak": (I, [I, P, ctypes.POINTER(D)]),
+    "fmm_kdtree_fields": (I, [I64, P, P, P, I, D, I, I, D, D, P, P, P, P, P, I]),
     "fmm_wall_create": (I, [ctypes.POINTER(P), I64, P]),
     "fmm_wall_forces": (I, [P, P, I64, D, D, P, P]),
     "fmm_md_kinetic": (I, [P, P, P, I64, D, P]),
