@@ -53,7 +53,6 @@ def tol_for(mode, n):
 # command and the figures are in profiles/); the line reports null for any
 # other kernel, workload or mode
 TRAFFIC = {
-    ("m2l", "globule", 30000, "mixed"): 5171000,          # profiles/launches_globule30k_mixed.md
     ("leaf_dipole", "globule", 30000, "mixed"): 1580000,
     ("p2m", "globule", 30000, "mixed"): 1149000,
     ("l2p", "globule", 30000, "mixed"): 7221000,
@@ -68,7 +67,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--mode", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
-    ap.add_argument("--m2l", default="auto", choices=["auto", "simt", "tensor"])
+    ap.add_argument("--m2l", default="auto", choices=["auto", "simt", "tensor", "ffma"])
     ap.add_argument("--workload", default="globule30k",
                     choices=["globule30k", "cube1k", "ring300k", "globule100k", "shell250k", "shell1M", "shell4M"],
                     help="workload (the default is the one the headline metric is quoted on)")
@@ -155,7 +154,17 @@ def radix_passes(depth):
     return (3 * depth + 7) // 8
 
 
-def family_work(w, n, near_pairs, box_pairs, nbox, mixed, iterations):
+def m2l_kernel(p, mixed, impl):
+    """The M2L kernel the library runs: FP32 FMAs on the CUDA cores (MIXED, p <= 6,
+    auto or ffma), tcgen05 TF32 (MIXED otherwise, unless simt), or the SIMT kernel."""
+    if not mixed:
+        return "simt"
+    if impl in ("auto", "ffma") and p <= 6:
+        return "ffma"
+    return "simt" if impl == "simt" else "tensor"
+
+
+def family_work(w, n, near_pairs, box_pairs, nbox, mixed, iterations, m2l_impl="auto"):
     """Algorithmic work of one launch of each kernel family (flops or bytes),
     with the bound it is measured against.  Counted from the tree and the
     operators, not from the kernels."""
@@ -168,7 +177,9 @@ def family_work(w, n, near_pairs, box_pairs, nbox, mixed, iterations):
     out = {
         # per solver pass: dipole field of the sources, 34 flops per ordered pair
         "leaf_dipole": (near_pairs * 34, "alu", alu, "34 flops per ordered near pair (dipole -> field)"),
-        "m2l": (box_pairs * m2l_flops_per_box_pair(p), "tensor" if mixed else "alu", "tf32" if mixed else "fp64",
+        "m2l": (box_pairs * m2l_flops_per_box_pair(p),
+                "tensor" if m2l_kernel(p, mixed, m2l_impl) == "tensor" else "alu",
+                {"tensor": "tf32", "ffma": "fp32", "simt": alu}[m2l_kernel(p, mixed, m2l_impl)],
                 f"{m2l_flops_per_box_pair(p)} flops per box pair (sum over |n|+|m| <= p of 2)"),
         # P2M of the dipoles (8 flops per site and coefficient) and M2M of every box below level 2
         "p2m": (n * nc * 8 + inner * m2m_flops_per_box(p), "alu", alu,
@@ -195,9 +206,19 @@ def family_work(w, n, near_pairs, box_pairs, nbox, mixed, iterations):
     return out
 
 
+def _morton3(x, y, z):
+    key = np.zeros(x.shape, dtype=np.int64)
+    for b in range(10):
+        key |= (((x >> b) & 1) << (3 * b)) | (((y >> b) & 1) << (3 * b + 1)) | (((z >> b) & 1) << (3 * b + 2))
+    return key
+
+
 def tree_work(pos, depth, lo, side):
-    """Near-field pairs (ordered, i != j, adjacent leaves) and far-field box
-    pairs (the 189-offset interaction lists, occupied sources only)."""
+    """Near-field pairs (ordered, i != j, adjacent leaves), far-field box pairs
+    (the 189-offset interaction lists, occupied sources only), tensor-core tiles,
+    and the entries of the FP32 CUDA-core M2L: per group of 32 boxes of one
+    octant class (levels >= 2 coarse first, Morton order within a level), the
+    offsets with at least one occupied source."""
     ns = 1 << depth
     h = side / ns
     cell = np.clip(np.floor((pos - lo) / h).astype(np.int64), 0, ns - 1)
@@ -212,28 +233,39 @@ def tree_work(pos, depth, lo, side):
     near_pairs = int(np.sum(cnt * nb) - pos.shape[0])
     box_pairs = 0
     class_rows = np.zeros(8, dtype=np.int64)
+    offsets = [(ox, oy, oz) for oz in range(-3, 4) for oy in range(-3, 4) for ox in range(-3, 4)
+               if max(abs(ox), abs(oy), abs(oz)) > 1]
+    present = [[] for _ in range(8)]  # per class: [rows, 343-grid offsets] occupancy of the source
     for l in range(2, depth + 1):
         m = 1 << l
         occ = np.zeros((m, m, m), dtype=bool)
         c = cell >> (depth - l)
         occ[c[:, 0], c[:, 1], c[:, 2]] = True
         tx, ty, tz = np.nonzero(occ)
-        class_rows += np.bincount((tx & 1) + 2 * (ty & 1) + 4 * (tz & 1), minlength=8)
-        for ox in range(-3, 4):
-            for oy in range(-3, 4):
-                for oz in range(-3, 4):
-                    if max(abs(ox), abs(oy), abs(oz)) <= 1:
-                        continue
-                    ok = np.ones(tx.shape, dtype=bool)
-                    for t, o in ((tx, ox), (ty, oy), (tz, oz)):
-                        b = t & 1
-                        ok &= (o >= b - 3) & (o <= b + 2)
-                    sx, sy, sz = tx - ox, ty - oy, tz - oz
-                    ok &= (sx >= 0) & (sy >= 0) & (sz >= 0) & (sx < m) & (sy < m) & (sz < m)
-                    ok[ok] &= occ[sx[ok], sy[ok], sz[ok]]
-                    box_pairs += int(ok.sum())
+        order = np.argsort(_morton3(tx, ty, tz), kind="stable")
+        tx, ty, tz = tx[order], ty[order], tz[order]
+        cls = (tx & 1) + 2 * (ty & 1) + 4 * (tz & 1)
+        class_rows += np.bincount(cls, minlength=8)
+        pres = np.zeros((tx.shape[0], len(offsets)), dtype=bool)
+        for j, (ox, oy, oz) in enumerate(offsets):
+            ok = np.ones(tx.shape, dtype=bool)
+            for t, o in ((tx, ox), (ty, oy), (tz, oz)):
+                b = t & 1
+                ok &= (o >= b - 3) & (o <= b + 2)
+            sx, sy, sz = tx - ox, ty - oy, tz - oz
+            ok &= (sx >= 0) & (sy >= 0) & (sz >= 0) & (sx < m) & (sy < m) & (sz < m)
+            ok[ok] &= occ[sx[ok], sy[ok], sz[ok]]
+            box_pairs += int(ok.sum())
+            pres[:, j] = ok
+        for k in range(8):
+            present[k].append(pres[cls == k])
     tc_tiles = int(sum((r + 127) // 128 for r in class_rows))
-    return near_pairs, box_pairs, tc_tiles
+    ffma_entries = 0
+    for k in range(8):
+        pk = np.concatenate(present[k]) if present[k] else np.zeros((0, len(offsets)), dtype=bool)
+        for g in range(0, pk.shape[0], 32):
+            ffma_entries += int(pk[g:g + 32].any(axis=0).sum())
+    return near_pairs, box_pairs, tc_tiles, ffma_entries
 
 
 # ---------------------------------------------------------------------------
@@ -459,7 +491,7 @@ def run_gpu(args, rank, world, local_rank):
     prof_total = sum(v[0] for v in prof.values())
 
     # roofline of every kernel family against its own measured peak
-    near_pairs, box_pairs, tc_tiles = tree_work(w.pos, w.depth, lo, side)
+    near_pairs, box_pairs, tc_tiles, ffma_entries = tree_work(w.pos, w.depth, lo, side)
     hbm_peak, bf16_burst, bf16_sust, peak_src = load_peaks()
     p = w.p
     mixed = args.mode == "mixed"
@@ -476,7 +508,7 @@ def run_gpu(args, rank, world, local_rank):
                  f"TF32 dense = {peak_src} burst bf16 {bf16_burst} x nominal TF32/BF16 1.1/2.25"),
         "hbm": (hbm_peak, "GB/s", f"{peak_src} HBM copy"),
     }
-    work = family_work(w, n, near_pairs, box_pairs, nbox, mixed, prof_iters / nprof)
+    work = family_work(w, n, near_pairs, box_pairs, nbox, mixed, prof_iters / nprof, args.m2l)
     roofs = {}
     for fam, (units, bound, pk, note) in work.items():
         ms, nl = prof[fam]
@@ -495,12 +527,19 @@ def run_gpu(args, rank, world, local_rank):
              "avg_launch_ms": round(ms / nl, 4), "launches_per_step": round(nl / nprof, 2),
              ("algorithmic_bytes_per_unit" if bound == "hbm" else "algorithmic_flops_per_launch"): int(units),
              "share_of_step": round(ms / prof_total, 4)}
-        if fam == "m2l" and mixed:
+        if fam == "m2l" and m2l_kernel(p, mixed, args.m2l) == "tensor":
             # what the kernel issues: three TF32 products over the block-sparse MMA
             # schedule on every tile row, present or not
             issued = 3 * 2 * 128 * tc_issued_macs_per_row(p) * tc_tiles * 189
             r["issued_tensor_tflops"] = round(issued / dur_s / 1e12, 3)
             r["issued_tensor_frac"] = round(issued / dur_s / 1e12 / peaks["tf32"][0], 5)
+        if fam == "m2l" and m2l_kernel(p, mixed, args.m2l) == "ffma":
+            # what the kernel issues: every lane of a group runs the whole
+            # contraction for each offset where any of the group's sources exists
+            issued = 32 * m2l_flops_per_box_pair(p) * ffma_entries
+            r["issued_fp32_tflops"] = round(issued / dur_s / 1e12, 3)
+            r["issued_fp32_frac"] = round(issued / dur_s / 1e12 / peaks["fp32"][0], 5)
+            r["lane_fill"] = round(box_pairs / (32 * ffma_entries), 4) if ffma_entries else None
         roofs[fam] = r
     dom = max(roofs, key=lambda f: prof[f][0]) if roofs else None
     roof = roofs.get(dom)
@@ -543,7 +582,8 @@ def run_gpu(args, rank, world, local_rank):
                           "graph, no near/far overlap): proportions, whose sum exceeds the graph-launched step",
         "kernel_share": {f: round(v[0] / prof_total, 4) for f, v in prof.items()} if prof_total > 0 else None,
         "roofline": roof, "roofline_kernels": roofs, "clocks": clocks, "e2e": e2e,
-        "tree": {"near_pairs": near_pairs, "m2l_box_pairs": box_pairs, "tc_tiles": tc_tiles, "boxes": nbox},
+        "tree": {"near_pairs": near_pairs, "m2l_box_pairs": box_pairs, "tc_tiles": tc_tiles,
+                 "ffma_entries": ffma_entries, "boxes": nbox},
         "peaks": {k: {"value": round(v[0], 2), "unit": v[1], "source": v[2]} for k, v in peaks.items()},
     }
     if world == 1 and not args.no_cpu:

@@ -66,10 +66,16 @@ extern "C" {
 #define POLFMM_SOLVER_PCG 0    /* conjugate gradients on (diag(1/alpha) - T) mu = E^q, Jacobi preconditioner */
 #define POLFMM_SOLVER_JACOBI 1 /* fixed point mu <- alpha (E^q + T mu) */
 
-/* Multipole-to-local implementation (MIXED only; FP64 always uses the SIMT kernel). */
+/* Multipole-to-local implementation (MIXED only; FP64 always uses the SIMT kernel).
+ * AUTO: FFMA for p <= 6, TENSOR for p = 7, 8.
+ * SIMT: the generic kernel (32-box tiles, accumulators in shared memory).
+ * TENSOR: tcgen05 TF32 tensor cores with three products (FP32-level accuracy).
+ * FFMA (p <= 6; otherwise as AUTO): FP32 on the CUDA cores, one target box per lane
+ * with its coefficients in registers. */
 #define POLFMM_M2L_AUTO 0
 #define POLFMM_M2L_SIMT 1
 #define POLFMM_M2L_TENSOR 2
+#define POLFMM_M2L_FFMA 3
 
 typedef struct polfmm_ctx polfmm_ctx; /* opaque; owned by the library */
 

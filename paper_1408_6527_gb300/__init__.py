@@ -15,14 +15,14 @@ import ctypes
 import numpy as np
 
 from . import _lib
-from ._lib import (FP64, M2L_AUTO, M2L_SIMT, M2L_TENSOR, MIXED, SOLVER_JACOBI, SOLVER_PCG, Options,
+from ._lib import (FP64, M2L_AUTO, M2L_FFMA, M2L_SIMT, M2L_TENSOR, MIXED, SOLVER_JACOBI, SOLVER_PCG, Options,
                    PolFMMError)
 
 __all__ = ["PolFMM", "PolFMMError", "build", "polarizable_energy", "FP64", "MIXED"]
 
 _MODES = {"fp64": FP64, "mixed": MIXED, FP64: FP64, MIXED: MIXED}
 _SOLVERS = {"pcg": SOLVER_PCG, "jacobi": SOLVER_JACOBI}
-_M2L = {"auto": M2L_AUTO, "simt": M2L_SIMT, "tensor": M2L_TENSOR}
+_M2L = {"auto": M2L_AUTO, "simt": M2L_SIMT, "tensor": M2L_TENSOR, "ffma": M2L_FFMA}
 
 
 def build(force: bool = False) -> str:

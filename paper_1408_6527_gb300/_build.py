@@ -10,7 +10,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 OBJDIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libpolfmm.so")
-SOURCES = ["api.cu", "tree.cu", "fmm_ops.cu", "solver.cu", "m2l_tc.cu", "peaks.cu", "polaris.cu", "md.cu", "kdtree.cu"]
+SOURCES = ["api.cu", "tree.cu", "fmm_ops.cu", "solver.cu", "m2l_tc.cu", "peaks.cu", "polaris.cu", "md.cu", "kdtree.cu", "m2l_ffma.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # -ftz=true: single-precision denormals flush to zero (the FP32 path works on
 # normalised O(1) coefficients and 1/r powers far from the denormal range)

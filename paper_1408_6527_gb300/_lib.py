@@ -25,6 +25,7 @@ SOLVER_JACOBI = 1
 M2L_AUTO = 0
 M2L_SIMT = 1
 M2L_TENSOR = 2
+M2L_FFMA = 3
 NOALLOC_MAX_SITES = 262144
 
 

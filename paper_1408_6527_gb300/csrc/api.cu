@@ -370,7 +370,8 @@ int allocate(polfmm_ctx* c) {
         c->mrow0[l] = mrows;
         mrows += std::min<int64_t>((int64_t)1 << (3 * l), n);
     }
-    c->Mall = A.get<unsigned char>((size_t)mrows * c->ld * rsz);
+    c->mrow_zero = mrows;  // one more row, kept at zero: the source of an empty box
+    c->Mall = A.get<unsigned char>((size_t)(mrows + 1) * c->ld * rsz);
     for (int l = 0; l <= c->depth; l++) {
         Level& B = c->lv[l];
         int64_t full = (int64_t)1 << (3 * l);
@@ -534,6 +535,7 @@ int rebuild(polfmm_ctx* c) {
         if (rc == POLFMM_ERR_CUDA) cuda_fail(cudaGetLastError(), "tensor-core M2L set-up");
         return rc;
     }
+    if ((rc = m2l_ffma_prepare(c)) != POLFMM_OK) return rc;  // sets the chunk count when it runs
     if ((rc = ensure_lp(c)) != POLFMM_OK) return rc;
     if (c->qE_s) gather_sites(c, c->in_buf + 8 * n, c->qE_s, 1);
     exclusion_inv_perm(c);
@@ -687,6 +689,7 @@ void destroy_impl(polfmm_ctx* c) {
         for (void* p : X->lp_bufs) cudaFree(p);
     }
     m2l_tensor_release(c);
+    m2l_ffma_release(c);
     free_tables(c->tab);
     if (c->tiles) cudaFree(c->tiles);
     if (c->th_idx) cudaFree(c->th_idx);

@@ -105,7 +105,7 @@ __device__ inline void store_multipole(const UpPtrs& up, int l, int box, int cc,
 // so that m_n = sum_i A_x[nx] P_y[ny] P_z[nz] - P_x[nx] (D_y[ny] P_z[nz] + P_y[ny] D_z[nz])
 enum { F_PX = 0, F_PY, F_PZ, F_AX, F_DY, F_DZ, F_NUM };
 
-template <typename R>
+template <typename R, bool PAIRS>
 __global__ void __launch_bounds__(kUpThreads) upward_kernel(
     int nleaf, int depth, const int* __restrict__ lstart, const int* __restrict__ lcount,
     const R* __restrict__ ploc, const double* __restrict__ q, const double* __restrict__ mu, UpPtrs up, int ld,
@@ -145,8 +145,9 @@ __global__ void __launch_bounds__(kUpThreads) upward_kernel(
     }
     // P2M entries: one per site; with dipoles as +-q pairs (dl > 0, Sec. II.C)
     // three per site: the charge at x, +q^mu at x + dl mu/|mu|, -q^mu at x - dl mu/|mu|
+    // (PAIRS is the dl > 0 form with dipoles; the plain form keeps its own instantiation)
     const int s0 = lstart[b], cnt = lcount[b];
-    const int per = (mu && dl > 0.0) ? 3 : 1;
+    constexpr int per = PAIRS ? 3 : 1;
     for (int k0 = 0; k0 < cnt * per; k0 += kP2MChunk) {
         const int m = min(kP2MChunk, cnt * per - k0);
         __syncthreads();
@@ -155,7 +156,7 @@ __global__ void __launch_bounds__(kUpThreads) upward_kernel(
             const int i = s0 + e / per, which = e % per;
             R qi = which == 0 && q ? R(q[i]) : R(0);
             R off[3] = {R(0), R(0), R(0)};
-            if (which > 0) {
+            if (PAIRS && which > 0) {
                 const double mx = mu[3 * i], my = mu[3 * i + 1], mz = mu[3 * i + 2];
                 const double nm = sqrt(mx * mx + my * my + mz * mz);
                 if (nm > 0.0) {
@@ -167,8 +168,8 @@ __global__ void __launch_bounds__(kUpThreads) upward_kernel(
                 }
             }
             for (int a = 0; a < 3; a++) {
-                const R v = -(ploc[3 * i + a] + off[a]) * inv_h;
-                const R ma = mu && per == 1 ? R(mu[3 * i + a]) * inv_h : R(0);
+                const R v = PAIRS ? -(ploc[3 * i + a] + off[a]) * inv_h : -ploc[3 * i + a] * inv_h;
+                const R ma = mu && !PAIRS ? R(mu[3 * i + a]) * inv_h : R(0);
                 R t = R(1), prev = R(0);
                 for (int k = 0; k <= p; k++) {
                     if (k > 0) t = t * v * RI[k];
@@ -1479,13 +1480,16 @@ static bool pass_impl(polfmm_ctx* c, int mode, bool use_q, const double* mu_sort
         {
             LaunchScope ls(c, F_P2M);
             R inv_h = R((double)(1 << d) / c->side);
-            upward_kernel<R><<<Lf.nbox, kUpThreads, upward_smem_bytes<R>(c->ncoef), c->stream>>>(
+            auto kern = mu_sorted && c->opt.dipole_dl > 0.0 ? upward_kernel<R, true> : upward_kernel<R, false>;
+            kern<<<Lf.nbox, kUpThreads, upward_smem_bytes<R>(c->ncoef), c->stream>>>(
                 Lf.nbox, d, c->lstart, c->lcount, (const R*)c->ploc, use_q ? c->q_s : nullptr, mu_sorted,
                 up_ptrs(c), c->ld, c->ncoef, c->p, T.mi, pick<R>(T.w4, T.w4f), pick<R>(T.rinv, T.rinvf), inv_h,
                 c->opt.dipole_dl);
         }
         // M2L, all levels >= 2 in one launch
-        if (m2l_tensor_enabled(c)) {
+        if (m2l_ffma_enabled(c)) {
+            m2l_ffma_launch(c);
+        } else if (m2l_tensor_enabled(c)) {
             m2l_tensor_launch(c);
         } else {
             LaunchScope ls(c, F_M2L);
@@ -1534,9 +1538,13 @@ int fmm_ops_init_attributes(polfmm_ctx*) {
     if (cudaFuncSetAttribute(m2l_simt_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need_f) !=
         cudaSuccess)
         return POLFMM_ERR_CUDA;
-    if (cudaFuncSetAttribute(upward_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (cudaFuncSetAttribute(upward_kernel<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)upward_smem_bytes<double>(nc_max)) != cudaSuccess ||
-        cudaFuncSetAttribute(upward_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(upward_kernel<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)upward_smem_bytes<double>(nc_max)) != cudaSuccess ||
+        cudaFuncSetAttribute(upward_kernel<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)upward_smem_bytes<float>(nc_max)) != cudaSuccess ||
+        cudaFuncSetAttribute(upward_kernel<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)upward_smem_bytes<float>(nc_max)) != cudaSuccess)
         return POLFMM_ERR_CUDA;
     if (cudaFuncSetAttribute(l2p_field_add_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -163,6 +163,7 @@ struct polfmm_ctx {
     polfmm::Level lv[polfmm::kMaxDepth + 1];
     void* Mall = nullptr;                      // multipoles of all levels; level l from row mrow0[l]
     int64_t mrow0[polfmm::kMaxDepth + 1] = {0};
+    int64_t mrow_zero = 0;                     // row after the last level's: all zeros
     polfmm::Tables tab;
     // M2L work list
     polfmm::M2LTile* tiles = nullptr;
@@ -259,6 +260,7 @@ struct polfmm_ctx {
     bool capturing_loop = false;           // kernels captured now take loop_cond
     int64_t loop_launches = 0;             // kernel launches per iteration of the body
     void* tc = nullptr;           // tensor-core M2L state
+    void* ff = nullptr;           // FP32 CUDA-core M2L state
     // profiling
     cudaEvent_t ev_pool[2 * 4096];
     int ev_used = 0;
@@ -302,6 +304,12 @@ int scan_exclusive(polfmm_ctx* c, const int* in, int* out, int n, int* total_dev
 bool fmm_pass(polfmm_ctx* c, int mode, bool use_q, const double* mu_sorted, double* phi, double* E,
               double* G, bool mu_packed = false, bool pcg = false);
 int m2l_setup(polfmm_ctx* c);
+// m2l_ffma.cu: the FP32 CUDA-core M2L (MIXED, p <= 6): per-tree lists, launch
+bool m2l_ffma_wanted(const polfmm_ctx* c);
+bool m2l_ffma_enabled(polfmm_ctx* c);
+int m2l_ffma_prepare(polfmm_ctx* c);
+void m2l_ffma_launch(polfmm_ctx* c);
+void m2l_ffma_release(polfmm_ctx* c);
 void pack_positions(polfmm_ctx* c);
 // MIXED: per-tree tables of the FP32 dipole near field (pair records, work items)
 int near_tables(polfmm_ctx* c);

@@ -1,0 +1,545 @@
+// FP32 multipole-to-local translation on the CUDA cores (MIXED, p <= 6).
+//
+// For a target box A and a source box B = A - o of its interaction list
+// (Sec. II.B; o one of the 189 offsets of A's octant class), the partial local
+// expansion is
+//     L_n(A) += sum_{|m| <= p - |n|} D_{n+m}(o) M_m(B),
+// D the Cartesian derivatives of 1/r at the integer offset o (normalised
+// coefficients, box side 1), the same contraction as the SIMT and tensor-core
+// kernels.  At p <= 6 one box pair is 924 multiply-adds on 84 + 84 values, so a
+// thread can hold its target's 84 accumulators and one source row in registers.
+//
+// Work decomposition.  The boxes of levels >= 2 are listed by octant class and
+// cut into groups of 32 (one per lane).  When the tree is built, every group
+// gets the list of offsets for which at least one of its 32 sources exists
+// (in offset order), with the 32 source rows of each.  Per pass a CTA of
+// kFfWarps warps takes one group and one of nchunk contiguous ranges of that
+// list; its warps take every kFfWarps-th entry.  Per entry a warp copies the 32
+// source rows and the offset's D into its own shared-memory stage with
+// cp.async, one entry ahead of the arithmetic, and each lane runs the 924 FMAs
+// in an order fixed at compile time (by n + m, so one D value is live at a
+// time).  At the end the warps' accumulators are added in warp order and the
+// CTA writes one partial local per box and chunk; the leaf kernels add the
+// chunks in order.  Every sum therefore has a fixed order.
+#include <algorithm>
+#include <utility>
+#include <vector>
+
+#include "internal.cuh"
+
+namespace polfmm {
+
+constexpr int kFfWarps = 4;
+constexpr int kFfThreads = 32 * kFfWarps;
+constexpr int kFfRows = 32;  // target boxes per group (one per lane)
+constexpr int kFfMaxP = 6;
+
+// ---------------------------------------------------------------------------
+// compile-time schedule of the contraction
+// ---------------------------------------------------------------------------
+constexpr int ff_ncoef(int p) { return (p + 1) * (p + 2) * (p + 3) / 6; }
+
+// the library's coefficient order: degree ascending, then x descending, then z ascending
+constexpr int ff_index(int x, int y, int z) {
+    const int o = x + y + z, a = o - x;
+    return o * (o + 1) * (o + 2) / 6 + a * (a + 1) / 2 + z;
+}
+
+// number of (n, m) with |n| + |m| <= p: sum over k = n + m of prod_d (k_d + 1)
+constexpr int ff_terms(int p) {
+    int s = 0;
+    for (int o = 0; o <= p; o++)
+        for (int x = o; x >= 0; x--)
+            for (int z = 0; z <= o - x; z++) s += (x + 1) * (o - x - z + 1) * (z + 1);
+    return s;
+}
+
+template <int P>
+struct FfPlan {
+    static constexpr int NT = ff_terms(P);
+    short n[NT] = {};
+    short m[NT] = {};
+    short k[NT] = {};
+    bool load[NT] = {};  // first term of the D group 4 * (k / 4): load that float4
+    constexpr FfPlan() {
+        int e = 0;
+        for (int o = 0; o <= P; o++)
+            for (int x = o; x >= 0; x--)
+                for (int z = 0; z <= o - x; z++) {
+                    const int y = o - x - z, kk = ff_index(x, y, z);
+                    for (int nx = 0; nx <= x; nx++)
+                        for (int ny = 0; ny <= y; ny++)
+                            for (int nz = 0; nz <= z; nz++) {
+                                n[e] = (short)ff_index(nx, ny, nz);
+                                m[e] = (short)ff_index(x - nx, y - ny, z - nz);
+                                k[e] = (short)kk;
+                                load[e] = kk % 4 == 0 && (e == 0 || k[e - 1] != kk);
+                                e++;
+                            }
+                }
+    }
+};
+
+template <int P>
+inline constexpr FfPlan<P> kFfPlan{};
+
+template <int P>
+struct FfDims {
+    static constexpr int NC = ff_ncoef(P);
+    static constexpr int NCP = (NC + 3) / 4 * 4;                  // = ld: floats per multipole row
+    static constexpr int RS = (NCP / 4) % 2 ? NCP : NCP + 4;      // staged row stride: an odd number of
+                                                                  // float4, so that lane-own rows are read
+                                                                  // without bank conflicts
+    static constexpr int STAGE = kFfRows * RS + NCP;              // 32 rows, then the offset's D
+};
+
+template <int J>
+__device__ __forceinline__ float ff_lane(const float4& v) {
+    if constexpr (J == 0) return v.x;
+    else if constexpr (J == 1) return v.y;
+    else if constexpr (J == 2) return v.z;
+    else return v.w;
+}
+
+template <int P, int E>
+__device__ __forceinline__ void ff_term(float (&L)[FfDims<P>::NC], const float4 (&M4)[FfDims<P>::NCP / 4],
+                                        const float4* __restrict__ D4, float4& d4) {
+    constexpr int n = kFfPlan<P>.n[E], m = kFfPlan<P>.m[E], k = kFfPlan<P>.k[E];
+    if constexpr (kFfPlan<P>.load[E]) d4 = D4[k / 4];
+    L[n] = fmaf(ff_lane<m % 4>(M4[m / 4]), ff_lane<k % 4>(d4), L[n]);
+}
+
+template <int P, int... E>
+__device__ __forceinline__ void ff_contract(float (&L)[FfDims<P>::NC], const float4 (&M4)[FfDims<P>::NCP / 4],
+                                            const float4* __restrict__ D4, std::integer_sequence<int, E...>) {
+    float4 d4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    (ff_term<P, E>(L, M4, D4, d4), ...);
+}
+
+// ---------------------------------------------------------------------------
+// asynchronous 16-byte copies into shared memory, shared-memory loads
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t ff_smem_addr(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ float4 ff_lds4(uint32_t addr) {
+    float4 v;
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];\n"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "r"(addr));
+    return v;
+}
+
+// a 16-byte copy issued only by the lanes with on != 0 (predicated, no branch)
+__device__ __forceinline__ void ff_cp16_if(uint32_t dst, const void* src, int on) {
+    asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %2, 0;\n @p cp.async.ca.shared.global [%0], [%1], 16;\n}\n" ::"r"(dst),
+                 "l"(src), "r"(on)
+                 : "memory");
+}
+
+__device__ __forceinline__ void ff_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+
+template <int N>
+__device__ __forceinline__ void ff_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+struct FfOut {
+    float* Lp[kMaxDepth + 1];  // [chunk][cap][ld] partial locals per level
+    int cap[kMaxDepth + 1];
+};
+
+// groups[g] = (first row, row count, octant class, 0); rows[r] = (level, slot)
+template <int P>
+__global__ void __launch_bounds__(kFfThreads, 2)
+    m2l_ffma_kernel(const int4* __restrict__ groups, const int2* __restrict__ rows, const int* __restrict__ ent_cnt,
+                    const int* __restrict__ ent_off, const int* __restrict__ ent_src, const float* __restrict__ Mall,
+                    const float* __restrict__ Dpad, FfOut out, int ld, int nchunk) {
+    using Dm = FfDims<P>;
+    extern __shared__ __align__(16) float ff_smem[];
+    __shared__ float* s_out[kFfRows];  // this chunk's partial-local row of each target
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g = blockIdx.x, chunk = blockIdx.y;
+    const int4 gr = groups[g];
+    if (threadIdx.x < gr.y) {
+        const int2 rs = rows[gr.x + threadIdx.x];
+        float* base = nullptr;
+        int cap = 0;
+#pragma unroll
+        for (int l = 2; l <= kMaxDepth; l++)
+            if (rs.x == l) {
+                base = out.Lp[l];
+                cap = out.cap[l];
+            }
+        s_out[threadIdx.x] = base + ((size_t)chunk * cap + rs.y) * ld;
+    }
+
+    const int cnt = ent_cnt[g];
+    const int e_lo = (int)((long long)chunk * cnt / nchunk), e_hi = (int)((long long)(chunk + 1) * cnt / nchunk);
+    const int* eoff = ent_off + (size_t)g * kNumOffsets;
+    const int* esrc = ent_src + (size_t)g * kNumOffsets * kFfRows;
+    float* stage0 = ff_smem + (size_t)warp * 2 * Dm::STAGE;
+
+    float L[Dm::NC];
+#pragma unroll
+    for (int i = 0; i < Dm::NC; i++) L[i] = 0.f;
+
+    // one entry's copies: source row i by the first CH lanes of instruction i,
+    // so that each instruction reads one contiguous row (an empty box's source
+    // is the zero row); lane i holds row i's source index.  The first CH lanes
+    // also copy the offset's derivative row.
+    constexpr int CH = Dm::NCP / 4;
+    const int copier = lane < CH;
+    const float* mbase = Mall + 4 * (copier ? lane : 0);
+    auto issue = [&](float* st, int src, int oi) {
+        const uint32_t dst = ff_smem_addr(st) + 16u * (uint32_t)(copier ? lane : 0);
+#pragma unroll
+        for (int i = 0; i < kFfRows; i++) {
+            const int s = __shfl_sync(0xffffffffu, src, i);
+            ff_cp16_if(dst + 4u * (uint32_t)(i * Dm::RS), mbase + (size_t)s * ld, copier);
+        }
+        ff_cp16_if(dst + 4u * (uint32_t)(kFfRows * Dm::RS), Dpad + (size_t)(copier ? oi * Dm::NCP + 4 * lane : 0), copier);
+    };
+
+    int e = e_lo + warp;
+    if (e < e_hi) issue(stage0, esrc[(size_t)e * kFfRows + lane], eoff[e]);
+    ff_commit();
+    int src_b = -1, oi_b = 0;  // the entry after the current one
+    if (e + kFfWarps < e_hi) {
+        src_b = esrc[(size_t)(e + kFfWarps) * kFfRows + lane];
+        oi_b = eoff[e + kFfWarps];
+    }
+    for (int it = 0; e < e_hi; it++, e += kFfWarps) {
+        float* cur = stage0 + (it & 1) * Dm::STAGE;
+        float* nxt = stage0 + ((it + 1) & 1) * Dm::STAGE;
+        if (e + kFfWarps < e_hi) issue(nxt, src_b, oi_b);
+        ff_commit();
+        // the lookups of the entry after next overlap this entry's arithmetic
+        if (e + 2 * kFfWarps < e_hi) {
+            src_b = esrc[(size_t)(e + 2 * kFfWarps) * kFfRows + lane];
+            oi_b = eoff[e + 2 * kFfWarps];
+        }
+        ff_wait<1>();
+        __syncwarp();
+        // the source row, loaded once (volatile: not re-read from shared memory later)
+        float4 M4[Dm::NCP / 4];
+        const uint32_t rrow = ff_smem_addr(cur + lane * Dm::RS);
+#pragma unroll
+        for (int j = 0; j < Dm::NCP / 4; j++) M4[j] = ff_lds4(rrow + 16u * j);
+        ff_contract<P>(L, M4, reinterpret_cast<const float4*>(cur + kFfRows * Dm::RS),
+                       std::make_integer_sequence<int, FfPlan<P>::NT>{});
+        __syncwarp();
+    }
+    ff_wait<0>();
+    __syncthreads();  // every warp is done with its stages: reuse them for the warp sums
+
+    float* red = ff_smem;  // [warp][row][RS]
+    {
+        float4* w4 = reinterpret_cast<float4*>(red + ((size_t)warp * kFfRows + lane) * Dm::RS);
+#pragma unroll
+        for (int j = 0; j < Dm::NCP / 4; j++) {
+            float4 v;
+            v.x = 4 * j < Dm::NC ? L[4 * j] : 0.f;
+            v.y = 4 * j + 1 < Dm::NC ? L[4 * j + 1] : 0.f;
+            v.z = 4 * j + 2 < Dm::NC ? L[4 * j + 2] : 0.f;
+            v.w = 4 * j + 3 < Dm::NC ? L[4 * j + 3] : 0.f;
+            w4[j] = v;
+        }
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < gr.y * Dm::NC; idx += kFfThreads) {
+        const int r = idx / Dm::NC, nn = idx - r * Dm::NC;
+        float s = 0.f;
+#pragma unroll
+        for (int w = 0; w < kFfWarps; w++) s += red[((size_t)w * kFfRows + r) * Dm::RS + nn];
+        s_out[r][nn] = s;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// per-tree tables
+// ---------------------------------------------------------------------------
+struct FfTree {
+    const int* key[kMaxDepth + 1];
+    const int* map[kMaxDepth + 1];
+    int row0[kMaxDepth + 1];  // first row of level l in the all-level multipole array
+    int zero_row;             // a row of zeros in that array: the source of an empty box
+};
+
+struct FfRowArgs {
+    int off[8], start[8];
+};
+
+// rows of one level, grouped by octant class after those of the coarser levels
+__global__ void ff_rows_kernel(int nbox, int level, const int* __restrict__ by_class, const int* __restrict__ key,
+                               FfRowArgs ra, int2* __restrict__ rows) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nbox) return;
+    const int slot = by_class[i];
+    const int c = key[slot] & 7;
+    rows[ra.off[c] + (i - ra.start[c])] = make_int2(level, slot);
+}
+
+// one block per group: the offsets with at least one source, in offset order,
+// and per such entry the 32 source rows (the zero row where there is no box)
+__global__ void __launch_bounds__(256) ff_lists_kernel(const int4* __restrict__ groups, const int2* __restrict__ rows,
+                                                       FfTree tp, const int* __restrict__ class_off,
+                                                       int* __restrict__ ent_off, int* __restrict__ ent_src,
+                                                       int* __restrict__ ent_cnt) {
+    __shared__ int s_flag[kNumOffsets];
+    __shared__ int s_pos[kNumOffsets];
+    const int g = blockIdx.x, warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+    const int4 gr = groups[g];
+    const bool has = lane < gr.y;
+    int level = 0, bx = 0, by = 0, bz = 0, nside = 0;
+    if (has) {
+        const int2 r = rows[gr.x + lane];
+        level = r.x;
+        const uint32_t k = (uint32_t)tp.key[level][r.y];
+        bx = (int)compact3(k);
+        by = (int)compact3(k >> 1);
+        bz = (int)compact3(k >> 2);
+        nside = 1 << level;
+    }
+    auto lookup = [&](int t, int& oi) {
+        const int o = class_off[gr.z * kNumOffsets + t];
+        const int ox = (o & 15) - 3, oy = ((o >> 4) & 15) - 3, oz = ((o >> 8) & 15) - 3;
+        oi = (ox + 3) + 7 * ((oy + 3) + 7 * (oz + 3));
+        const int ax = bx - ox, ay = by - oy, az = bz - oz;
+        int s = -1;
+        if (has && ax >= 0 && ay >= 0 && az >= 0 && ax < nside && ay < nside && az < nside) {
+            const int slot = tp.map[level][morton3(ax, ay, az)];
+            if (slot >= 0) s = tp.row0[level] + slot;
+        }
+        return s;
+    };
+    for (int t = warp; t < kNumOffsets; t += nwarp) {
+        int oi;
+        const int s = lookup(t, oi);
+        const unsigned b = __ballot_sync(0xffffffffu, s >= 0);
+        if (lane == 0) s_flag[t] = b != 0u;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        // exclusive scan of the flags: lane owns offsets 6 lane .. 6 lane + 5
+        constexpr int per = (kNumOffsets + 31) / 32;
+        int v[per], tot = 0;
+#pragma unroll
+        for (int j = 0; j < per; j++) {
+            const int t = per * lane + j;
+            v[j] = t < kNumOffsets ? s_flag[t] : 0;
+            tot += v[j];
+        }
+        int incl = tot;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int u = __shfl_up_sync(0xffffffffu, incl, d);
+            if (lane >= d) incl += u;
+        }
+        int run = incl - tot;
+#pragma unroll
+        for (int j = 0; j < per; j++) {
+            const int t = per * lane + j;
+            if (t < kNumOffsets) s_pos[t] = run;
+            run += v[j];
+        }
+        if (lane == 31) ent_cnt[g] = incl;
+    }
+    __syncthreads();
+    for (int t = warp; t < kNumOffsets; t += nwarp) {
+        if (!s_flag[t]) continue;
+        int oi;
+        const int s = lookup(t, oi);
+        const size_t e = (size_t)g * kNumOffsets + s_pos[t];
+        ent_src[e * kFfRows + lane] = s >= 0 ? s : tp.zero_row;
+        if (lane == 0) ent_off[e] = oi;
+    }
+}
+
+// derivative rows padded to NCP floats (16-byte aligned rows for cp.async)
+__global__ void ff_pad_kernel(const float* __restrict__ Df, int nc, int ncp, float* __restrict__ Dpad) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= 343 * ncp) return;
+    const int oi = i / ncp, k = i - oi * ncp;
+    Dpad[i] = k < nc ? Df[(size_t)oi * nc + k] : 0.f;
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+struct FfState {
+    float* Dpad = nullptr;
+    int2* rows = nullptr;
+    size_t rows_cap = 0;
+    int4* groups = nullptr;
+    int* ent_off = nullptr;
+    int* ent_src = nullptr;
+    int* ent_cnt = nullptr;
+    int groups_cap = 0;
+    int ngroups = 0;
+    size_t smem = 0;
+    bool ready = false;
+};
+
+static FfState* ff_state(polfmm_ctx* c) { return reinterpret_cast<FfState*>(c->ff); }
+
+bool m2l_ffma_wanted(const polfmm_ctx* c) {
+    return c->mixed && c->p >= 1 && c->p <= kFfMaxP && c->depth >= 2 &&
+           (c->opt.m2l_impl == POLFMM_M2L_AUTO || c->opt.m2l_impl == POLFMM_M2L_FFMA);
+}
+
+bool m2l_ffma_enabled(polfmm_ctx* c) {
+    FfState* S = ff_state(c);
+    return m2l_ffma_wanted(c) && S && S->ready && S->ngroups > 0;
+}
+
+template <int P>
+static size_t ff_smem_bytes() {
+    return sizeof(float) * (size_t)kFfWarps * 2 * FfDims<P>::STAGE;
+}
+
+template <int P>
+static cudaError_t ff_set_attr(size_t& smem) {
+    smem = ff_smem_bytes<P>();
+    return cudaFuncSetAttribute(m2l_ffma_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+int m2l_ffma_prepare(polfmm_ctx* c) {
+    if (!m2l_ffma_wanted(c)) return POLFMM_OK;
+    FfState* S = ff_state(c);
+    if (!S) {
+        S = new FfState();
+        c->ff = S;
+        const int nc = c->ncoef, ncp = c->ld;
+        if (ncp != (nc + 3) / 4 * 4) return POLFMM_ERR_INVALID_ARG;
+        if (dev_alloc(reinterpret_cast<void**>(&S->Dpad), sizeof(float) * 343 * (size_t)ncp) != cudaSuccess)
+            return POLFMM_ERR_OUT_OF_MEMORY;
+        {
+            LaunchScope ls(c, F_TREE);
+            ff_pad_kernel<<<grid_for(343 * ncp, 256), 256, 0, c->stream>>>(c->tab.Df, nc, ncp, S->Dpad);
+        }
+        cudaError_t e = cudaSuccess;
+        switch (c->p) {
+            case 1: e = ff_set_attr<1>(S->smem); break;
+            case 2: e = ff_set_attr<2>(S->smem); break;
+            case 3: e = ff_set_attr<3>(S->smem); break;
+            case 4: e = ff_set_attr<4>(S->smem); break;
+            case 5: e = ff_set_attr<5>(S->smem); break;
+            default: e = ff_set_attr<6>(S->smem); break;
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "FP32 M2L shared-memory attribute");
+        S->ready = true;
+    }
+    // rows of all levels >= 2 grouped by octant class, coarse levels first
+    int total[8] = {0};
+    size_t nrows = 0;
+    for (int l = 2; l <= c->depth; l++)
+        for (int k = 0; k < 8; k++) total[k] += c->lv[l].class_count[k];
+    int cls_first[8];
+    for (int k = 0; k < 8; k++) {
+        cls_first[k] = (int)nrows;
+        nrows += total[k];
+    }
+    if (nrows > S->rows_cap) {
+        if (S->rows) cudaFree(S->rows);
+        S->rows = nullptr;
+        S->rows_cap = std::max<size_t>(nrows, 64);
+        if (dev_alloc(reinterpret_cast<void**>(&S->rows), sizeof(int2) * S->rows_cap) != cudaSuccess)
+            return POLFMM_ERR_OUT_OF_MEMORY;
+    }
+    int fill[8];
+    for (int k = 0; k < 8; k++) fill[k] = cls_first[k];
+    for (int l = 2; l <= c->depth; l++) {
+        Level& B = c->lv[l];
+        FfRowArgs ra;
+        for (int k = 0; k < 8; k++) {
+            ra.off[k] = fill[k];
+            ra.start[k] = B.class_start[k];
+            fill[k] += B.class_count[k];
+        }
+        if (B.nbox > 0) {
+            LaunchScope ls(c, F_TREE);
+            ff_rows_kernel<<<grid_for(B.nbox, 256), 256, 0, c->stream>>>(B.nbox, l, B.by_class, B.key, ra, S->rows);
+        }
+    }
+    std::vector<int4> gl;
+    for (int k = 0; k < 8; k++)
+        for (int f = 0; f < total[k]; f += kFfRows)
+            gl.push_back(make_int4(cls_first[k] + f, std::min(kFfRows, total[k] - f), k, 0));
+    S->ngroups = (int)gl.size();
+    if (S->ngroups == 0) return POLFMM_OK;
+    if (S->ngroups > S->groups_cap) {
+        for (void* p : {(void*)S->groups, (void*)S->ent_off, (void*)S->ent_src, (void*)S->ent_cnt})
+            if (p) cudaFree(p);
+        S->groups = nullptr;
+        S->ent_off = S->ent_src = S->ent_cnt = nullptr;
+        S->groups_cap = std::max(S->ngroups, 16);
+        const size_t G = (size_t)S->groups_cap;
+        if (dev_alloc(reinterpret_cast<void**>(&S->groups), sizeof(int4) * G) != cudaSuccess ||
+            dev_alloc(reinterpret_cast<void**>(&S->ent_off), sizeof(int) * G * kNumOffsets) != cudaSuccess ||
+            dev_alloc(reinterpret_cast<void**>(&S->ent_src), sizeof(int) * G * kNumOffsets * kFfRows) != cudaSuccess ||
+            dev_alloc(reinterpret_cast<void**>(&S->ent_cnt), sizeof(int) * G) != cudaSuccess)
+            return POLFMM_ERR_OUT_OF_MEMORY;
+    }
+    if (cudaMemcpyAsync(S->groups, gl.data(), sizeof(int4) * gl.size(), cudaMemcpyHostToDevice, c->stream) !=
+        cudaSuccess)
+        return POLFMM_ERR_CUDA;
+    FfTree tp{};
+    tp.zero_row = (int)c->mrow_zero;
+    if (cudaMemsetAsync(static_cast<float*>(c->Mall) + (size_t)c->mrow_zero * c->ld, 0, sizeof(float) * c->ld,
+                        c->stream) != cudaSuccess)
+        return POLFMM_ERR_CUDA;
+    for (int l = 2; l <= c->depth; l++) {
+        tp.key[l] = c->lv[l].key;
+        tp.map[l] = c->lv[l].map;
+        tp.row0[l] = (int)c->mrow0[l];
+    }
+    {
+        LaunchScope ls(c, F_TREE);
+        ff_lists_kernel<<<S->ngroups, 256, 0, c->stream>>>(S->groups, S->rows, tp, c->tab.class_off, S->ent_off,
+                                                           S->ent_src, S->ent_cnt);
+    }
+    // chunks of each group's list so that the CTAs (two per SM) fill the SMs once
+    const int slots = 2 * c->num_sms;
+    c->m2l_chunks = std::max(1, std::min(27, slots / S->ngroups));
+    return POLFMM_OK;
+}
+
+template <int P>
+static void ff_launch(polfmm_ctx* c, FfState* S, const FfOut& out) {
+    dim3 grid(S->ngroups, c->m2l_chunks);
+    m2l_ffma_kernel<P><<<grid, kFfThreads, S->smem, c->stream>>>(S->groups, S->rows, S->ent_cnt, S->ent_off,
+                                                                  S->ent_src, (const float*)c->Mall, S->Dpad, out,
+                                                                  c->ld, c->m2l_chunks);
+}
+
+void m2l_ffma_launch(polfmm_ctx* c) {
+    FfState* S = ff_state(c);
+    FfOut out{};
+    for (int l = 2; l <= c->depth; l++) {
+        out.Lp[l] = (float*)c->lv[l].Lp;
+        out.cap[l] = c->lv[l].cap;
+    }
+    LaunchScope ls(c, F_M2L);
+    switch (c->p) {
+        case 1: ff_launch<1>(c, S, out); break;
+        case 2: ff_launch<2>(c, S, out); break;
+        case 3: ff_launch<3>(c, S, out); break;
+        case 4: ff_launch<4>(c, S, out); break;
+        case 5: ff_launch<5>(c, S, out); break;
+        default: ff_launch<6>(c, S, out); break;
+    }
+}
+
+void m2l_ffma_release(polfmm_ctx* c) {
+    FfState* S = ff_state(c);
+    if (!S) return;
+    for (void* p : {(void*)S->Dpad, (void*)S->rows, (void*)S->groups, (void*)S->ent_off, (void*)S->ent_src,
+                    (void*)S->ent_cnt})
+        if (p) cudaFree(p);
+    delete S;
+    c->ff = nullptr;
+}
+
+}  // namespace polfmm

@@ -958,7 +958,7 @@ static TcState* state(polfmm_ctx* c) { return reinterpret_cast<TcState*>(c->tc);
 
 bool m2l_tensor_enabled(polfmm_ctx* c) {
     TcState* S = state(c);
-    return c->mixed && c->opt.m2l_impl != POLFMM_M2L_SIMT && S && S->ready && S->ntiles > 0;
+    return c->mixed && c->opt.m2l_impl != POLFMM_M2L_SIMT && !m2l_ffma_wanted(c) && S && S->ready && S->ntiles > 0;
 }
 
 static int degree_of(int idx, int p) {
@@ -1020,7 +1020,8 @@ static size_t ws_smem_bytes(const WsSchedule& w) {
 }
 
 int m2l_tensor_prepare(polfmm_ctx* c) {
-    if (!c->mixed || c->opt.m2l_impl == POLFMM_M2L_SIMT || c->p > 8 || c->depth < 2) return POLFMM_OK;
+    if (!c->mixed || c->opt.m2l_impl == POLFMM_M2L_SIMT || c->p > 8 || c->depth < 2 || m2l_ffma_wanted(c))
+        return POLFMM_OK;
     TcState* S = state(c);
     if (!S) {
         S = new TcState();

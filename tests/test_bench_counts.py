@@ -64,7 +64,7 @@ def test_tree_work_counts_pairs_by_brute_force():
     w = synth.workload(1)
     lo, side = oracle.root_box(w.pos)
     depth = 3
-    near, boxes, _ = bench.tree_work(w.pos, depth, lo, side)
+    near, boxes, _, _ = bench.tree_work(w.pos, depth, lo, side)
     cells = oracle.leaf_cells(w.pos, depth, lo, side).astype(np.int64)
     # ordered site pairs i != j in adjacent (or the same) leaves
     adj = np.abs(cells[:, None, :] - cells[None, :, :]).max(axis=2) <= 1
@@ -85,3 +85,35 @@ def test_tolerance_rule():
     assert bench.tol_for("fp64", 10 ** 6) == 1e-8
     assert bench.tol_for("mixed", 100_000) == 1e-6
     assert bench.tol_for("mixed", 100_001) == 3e-7
+
+
+def test_tree_work_counts_ffma_entries_by_brute_force():
+    """Entries of the FP32 CUDA-core M2L: boxes of levels >= 2 per octant class
+    (coarse levels first, Morton order within a level) in groups of 32; a group
+    has an entry for each offset of its class at which any member's source
+    box is occupied."""
+    w = synth.workload(1)
+    lo, side = oracle.root_box(w.pos)
+    depth = 3
+    _, _, _, entries = bench.tree_work(w.pos, depth, lo, side)
+    cells = oracle.leaf_cells(w.pos, depth, lo, side).astype(np.int64)
+
+    def morton(t):
+        return sum(((t[a] >> b) & 1) << (3 * b + a) for b in range(8) for a in range(3))
+
+    rows = {k: [] for k in range(8)}
+    occ = {}
+    for l in range(2, depth + 1):
+        occ[l] = {tuple(c) for c in (cells >> (depth - l)).tolist()}
+        for t in sorted(occ[l], key=morton):
+            rows[(t[0] & 1) + 2 * (t[1] & 1) + 4 * (t[2] & 1)].append((l, t))
+    total = 0
+    for k in range(8):
+        b = (k & 1, (k >> 1) & 1, (k >> 2) & 1)
+        offs = [o for o in itertools.product(range(-3, 4), repeat=3)
+                if max(map(abs, o)) > 1 and all(bd - 3 <= od <= bd + 2 for od, bd in zip(o, b))]
+        assert len(offs) == 189
+        for g in range(0, len(rows[k]), 32):
+            grp = rows[k][g:g + 32]
+            total += sum(any(tuple(t[a] - o[a] for a in range(3)) in occ[l] for l, t in grp) for o in offs)
+    assert entries == total

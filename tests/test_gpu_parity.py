@@ -326,6 +326,58 @@ def test_tensor_core_m2l_matches_simt(case, w1, w2):
     assert max_site_err(out["tensor"][1], out["simt"][1]) < 1e-4
 
 
+# ---------------------------------------------------------------------------
+# FP32 CUDA-core multipole-to-local (MIXED, p <= 6) against SIMT and FP64
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("case", ["p2", "p3", "small", "cube", "globule", "deep"])
+def test_ffma_m2l_matches_simt(case, w1, w2):
+    if case in ("p2", "p3"):
+        pos, q, alpha = synth.small_random(43, 500, box=16.0)
+        p, depth = int(case[1]), 3
+    elif case == "small":
+        pos, q, alpha = synth.small_random(41, 300, box=14.0)
+        p, depth = 5, 3
+    elif case == "cube":
+        pos, q, alpha, p, depth = w1.pos, w1.q, w1.alpha, 4, 3
+    elif case == "globule":
+        pos, q, alpha, p, depth = w2.pos, w2.q, w2.alpha, 6, 4
+    else:
+        # depth 6: 8^l maps, empty boxes and groups that straddle levels
+        pos, q, alpha = synth.small_random(47, 6000, box=60.0, d_min=1.2)
+        p, depth = 6, 6
+    rng = np.random.default_rng(7)
+    mu = 0.3 * rng.normal(size=(len(q), 3))
+    out = {}
+    for impl in ("simt", "ffma", "auto"):
+        with PolFMM(dev(pos), dev(q), dev(alpha), p=p, depth=depth, mode="mixed", m2l=impl) as f:
+            out[impl] = (host(f.dipole_field(dev(mu))), host(f.static_field()["E"]), host(f.static_field()["phi"]))
+    with PolFMM(dev(pos), dev(q), dev(alpha), p=p, depth=depth, mode="fp64") as f:
+        ref = host(f.dipole_field(dev(mu)))
+        ref_s = f.static_field()
+        ref_e, ref_phi = host(ref_s["E"]), host(ref_s["phi"])
+    # AUTO takes the CUDA-core kernel at p <= 6
+    for a, b in zip(out["auto"], out["ffma"]):
+        assert np.array_equal(a, b)
+    # FP32 arithmetic throughout: within FP32 round-off of FP64
+    assert oracle.rel_rms(out["ffma"][0], ref) < 5e-6
+    assert oracle.rel_rms(out["ffma"][1], ref_e) < 5e-6
+    assert oracle.rel_rms(out["ffma"][2], ref_phi) < 5e-6
+    assert oracle.rel_rms(out["ffma"][0], out["simt"][0]) < 5e-6
+    assert max_site_err(out["ffma"][0], ref) < 1e-4
+    assert max_site_err(out["ffma"][1], ref_e) < 1e-4
+
+
+def test_ffma_m2l_forces_within_gate(w2):
+    outs = {}
+    for mode, impl in (("fp64", "simt"), ("mixed", "ffma")):
+        with PolFMM(dev(w2.pos), dev(w2.q), dev(w2.alpha), p=w2.p, depth=w2.depth, mode=mode, m2l=impl) as f:
+            f.solve(1e-8 if mode == "fp64" else 1e-7)
+            outs[mode] = host(f.energy_forces()["F"])
+    assert oracle.rel_rms(outs["mixed"], outs["fp64"]) < MIXED_FORCE_TOL
+    assert max_site_err(outs["mixed"], outs["fp64"]) < MIXED_SITE_TOL
+
+
 def test_tensor_core_m2l_forces_within_gate(w2):
     outs = {}
     for mode, impl in (("fp64", "simt"), ("mixed", "tensor")):
