@@ -12,15 +12,19 @@
 // Work decomposition.  The boxes of levels >= 2 are listed by octant class and
 // cut into groups of 32 (one per lane).  When the tree is built, every group
 // gets the list of offsets for which at least one of its 32 sources exists
-// (in offset order), with the 32 source rows of each.  Per pass a CTA of
-// kFfWarps warps takes one group and one of nchunk contiguous ranges of that
-// list; its warps take every kFfWarps-th entry.  Per entry a warp copies the 32
-// source rows and the offset's D into its own shared-memory stage with
-// cp.async, one entry ahead of the arithmetic, and each lane runs the 924 FMAs
-// in an order fixed at compile time (by n + m, so one D value is live at a
-// time).  At the end the warps' accumulators are added in warp order and the
-// CTA writes one partial local per box and chunk; the leaf kernels add the
-// chunks in order.  Every sum therefore has a fixed order.
+// (in offset order), with the 32 source rows of each (a row of zeros for an
+// empty box).  Per pass a CTA of kFfPairs warp pairs takes one group and one of
+// nchunk contiguous ranges of that list; its pairs take every kFfPairs-th
+// entry.  The two warps of a pair share a shared-memory stage per entry, filled
+// with cp.async one entry ahead of the arithmetic (half the rows each, one
+// contiguous row per instruction), and split the outputs by degree: at p = 6
+// the first takes |n| <= 2 (10 accumulators, all 84 inputs), the second
+// |n| >= 3 (74 accumulators, the 20 inputs of |m| <= 3), 462 FMAs each, so that
+// both fit in 128 registers and four warps share each scheduler.  The FMAs run
+// in an order fixed at compile time (by n + m, one float4 of D live at a time).
+// At the end the pairs' accumulators are added in pair order and the CTA writes
+// one partial local per box and chunk; the leaf kernels add the chunks in order.
+// Every sum therefore has a fixed order.
 #include <algorithm>
 #include <utility>
 #include <vector>
@@ -29,10 +33,11 @@
 
 namespace polfmm {
 
-constexpr int kFfWarps = 4;
-constexpr int kFfThreads = 32 * kFfWarps;
+constexpr int kFfPairs = 4;  // warp pairs per CTA; the two warps of a pair share the staged entries
+constexpr int kFfThreads = 64 * kFfPairs;
 constexpr int kFfRows = 32;  // target boxes per group (one per lane)
 constexpr int kFfMaxP = 6;
+constexpr int kFfMaxChunks = 16;  // partial locals per box (the leaf kernels add them in order)
 
 // ---------------------------------------------------------------------------
 // compile-time schedule of the contraction
@@ -54,14 +59,51 @@ constexpr int ff_terms(int p) {
     return s;
 }
 
+// terms of the outputs of degree s: (s + 1)(s + 2)/2 outputs of ncoef(p - s) terms
+constexpr int ff_terms_of_degree(int p, int s) { return (s + 1) * (s + 2) / 2 * ff_ncoef(p - s); }
+
+// the two warps of a pair split the outputs by degree: |n| <= split to the
+// first, the rest to the second, with the term counts as equal as they come
+constexpr int ff_split(int p) {
+    const int tot = ff_terms(p);
+    int best = 0, bestd = 1 << 30, run = 0;
+    for (int s = 0; s < p; s++) {
+        run += ff_terms_of_degree(p, s);
+        const int d = 2 * run > tot ? 2 * run - tot : tot - 2 * run;
+        if (d < bestd) {
+            bestd = d;
+            best = s;
+        }
+    }
+    return best;
+}
+
 template <int P>
+struct FfSplit {
+    static constexpr int SA = ff_split(P);
+    static constexpr int NA = ff_ncoef(SA);               // outputs of the first warp: 0 .. NA - 1
+    static constexpr int NB = ff_ncoef(P) - NA;           // outputs of the second: NA .. ncoef - 1
+    static constexpr int MB = ff_ncoef(P - SA - 1);       // inputs the second warp uses (|m| <= P - SA - 1)
+};
+
+constexpr int ff_part_terms(int p, int part) {
+    int s = 0;
+    for (int d = 0; d <= p; d++)
+        if ((part == 0) == (d <= ff_split(p))) s += ff_terms_of_degree(p, d);
+    return s;
+}
+
+// the terms of one part ordered by k = n + m (the D index), so that one float4
+// of D is live at a time; n is relative to the part's first output
+template <int P, int PART>
 struct FfPlan {
-    static constexpr int NT = ff_terms(P);
+    static constexpr int NT = ff_part_terms(P, PART);
     short n[NT] = {};
     short m[NT] = {};
     short k[NT] = {};
-    bool load[NT] = {};  // first term of the D group 4 * (k / 4): load that float4
+    bool load[NT] = {};  // first term of its D group 4 * (k / 4) in this part: load that float4
     constexpr FfPlan() {
+        const int sa = ff_split(P), n0 = PART == 0 ? 0 : ff_ncoef(sa);
         int e = 0;
         for (int o = 0; o <= P; o++)
             for (int x = o; x >= 0; x--)
@@ -70,18 +112,19 @@ struct FfPlan {
                     for (int nx = 0; nx <= x; nx++)
                         for (int ny = 0; ny <= y; ny++)
                             for (int nz = 0; nz <= z; nz++) {
-                                n[e] = (short)ff_index(nx, ny, nz);
+                                if ((PART == 0) != (nx + ny + nz <= sa)) continue;
+                                n[e] = (short)(ff_index(nx, ny, nz) - n0);
                                 m[e] = (short)ff_index(x - nx, y - ny, z - nz);
                                 k[e] = (short)kk;
-                                load[e] = kk % 4 == 0 && (e == 0 || k[e - 1] != kk);
+                                load[e] = e == 0 || k[e - 1] / 4 != kk / 4;
                                 e++;
                             }
                 }
     }
 };
 
-template <int P>
-inline constexpr FfPlan<P> kFfPlan{};
+template <int P, int PART>
+inline constexpr FfPlan<P, PART> kFfPlan{};
 
 template <int P>
 struct FfDims {
@@ -101,19 +144,19 @@ __device__ __forceinline__ float ff_lane(const float4& v) {
     else return v.w;
 }
 
-template <int P, int E>
-__device__ __forceinline__ void ff_term(float (&L)[FfDims<P>::NC], const float4 (&M4)[FfDims<P>::NCP / 4],
-                                        const float4* __restrict__ D4, float4& d4) {
-    constexpr int n = kFfPlan<P>.n[E], m = kFfPlan<P>.m[E], k = kFfPlan<P>.k[E];
-    if constexpr (kFfPlan<P>.load[E]) d4 = D4[k / 4];
+template <int P, int PART, int NL, int NM, int E>
+__device__ __forceinline__ void ff_term(float (&L)[NL], const float4 (&M4)[NM], const float4* __restrict__ D4,
+                                        float4& d4) {
+    constexpr int n = kFfPlan<P, PART>.n[E], m = kFfPlan<P, PART>.m[E], k = kFfPlan<P, PART>.k[E];
+    if constexpr (kFfPlan<P, PART>.load[E]) d4 = D4[k / 4];
     L[n] = fmaf(ff_lane<m % 4>(M4[m / 4]), ff_lane<k % 4>(d4), L[n]);
 }
 
-template <int P, int... E>
-__device__ __forceinline__ void ff_contract(float (&L)[FfDims<P>::NC], const float4 (&M4)[FfDims<P>::NCP / 4],
-                                            const float4* __restrict__ D4, std::integer_sequence<int, E...>) {
+template <int P, int PART, int NL, int NM, int... E>
+__device__ __forceinline__ void ff_contract(float (&L)[NL], const float4 (&M4)[NM], const float4* __restrict__ D4,
+                                            std::integer_sequence<int, E...>) {
     float4 d4 = make_float4(0.f, 0.f, 0.f, 0.f);
-    (ff_term<P, E>(L, M4, D4, d4), ...);
+    (ff_term<P, PART, NL, NM, E>(L, M4, D4, d4), ...);
 }
 
 // ---------------------------------------------------------------------------
@@ -150,6 +193,78 @@ struct FfOut {
     int cap[kMaxDepth + 1];
 };
 
+__device__ __forceinline__ void ff_bar(int id, int nthreads) {
+    asm volatile("bar.sync %0, %1;\n" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+// one warp of a pair: its entries, its half of the copies, its part of the
+// outputs; at the end its accumulators go to red[pair][row][RS]
+template <int P, int PART>
+__device__ __forceinline__ void ff_warp(const int* __restrict__ eoff, const int* __restrict__ esrc, int e, int e_hi,
+                                        float* stage0, const float* __restrict__ Mall, const float* __restrict__ Dpad,
+                                        int ld, int pair, int lane, float* red) {
+    using Dm = FfDims<P>;
+    using Sp = FfSplit<P>;
+    constexpr int NL = PART == 0 ? Sp::NA : Sp::NB;            // accumulators
+    constexpr int NM = PART == 0 ? Dm::NCP / 4 : (Sp::MB + 3) / 4;  // float4 of the source row used
+    constexpr int CH = Dm::NCP / 4;
+    float L[NL];
+#pragma unroll
+    for (int i = 0; i < NL; i++) L[i] = 0.f;
+
+    // this warp's copies of an entry: rows 16 PART .. 16 PART + 15, one row per
+    // instruction by the first CH lanes (each instruction reads one contiguous
+    // row), and by the first warp the offset's derivative row; lane i holds row
+    // i's source index (an empty box's source is the zero row).
+    const int copier = lane < CH;
+    const float* mbase = Mall + 4 * (copier ? lane : 0);
+    auto issue = [&](float* st, int src, int oi) {
+        const uint32_t dst = ff_smem_addr(st) + 16u * (uint32_t)(copier ? lane : 0);
+#pragma unroll
+        for (int i = 16 * PART; i < 16 * PART + 16; i++) {
+            const int s = __shfl_sync(0xffffffffu, src, i);
+            ff_cp16_if(dst + 4u * (uint32_t)(i * Dm::RS), mbase + (size_t)s * ld, copier);
+        }
+        if (PART == 0)
+            ff_cp16_if(dst + 4u * (uint32_t)(kFfRows * Dm::RS), Dpad + (size_t)(copier ? oi * Dm::NCP + 4 * lane : 0),
+                       copier);
+    };
+
+    if (e < e_hi) issue(stage0, esrc[(size_t)e * kFfRows + lane], eoff[e]);
+    ff_commit();
+    int src_b = 0, oi_b = 0;  // the entry after the current one
+    if (e + kFfPairs < e_hi) {
+        src_b = esrc[(size_t)(e + kFfPairs) * kFfRows + lane];
+        oi_b = eoff[e + kFfPairs];
+    }
+    for (int it = 0; e < e_hi; it++, e += kFfPairs) {
+        float* cur = stage0 + (it & 1) * Dm::STAGE;
+        float* nxt = stage0 + ((it + 1) & 1) * Dm::STAGE;
+        ff_wait<0>();
+        // both halves of this entry have landed, and both warps are done with nxt
+        ff_bar(1 + pair, 64);
+        if (e + kFfPairs < e_hi) issue(nxt, src_b, oi_b);
+        ff_commit();
+        // the lookups of the entry after next overlap this entry's arithmetic
+        if (e + 2 * kFfPairs < e_hi) {
+            src_b = esrc[(size_t)(e + 2 * kFfPairs) * kFfRows + lane];
+            oi_b = eoff[e + 2 * kFfPairs];
+        }
+        // the source row, loaded once (volatile: not re-read from shared memory later)
+        float4 M4[NM];
+        const uint32_t rrow = ff_smem_addr(cur + lane * Dm::RS);
+#pragma unroll
+        for (int j = 0; j < NM; j++) M4[j] = ff_lds4(rrow + 16u * j);
+        ff_contract<P, PART, NL, NM>(L, M4, reinterpret_cast<const float4*>(cur + kFfRows * Dm::RS),
+                                     std::make_integer_sequence<int, FfPlan<P, PART>::NT>{});
+    }
+    ff_wait<0>();
+    ff_bar(0, kFfThreads);  // every warp is done with its stages: reuse them for the pair sums
+    float* row = red + ((size_t)pair * kFfRows + lane) * Dm::RS + (PART == 0 ? 0 : Sp::NA);
+#pragma unroll
+    for (int i = 0; i < NL; i++) row[i] = L[i];
+}
+
 // groups[g] = (first row, row count, octant class, 0); rows[r] = (level, slot)
 template <int P>
 __global__ void __launch_bounds__(kFfThreads, 2)
@@ -159,7 +274,7 @@ __global__ void __launch_bounds__(kFfThreads, 2)
     using Dm = FfDims<P>;
     extern __shared__ __align__(16) float ff_smem[];
     __shared__ float* s_out[kFfRows];  // this chunk's partial-local row of each target
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, pair = warp >> 1;
     const int g = blockIdx.x, chunk = blockIdx.y;
     const int4 gr = groups[g];
     if (threadIdx.x < gr.y) {
@@ -174,85 +289,24 @@ __global__ void __launch_bounds__(kFfThreads, 2)
             }
         s_out[threadIdx.x] = base + ((size_t)chunk * cap + rs.y) * ld;
     }
-
     const int cnt = ent_cnt[g];
     const int e_lo = (int)((long long)chunk * cnt / nchunk), e_hi = (int)((long long)(chunk + 1) * cnt / nchunk);
     const int* eoff = ent_off + (size_t)g * kNumOffsets;
     const int* esrc = ent_src + (size_t)g * kNumOffsets * kFfRows;
-    float* stage0 = ff_smem + (size_t)warp * 2 * Dm::STAGE;
-
-    float L[Dm::NC];
-#pragma unroll
-    for (int i = 0; i < Dm::NC; i++) L[i] = 0.f;
-
-    // one entry's copies: source row i by the first CH lanes of instruction i,
-    // so that each instruction reads one contiguous row (an empty box's source
-    // is the zero row); lane i holds row i's source index.  The first CH lanes
-    // also copy the offset's derivative row.
-    constexpr int CH = Dm::NCP / 4;
-    const int copier = lane < CH;
-    const float* mbase = Mall + 4 * (copier ? lane : 0);
-    auto issue = [&](float* st, int src, int oi) {
-        const uint32_t dst = ff_smem_addr(st) + 16u * (uint32_t)(copier ? lane : 0);
-#pragma unroll
-        for (int i = 0; i < kFfRows; i++) {
-            const int s = __shfl_sync(0xffffffffu, src, i);
-            ff_cp16_if(dst + 4u * (uint32_t)(i * Dm::RS), mbase + (size_t)s * ld, copier);
-        }
-        ff_cp16_if(dst + 4u * (uint32_t)(kFfRows * Dm::RS), Dpad + (size_t)(copier ? oi * Dm::NCP + 4 * lane : 0), copier);
-    };
-
-    int e = e_lo + warp;
-    if (e < e_hi) issue(stage0, esrc[(size_t)e * kFfRows + lane], eoff[e]);
-    ff_commit();
-    int src_b = -1, oi_b = 0;  // the entry after the current one
-    if (e + kFfWarps < e_hi) {
-        src_b = esrc[(size_t)(e + kFfWarps) * kFfRows + lane];
-        oi_b = eoff[e + kFfWarps];
-    }
-    for (int it = 0; e < e_hi; it++, e += kFfWarps) {
-        float* cur = stage0 + (it & 1) * Dm::STAGE;
-        float* nxt = stage0 + ((it + 1) & 1) * Dm::STAGE;
-        if (e + kFfWarps < e_hi) issue(nxt, src_b, oi_b);
-        ff_commit();
-        // the lookups of the entry after next overlap this entry's arithmetic
-        if (e + 2 * kFfWarps < e_hi) {
-            src_b = esrc[(size_t)(e + 2 * kFfWarps) * kFfRows + lane];
-            oi_b = eoff[e + 2 * kFfWarps];
-        }
-        ff_wait<1>();
-        __syncwarp();
-        // the source row, loaded once (volatile: not re-read from shared memory later)
-        float4 M4[Dm::NCP / 4];
-        const uint32_t rrow = ff_smem_addr(cur + lane * Dm::RS);
-#pragma unroll
-        for (int j = 0; j < Dm::NCP / 4; j++) M4[j] = ff_lds4(rrow + 16u * j);
-        ff_contract<P>(L, M4, reinterpret_cast<const float4*>(cur + kFfRows * Dm::RS),
-                       std::make_integer_sequence<int, FfPlan<P>::NT>{});
-        __syncwarp();
-    }
-    ff_wait<0>();
-    __syncthreads();  // every warp is done with its stages: reuse them for the warp sums
-
-    float* red = ff_smem;  // [warp][row][RS]
-    {
-        float4* w4 = reinterpret_cast<float4*>(red + ((size_t)warp * kFfRows + lane) * Dm::RS);
-#pragma unroll
-        for (int j = 0; j < Dm::NCP / 4; j++) {
-            float4 v;
-            v.x = 4 * j < Dm::NC ? L[4 * j] : 0.f;
-            v.y = 4 * j + 1 < Dm::NC ? L[4 * j + 1] : 0.f;
-            v.z = 4 * j + 2 < Dm::NC ? L[4 * j + 2] : 0.f;
-            v.w = 4 * j + 3 < Dm::NC ? L[4 * j + 3] : 0.f;
-            w4[j] = v;
-        }
-    }
-    __syncthreads();
+    float* stage0 = ff_smem + (size_t)pair * 2 * Dm::STAGE;
+    // warp 2i takes the low-degree outputs of pair i, warp 2i + 1 the others
+    if ((warp & 1) == 0)
+        ff_warp<P, 0>(eoff, esrc, e_lo + pair, e_hi, stage0, Mall, Dpad, ld, pair, lane, ff_smem);
+    else
+        ff_warp<P, 1>(eoff, esrc, e_lo + pair, e_hi, stage0, Mall, Dpad, ld, pair, lane, ff_smem);
+    ff_bar(0, kFfThreads);
+    // the pairs' sums in pair order
+    const float* red = ff_smem;
     for (int idx = threadIdx.x; idx < gr.y * Dm::NC; idx += kFfThreads) {
         const int r = idx / Dm::NC, nn = idx - r * Dm::NC;
         float s = 0.f;
 #pragma unroll
-        for (int w = 0; w < kFfWarps; w++) s += red[((size_t)w * kFfRows + r) * Dm::RS + nn];
+        for (int w = 0; w < kFfPairs; w++) s += red[((size_t)w * kFfRows + r) * Dm::RS + nn];
         s_out[r][nn] = s;
     }
 }
@@ -396,7 +450,7 @@ bool m2l_ffma_enabled(polfmm_ctx* c) {
 
 template <int P>
 static size_t ff_smem_bytes() {
-    return sizeof(float) * (size_t)kFfWarps * 2 * FfDims<P>::STAGE;
+    return sizeof(float) * (size_t)kFfPairs * 2 * FfDims<P>::STAGE;
 }
 
 template <int P>
@@ -502,7 +556,7 @@ int m2l_ffma_prepare(polfmm_ctx* c) {
     }
     // chunks of each group's list so that the CTAs (two per SM) fill the SMs once
     const int slots = 2 * c->num_sms;
-    c->m2l_chunks = std::max(1, std::min(27, slots / S->ngroups));
+    c->m2l_chunks = std::max(1, std::min(kFfMaxChunks, slots / S->ngroups));
     return POLFMM_OK;
 }
 
