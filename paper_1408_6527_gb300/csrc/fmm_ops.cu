@@ -77,7 +77,7 @@ __device__ inline void stage_small(R* dst, const R* __restrict__ src, int p) {
 // one-axis convolutions (exact: the truncation k <= n is a box).
 // ---------------------------------------------------------------------------
 constexpr int kP2MChunk = 64;
-constexpr int kUpThreads = 256;
+constexpr int kUpThreads = 128;
 constexpr int kUpMaxSlices = 8;
 
 struct UpPtrs {
