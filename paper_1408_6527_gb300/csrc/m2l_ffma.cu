@@ -337,7 +337,9 @@ __global__ void ff_rows_kernel(int nbox, int level, const int* __restrict__ by_c
 
 // one block per group: the offsets with at least one source, in offset order,
 // and per such entry the 32 source rows (the zero row where there is no box)
-__global__ void __launch_bounds__(256) ff_lists_kernel(const int4* __restrict__ groups, const int2* __restrict__ rows,
+constexpr int kFfListThreads = 1024;  // 32 warps share a group's 189 offsets
+
+__global__ void __launch_bounds__(kFfListThreads) ff_lists_kernel(const int4* __restrict__ groups, const int2* __restrict__ rows,
                                                        FfTree tp, const int* __restrict__ class_off,
                                                        int* __restrict__ ent_off, int* __restrict__ ent_src,
                                                        int* __restrict__ ent_cnt) {
@@ -551,7 +553,7 @@ int m2l_ffma_prepare(polfmm_ctx* c) {
     }
     {
         LaunchScope ls(c, F_TREE);
-        ff_lists_kernel<<<S->ngroups, 256, 0, c->stream>>>(S->groups, S->rows, tp, c->tab.class_off, S->ent_off,
+        ff_lists_kernel<<<S->ngroups, kFfListThreads, 0, c->stream>>>(S->groups, S->rows, tp, c->tab.class_off, S->ent_off,
                                                            S->ent_src, S->ent_cnt);
     }
     // chunks of each group's list so that the CTAs (two per SM) fill the SMs once

@@ -331,7 +331,11 @@ def main(argv=None):
     ap.add_argument("--predictor", type=int, default=0, choices=[0, 1],
                     help="start of each solve: 0 = last dipoles, 1 = linear extrapolation from the last two")
     ap.add_argument("--seed", type=int, default=7)
+    ap.add_argument("--modes", default="fp64,mixed", help="comma-separated precision modes to run (fp64, mixed)")
     args = ap.parse_args(argv)
+    modes = [m.strip() for m in args.modes.split(",") if m.strip()]
+    if not modes or any(m not in ("fp64", "mixed") for m in modes):
+        ap.error("--modes takes fp64 and/or mixed")
     w = synth.workload(4, n=args.sites)
     rng = np.random.default_rng(args.seed)
     masses = rng.uniform(1.0, 16.0, w.n)
@@ -347,6 +351,8 @@ def main(argv=None):
                               "max_rel_diff": fd_check(w.pos, w.q, w.alpha, w.p, w.depth, args.fd_sites),
                               "seconds": round(time.perf_counter() - t0, 1)}
     for mode, tol in (("fp64", 1e-8), ("mixed", 1e-6)):
+        if mode not in modes:
+            continue
         dyn = Dynamics(w.pos, w.q, args.alpha_scale * w.alpha, masses, p=w.p, depth=w.depth, mode=mode, tol=tol,
                        predictor=args.predictor)
         v = torch.as_tensor(v0, dtype=torch.float64, device="cuda")
