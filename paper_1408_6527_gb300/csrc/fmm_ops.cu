@@ -60,6 +60,60 @@ __device__ inline void stage_small(R* dst, const R* __restrict__ src, int p) {
     if ((int)threadIdx.x <= p) dst[threadIdx.x] = src[threadIdx.x];
 }
 
+// The index of the multi-index n +- k e_AX in the coefficient order, stepped
+// term by term from idx(x, y, z) = T3(o) + T2(a) + z (o = |n|, a = o - x,
+// T3(m) = m(m+1)(m+2)/6, T2(m) = m(m+1)/2): one step changes T3 by T2(o + k)
+// (or -T2(o - k + 1)), T2(a) by a + k (or -(a - k + 1)) when AX >= 1, and z by
+// 1 when AX = 2, so that no term evaluates the cubic.
+//
+// one L2L pass along axis AX: a_n = sum_{k <= p - |n|} W_k f_{n + k e_AX}, with
+// sign (-1)^k where the shift is negative
+template <int AX, typename R>
+__device__ inline R shift_up_axis(const R* src, int cc, int pk, bool neg, const R* W, int p) {
+    const int x = pk & 0xff, o = pk >> 24;
+    const int kmax = p - o;
+    int a1 = o - x;
+    int t = (o + 1) * (o + 2) / 2;  // T2(o + 1)
+    int idx = cc;
+    R a = src[cc];
+    for (int k = 1; k <= kmax; k++) {
+        idx += t;
+        t += o + k + 1;
+        if (AX >= 1) {
+            a1 += 1;
+            idx += a1;
+        }
+        if (AX == 2) idx += 1;
+        const R v = W[k] * src[idx];
+        a += (neg && (k & 1)) ? -v : v;
+    }
+    return a;
+}
+
+// one M2M pass along axis AX: g_n = sum_{k <= n_AX} W_k m_{n - k e_AX}, with
+// sign (-1)^k where the shift is negative
+template <int AX, typename R>
+__device__ inline R shift_down_axis(const R* src, int cc, int pk, bool neg, const R* W) {
+    const int x = pk & 0xff, y = (pk >> 8) & 0xff, z = (pk >> 16) & 0xff, o = pk >> 24;
+    const int kmax = AX == 0 ? x : (AX == 1 ? y : z);
+    int a1 = o - x;
+    int t = o * (o + 1) / 2;  // T2(o)
+    int idx = cc;
+    R a = src[cc];
+    for (int k = 1; k <= kmax; k++) {
+        idx -= t;
+        t -= o - k + 1;
+        if (AX >= 1) {
+            idx -= a1;
+            a1 -= 1;
+        }
+        if (AX == 2) idx -= 1;
+        const R v = W[k] * src[idx];
+        a += (neg && (k & 1)) ? -v : v;
+    }
+    return a;
+}
+
 // ---------------------------------------------------------------------------
 // upward pass: P2M of every leaf, then M2M up to level 2 inside the same
 // launch.  Each box shifts its own multipole to its parent's centre as soon as
@@ -232,24 +286,12 @@ __global__ void __launch_bounds__(kUpThreads) upward_kernel(
         for (int cc = tid; cc < ncoef; cc += kUpThreads) T0[cc] = Mrow[cc] * pow2neg<R>(smi[cc] >> 24);
         __syncthreads();
         // g_n = sum_{k <= n_d} (s/4)^k/k! m_{n - k e_d}, along x (T0 -> T1), y (T1 -> T0), z (T0 -> T1)
-        for (int ax = 0; ax < 3; ax++) {
-            const R* src = ax == 1 ? T1 : T0;
-            R* dst = ax == 1 ? T0 : T1;
-            const bool neg = ax == 0 ? neg_x : (ax == 1 ? neg_y : neg_z);
-            for (int cc = tid; cc < ncoef; cc += kUpThreads) {
-                const int pk = smi[cc];
-                const int x = pk & 0xff, y = (pk >> 8) & 0xff, z = (pk >> 16) & 0xff;
-                const int ex = ax == 0, ey = ax == 1, ez = ax == 2;
-                const int kmax = ex * x + ey * y + ez * z;
-                R a = src[cc];
-                for (int k = 1; k <= kmax; k++) {
-                    const R v = W[k] * src[mi_index(x - k * ex, y - k * ey, z - k * ez)];
-                    a += (neg && (k & 1)) ? -v : v;
-                }
-                dst[cc] = a;
-            }
-            __syncthreads();
-        }
+        for (int cc = tid; cc < ncoef; cc += kUpThreads) T1[cc] = shift_down_axis<0>(T0, cc, smi[cc], neg_x, W);
+        __syncthreads();
+        for (int cc = tid; cc < ncoef; cc += kUpThreads) T0[cc] = shift_down_axis<1>(T1, cc, smi[cc], neg_y, W);
+        __syncthreads();
+        for (int cc = tid; cc < ncoef; cc += kUpThreads) T1[cc] = shift_down_axis<2>(T0, cc, smi[cc], neg_z, W);
+        __syncthreads();
         R* msh = reinterpret_cast<R*>(up.Msh[l]) + (int64_t)box * ld;
         for (int cc = tid; cc < ncoef; cc += kUpThreads) msh[cc] = T1[cc];
         __threadfence();  // the shifted row is visible before the count
@@ -298,21 +340,6 @@ struct DownPtrs {
     int depth, nchunk, p;
 };
 
-// one L2L pass along axis ax: a_n = sum_{k <= p - |n|} (t/4)^k... with sign
-// (-1)^k where the shift is negative; indices by formula, so the loads are independent
-template <typename R>
-__device__ inline R shift_up_axis(const R* src, int cc, int pk, int ax, bool neg, const R* W, int p) {
-    const int x = pk & 0xff, y = (pk >> 8) & 0xff, z = (pk >> 16) & 0xff;
-    const int ex = ax == 0, ey = ax == 1, ez = ax == 2;
-    const int kmax = p - (pk >> 24);
-    R a = src[cc];
-    for (int k = 1; k <= kmax; k++) {
-        const R v = W[k] * src[mi_index(x + k * ex, y + k * ey, z + k * ez)];
-        a += (neg && (k & 1)) ? -v : v;
-    }
-    return a;
-}
-
 // all threads of the block call it; f, t0, t1: ncoef each, psum: (depth - 1)
 // x ncoef, all in shared memory; cinfo[4 c] = packed multi-index of c.  The
 // ancestors come from the leaf's Morton key, the M2L partials of all of them
@@ -352,14 +379,14 @@ __device__ void far_locals(const DownPtrs& dp, int b, R* f, R* t0, R* t1, R* psu
     __syncthreads();
     for (int l = 3; l <= d; l++) {
         const int oct = coct[l];
-        for (int cc = tid; cc < ncoef; cc += NT) t0[cc] = shift_up_axis(f, cc, cinfo[4 * cc], 0, !(oct & 1), W, dp.p);
+        for (int cc = tid; cc < ncoef; cc += NT) t0[cc] = shift_up_axis<0>(f, cc, cinfo[4 * cc], !(oct & 1), W, dp.p);
         __syncthreads();
-        for (int cc = tid; cc < ncoef; cc += NT) t1[cc] = shift_up_axis(t0, cc, cinfo[4 * cc], 1, !(oct & 2), W, dp.p);
+        for (int cc = tid; cc < ncoef; cc += NT) t1[cc] = shift_up_axis<1>(t0, cc, cinfo[4 * cc], !(oct & 2), W, dp.p);
         __syncthreads();
         const R* pl = psum + (l - 2) * ncoef;
         for (int cc = tid; cc < ncoef; cc += NT) {
             const int pk = cinfo[4 * cc];
-            f[cc] = pl[cc] + pow2neg<R>((pk >> 24) + 1) * shift_up_axis(t1, cc, pk, 2, !(oct & 4), W, dp.p);
+            f[cc] = pl[cc] + pow2neg<R>((pk >> 24) + 1) * shift_up_axis<2>(t1, cc, pk, !(oct & 4), W, dp.p);
         }
         __syncthreads();
     }
