@@ -99,6 +99,10 @@ typedef struct {
                             dipole.  FP64 mode only (in FP32 the pair's multipole cancels
                             catastrophically); dl must not exceed a quarter of the leaf side:
                             POLFMM_ERR_INVALID_ARG otherwise, at fmm_build or at a rebuild. */
+    int no_pdl;          /* 1: launch the kernels of a solver iteration with plain stream order
+                            instead of programmatic dependent launch (0, the default: each of
+                            them may be scheduled while its predecessor drains; it waits for the
+                            predecessor's completion before it reads that kernel's output) */
 } polfmm_options;
 
 /* Fill *opt with the defaults: FP64, PCG, max_iter 100, coulomb_k 1, bounding

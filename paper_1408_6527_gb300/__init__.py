@@ -69,7 +69,8 @@ class PolFMM:
     """One octree, its static pass and the induced dipoles (an opaque C context)."""
 
     def __init__(self, pos, q, alpha, p=6, depth=4, mode="fp64", solver="pcg", max_iter=100, coulomb_k=1.0,
-                 root_box=None, m2l="auto", profile=False, stream=None, graphs=True, dipole_dl=0.0):
+                 root_box=None, m2l="auto", profile=False, stream=None, graphs=True, dipole_dl=0.0,
+                 pdl=True):
         self.lib = _lib.load()
         self.device = _is_torch(pos) and pos.is_cuda
         self.n = int(pos.shape[0])
@@ -83,6 +84,7 @@ class PolFMM:
         opt.profile = int(bool(profile))
         opt.no_graphs = int(not graphs)
         opt.dipole_dl = float(dipole_dl)
+        opt.no_pdl = int(not pdl)
         if root_box is not None:
             opt.use_root_box = 1
             for d in range(3):

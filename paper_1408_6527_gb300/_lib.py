@@ -43,6 +43,7 @@ class Options(ctypes.Structure):
         ("cuda_stream", ctypes.c_void_p),
         ("no_graphs", ctypes.c_int),
         ("dipole_dl", ctypes.c_double),
+        ("no_pdl", ctypes.c_int),
     ]
 
 

@@ -308,7 +308,10 @@ __global__ void __launch_bounds__(kUpThreads) upward_kernel(
         }
         __syncthreads();
         const int par = s_next;
-        if (par < 0) return;
+        if (par < 0) {
+            pdl_launch_dependents();
+            return;
+        }
         __threadfence();
         const int c0 = up.child0[l - 1][par], nc = up.nchild[l - 1][par];
         const R* shc = reinterpret_cast<const R*>(up.Msh[l]);
@@ -320,6 +323,7 @@ __global__ void __launch_bounds__(kUpThreads) upward_kernel(
         }
         box = par;
     }
+    pdl_launch_dependents();
 }
 
 // ---------------------------------------------------------------------------
@@ -1225,6 +1229,9 @@ __global__ void __launch_bounds__(kL2PThreads) l2p_field_add_kernel(
     }
     stage_small(W, w4, p);
     stage_small(RI, rinv, p);
+    // launched after the M2L with programmatic serialization: its partials and
+    // the near field are complete from here on
+    pdl_wait();
     // the first site group's near field, alpha and d, read now so that their
     // latency hides behind the downward pass
     const int s0 = lstart[b], cnt = lcount[b];
@@ -1306,6 +1313,7 @@ __global__ void __launch_bounds__(kL2PThreads) l2p_field_add_kernel(
         }
         __syncthreads();
     }
+    pdl_launch_dependents();
     if (!pf.Ad) return;
     // leaf partial, then the last block adds all leaves in order
     for (int o = 16; o > 0; o >>= 1) dot += __shfl_down_sync(0xffffffffu, dot, o);
@@ -1537,9 +1545,9 @@ static bool pass_impl(polfmm_ctx* c, int mode, bool use_q, const double* mu_sort
         if (pcg)
             pf = PcgFuse{c->inv_alpha_s, c->d,      c->Ad, c->leaf_partial,
                          c->scal,    c->ticket, c->capturing_loop ? c->loop_cond : 0};
-        l2p_field_add_kernel<R><<<Lf.nbox, kL2PThreads, smem, c->stream>>>(
-            Lf.nbox, c->lstart, c->lcount, reinterpret_cast<const Q4<R>*>(c->srcA), down_ptrs(c), c->ld, c->ncoef,
-            c->p, T.mi, T.up1, pick<R>(T.w4, T.w4f), pick<R>(T.rinv, T.rinvf), h, E, pf);
+        launch_pdl(!c->opt.no_pdl, l2p_field_add_kernel<R>, dim3(Lf.nbox), dim3(kL2PThreads), smem, c->stream,
+                   Lf.nbox, c->lstart, c->lcount, reinterpret_cast<const Q4<R>*>(c->srcA), down_ptrs(c), c->ld,
+                   c->ncoef, c->p, T.mi, T.up1, pick<R>(T.w4, T.w4f), pick<R>(T.rinv, T.rinvf), h, E, pf);
         return pcg;
     }
     launch_leaf<R>(c, mode, mu_sorted, phi, E, G, mu_packed, c->stream, d >= 2 ? 1 : 0);

@@ -375,6 +375,36 @@ __host__ __device__ inline uint32_t morton3(uint32_t i, uint32_t j, uint32_t k) 
 
 inline int grid_for(int64_t n, int block) { return (int)((n + block - 1) / block); }
 
+// Programmatic dependent launch (the solver iteration's chain of kernels).
+// pdl_wait: a kernel launched with programmatic stream serialization waits here
+// until the previous kernel of its stream has completed and its writes are
+// visible (without the attribute it returns at once); nothing that kernel
+// writes may be read, and nothing it reads may be written, before this call.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+// lets the next kernel of the stream be scheduled; called by each block when
+// its work is done, so that waiting blocks never hold an SM this grid needs
+__device__ __forceinline__ void pdl_launch_dependents() {
+    asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+}
+
+// launch with programmatic stream serialization when pdl is set (the kernel
+// calls pdl_wait before touching its predecessor's output)
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(bool pdl, void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                              Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
 }  // namespace polfmm
 
 #define POLFMM_CUDA_TRY(expr)                         \

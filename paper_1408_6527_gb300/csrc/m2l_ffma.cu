@@ -294,6 +294,9 @@ __global__ void __launch_bounds__(kFfThreads, 2)
     const int* eoff = ent_off + (size_t)g * kNumOffsets;
     const int* esrc = ent_src + (size_t)g * kNumOffsets * kFfRows;
     float* stage0 = ff_smem + (size_t)pair * 2 * Dm::STAGE;
+    // launched after the upward pass with programmatic serialization: the
+    // multipoles are complete from here on
+    pdl_wait();
     // warp 2i takes the low-degree outputs of pair i, warp 2i + 1 the others
     if ((warp & 1) == 0)
         ff_warp<P, 0>(eoff, esrc, e_lo + pair, e_hi, stage0, Mall, Dpad, ld, pair, lane, ff_smem);
@@ -309,6 +312,7 @@ __global__ void __launch_bounds__(kFfThreads, 2)
         for (int w = 0; w < kFfPairs; w++) s += red[((size_t)w * kFfRows + r) * Dm::RS + nn];
         s_out[r][nn] = s;
     }
+    pdl_launch_dependents();
 }
 
 // ---------------------------------------------------------------------------
@@ -564,10 +568,9 @@ int m2l_ffma_prepare(polfmm_ctx* c) {
 
 template <int P>
 static void ff_launch(polfmm_ctx* c, FfState* S, const FfOut& out) {
-    dim3 grid(S->ngroups, c->m2l_chunks);
-    m2l_ffma_kernel<P><<<grid, kFfThreads, S->smem, c->stream>>>(S->groups, S->rows, S->ent_cnt, S->ent_off,
-                                                                  S->ent_src, (const float*)c->Mall, S->Dpad, out,
-                                                                  c->ld, c->m2l_chunks);
+    launch_pdl(!c->opt.no_pdl, m2l_ffma_kernel<P>, dim3(S->ngroups, c->m2l_chunks), dim3(kFfThreads), S->smem,
+               c->stream, S->groups, S->rows, S->ent_cnt, S->ent_off, S->ent_src, (const float*)c->Mall, S->Dpad,
+               out, c->ld, c->m2l_chunks);
 }
 
 void m2l_ffma_launch(polfmm_ctx* c) {

@@ -187,6 +187,7 @@ __global__ void pcg_update_kernel(int64_t n, const double* __restrict__ alpha, d
                                   int* __restrict__ ticket, cudaGraphConditionalHandle cond) {
     __shared__ double sh[kRedThreads];
     __shared__ double step_sh;
+    pdl_wait();  // d.Ad and Ad come from the kernel before
     const double dad = scal[S_DAD];
     const bool ok = dad > 0.0 && isfinite(dad);
     // one FP64 division per block, not per thread (FP64 is a narrow unit here)
@@ -235,6 +236,7 @@ __global__ void pcg_update_kernel(int64_t n, const double* __restrict__ alpha, d
             }
         }
     }
+    pdl_launch_dependents();
 }
 
 // solve-graph start: tolerance, iteration limit, iteration count
@@ -248,6 +250,7 @@ __global__ void loop_setup_kernel(double* __restrict__ scal, double tol, double 
 template <typename R>
 __global__ void pcg_direction_kernel(int64_t n, const double* __restrict__ scal, const double* __restrict__ z,
                                      double* __restrict__ d, void* __restrict__ packed, const int* __restrict__ slot) {
+    pdl_wait();  // beta and z come from the update kernel before
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
     const double beta = scal[S_BETA];
@@ -478,17 +481,17 @@ void solver_pcg_step(polfmm_ctx* c) {
     }
     {
         LaunchScope ls(c, F_SOLVER);
-        pcg_update_kernel<<<kRedBlocks, kRedThreads, 0, c->stream>>>(c->n, c->alpha_s, c->scal, c->d, c->Ad, c->mu,
-                                                                      c->r, c->z, c->partial, c->ticket, cond);
+        launch_pdl(!c->opt.no_pdl, pcg_update_kernel, dim3(kRedBlocks), dim3(kRedThreads), 0, c->stream, c->n,
+                   c->alpha_s, c->scal, c->d, c->Ad, c->mu, c->r, c->z, c->partial, c->ticket, cond);
     }
     {
         LaunchScope ls(c, F_SOLVER);
         if (c->mixed)
-            pcg_direction_kernel<float><<<grid_for(c->n, 256), 256, 0, c->stream>>>(c->n, c->scal, c->z, c->d,
-                                                                                    c->near_pairs, c->near_slot);
+            launch_pdl(!c->opt.no_pdl, pcg_direction_kernel<float>, dim3(grid_for(c->n, 256)), dim3(256), 0,
+                       c->stream, c->n, c->scal, c->z, c->d, (void*)c->near_pairs, (const int*)c->near_slot);
         else
-            pcg_direction_kernel<double><<<grid_for(c->n, 256), 256, 0, c->stream>>>(c->n, c->scal, c->z, c->d,
-                                                                                     c->srcB, nullptr);
+            launch_pdl(!c->opt.no_pdl, pcg_direction_kernel<double>, dim3(grid_for(c->n, 256)), dim3(256), 0,
+                       c->stream, c->n, c->scal, c->z, c->d, (void*)c->srcB, (const int*)nullptr);
     }
 }
 

@@ -388,6 +388,22 @@ def test_tensor_core_m2l_forces_within_gate(w2):
     assert max_site_err(outs["mixed"], outs["fp64"]) < MIXED_SITE_TOL
 
 
+def test_programmatic_launch_matches_stream_order(w2):
+    """The solver iteration's kernels with programmatic dependent launch (each
+    waits for its predecessor's completion before reading its output) give
+    bit-for-bit the same dipoles, energy and forces as plain stream order."""
+    res = {}
+    for pdl in (True, False):
+        with PolFMM(dev(w2.pos), dev(w2.q), dev(w2.alpha), p=w2.p, depth=w2.depth, mode="mixed", pdl=pdl) as f:
+            info = f.solve(1e-6)
+            out = f.energy_forces()
+            res[pdl] = (info["iterations"], host(f.dipoles()), float(out["U"]), host(out["F"]))
+    assert res[True][0] == res[False][0]
+    assert np.array_equal(res[True][1], res[False][1])
+    assert res[True][2] == res[False][2]
+    assert np.array_equal(res[True][3], res[False][3])
+
+
 def test_graph_replay_matches_direct_launches(w1):
     res = {}
     for graphs in (True, False):
