@@ -103,6 +103,14 @@ typedef struct {
                             instead of programmatic dependent launch (0, the default: each of
                             them may be scheduled while its predecessor drains; it waits for the
                             predecessor's completion before it reads that kernel's output) */
+    int dipole_tree;     /* 0 (default): one tree for everything.  1: the dipole solve runs on a
+                            second tree over the polarizable sites only (alpha > 0), T^mu of
+                            Sec. III: its depth is the given depth less log8(n / n_mu), rounded
+                            down; the field that polarizes the sites comes from the full tree,
+                            and the converged dipoles go back to it for the energy and forces.
+                            Exclusions (pairs of polarizable sites), Thole damping, the dipole
+                            predictor and set dipoles are passed on to it.  When every site (or
+                            none) is polarizable the two trees coincide and one is used. */
 } polfmm_options;
 
 /* Fill *opt with the defaults: FP64, PCG, max_iter 100, coulomb_k 1, bounding

@@ -70,7 +70,7 @@ class PolFMM:
 
     def __init__(self, pos, q, alpha, p=6, depth=4, mode="fp64", solver="pcg", max_iter=100, coulomb_k=1.0,
                  root_box=None, m2l="auto", profile=False, stream=None, graphs=True, dipole_dl=0.0,
-                 pdl=True):
+                 pdl=True, dipole_tree=False):
         self.lib = _lib.load()
         self.device = _is_torch(pos) and pos.is_cuda
         self.n = int(pos.shape[0])
@@ -85,6 +85,7 @@ class PolFMM:
         opt.no_graphs = int(not graphs)
         opt.dipole_dl = float(dipole_dl)
         opt.no_pdl = int(not pdl)
+        opt.dipole_tree = int(bool(dipole_tree))
         if root_box is not None:
             opt.use_root_box = 1
             for d in range(3):

@@ -44,6 +44,7 @@ class Options(ctypes.Structure):
         ("no_graphs", ctypes.c_int),
         ("dipole_dl", ctypes.c_double),
         ("no_pdl", ctypes.c_int),
+        ("dipole_tree", ctypes.c_int),
     ]
 
 

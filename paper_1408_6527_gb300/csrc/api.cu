@@ -31,6 +31,22 @@ __global__ void extrapolate_kernel(int64_t n3, double* __restrict__ cur, double*
     cur[k] = 2.0 * v - hist[k];
     hist[k] = v;
 }
+// rows of a caller-order array: dst[k] = src[rows[k]] (take) or dst[rows[k]] = src[k] (put),
+// comps values per row
+__global__ void take_rows_kernel(int64_t m, int comps, const int* __restrict__ rows, const double* __restrict__ src,
+                                 double* __restrict__ dst) {
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= m * comps) return;
+    const int64_t r = k / comps, c = k - r * comps;
+    dst[k] = src[(int64_t)rows[r] * comps + c];
+}
+__global__ void put_rows_kernel(int64_t m, int comps, const int* __restrict__ rows, const double* __restrict__ src,
+                                double* __restrict__ dst) {
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= m * comps) return;
+    const int64_t r = k / comps, c = k - r * comps;
+    dst[(int64_t)rows[r] * comps + c] = src[k];
+}
 int fmm_ops_init_attributes(polfmm_ctx* c);
 size_t m2l_simt_smem(int ncoef, size_t rsize);
 int m2l_tensor_prepare(polfmm_ctx* c);
@@ -320,6 +336,7 @@ struct CtxExtra {
     Alloc alloc;
     std::vector<void*> lp_bufs;
     size_t lp_cap_chunks = 0;
+    std::vector<int> tmu_index;  // caller index -> index in the dipole tree (-1: not polarizable)
 };
 
 CtxExtra* extra_of(polfmm_ctx* c) { return reinterpret_cast<CtxExtra*>(c->extra); }
@@ -504,6 +521,7 @@ struct FieldChargeSources {
 // charges q, and with field charges set those of the q^E, which polarize the
 // sites; every pass without the excluded pairs
 void static_passes(polfmm_ctx* c) {
+    if (c->dipole_only) return;  // a dipole tree: its field comes from the full tree
     fmm_pass(c, LEAF_CHARGE_PHI_E, true, nullptr, c->phiq, c->Eq, nullptr);
     if (c->qE_s) {
         FieldChargeSources fc(c);
@@ -683,6 +701,8 @@ int pcg_iteration(polfmm_ctx* c) {
 void destroy_impl(polfmm_ctx* c) {
     if (!c) return;
     cudaStreamSynchronize(c->stream);
+    if (c->tmu) destroy_impl(c->tmu);
+    c->tmu = nullptr;
     CtxExtra* X = extra_of(c);
     if (X) {
         for (void* p : X->alloc.ptrs) cudaFree(p);
@@ -734,9 +754,9 @@ void fmm_default_options(polfmm_options* o) {
     o->m2l_impl = POLFMM_M2L_AUTO;
 }
 
-int fmm_build(polfmm_ctx** out, int64_t n, const double* positions, const double* charges,
-              const double* polarizabilities, int order_p, int tree_depth, const polfmm_options* opt,
-              int inputs_on_device) {
+static int build_impl(polfmm_ctx** out, int64_t n, const double* positions, const double* charges,
+                      const double* polarizabilities, int order_p, int tree_depth, const polfmm_options* opt,
+                      int inputs_on_device, bool dipole_only) {
     if (!out) return POLFMM_ERR_INVALID_ARG;
     *out = nullptr;
     // 3 n must fit the 32-bit indices of the per-component solver loops
@@ -770,6 +790,7 @@ int fmm_build(polfmm_ctx** out, int64_t n, const double* positions, const double
         return POLFMM_ERR_OUT_OF_MEMORY;
     }
     c->opt = o;
+    c->dipole_only = dipole_only;
     c->n = n;
     c->p = order_p;
     c->depth = tree_depth;
@@ -814,8 +835,94 @@ int fmm_build(polfmm_ctx** out, int64_t n, const double* positions, const double
     return POLFMM_OK;
 }
 
+// the dipole solve's tree over the polarizable sites (T^mu of Sec. III)
+static int build_dipole_tree(polfmm_ctx* c) {
+    const int64_t n = c->n;
+    std::vector<double> a((size_t)n);
+    if (cudaMemcpyAsync(a.data(), c->in_buf + 4 * n, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(c->stream) != cudaSuccess)
+        return cuda_fail(cudaGetLastError(), "copy of the polarizabilities");
+    CtxExtra* X = extra_of(c);
+    X->tmu_index.assign((size_t)n, -1);
+    std::vector<int> rows;
+    for (int64_t i = 0; i < n; i++)
+        if (a[i] > 0.0) {
+            X->tmu_index[i] = (int)rows.size();
+            rows.push_back((int)i);
+        }
+    const int64_t m = (int64_t)rows.size();
+    if (m == 0 || m == n) return POLFMM_OK;  // the two trees would coincide (or there is nothing to solve)
+    Alloc& A = X->alloc;
+    c->mu_rows = A.get<int>(m);
+    c->tmu_caller = A.get<double>(std::max(3 * n, 5 * m));
+    c->tmu_rows = A.get<double>(3 * m);
+    if (!A.ok) return POLFMM_ERR_OUT_OF_MEMORY;
+    if (cudaMemcpyAsync(c->mu_rows, rows.data(), sizeof(int) * m, cudaMemcpyHostToDevice, c->stream) != cudaSuccess)
+        return cuda_fail(cudaGetLastError(), "upload of the polarizable sites");
+    c->nmu = m;
+    // positions and polarizabilities of those sites; no charges
+    double* xq = c->tmu_caller;  // 3 m positions, then m zeros, then m polarizabilities (m <= n - 1)
+    {
+        LaunchScope ls(c, F_TREE);
+        take_rows_kernel<<<grid_for(3 * m, 256), 256, 0, c->stream>>>(m, 3, c->mu_rows, c->in_buf, xq);
+        take_rows_kernel<<<grid_for(m, 256), 256, 0, c->stream>>>(m, 1, c->mu_rows, c->in_buf + 4 * n, xq + 4 * m);
+    }
+    cudaMemsetAsync(xq + 3 * m, 0, sizeof(double) * m, c->stream);
+    // depth less log8(n / m), rounded down
+    int depth = c->depth;
+    for (int64_t r = n / m; r >= 8 && depth > 1; r /= 8) depth--;
+    polfmm_options o = c->opt;
+    o.dipole_tree = 0;
+    polfmm_ctx* t = nullptr;
+    int rc = build_impl(&t, m, xq, xq + 3 * m, xq + 4 * m, c->p, depth, &o, 1, true);
+    if (rc != POLFMM_OK) return rc;
+    c->tmu = t;
+    return POLFMM_OK;
+}
+
+int fmm_build(polfmm_ctx** out, int64_t n, const double* positions, const double* charges,
+              const double* polarizabilities, int order_p, int tree_depth, const polfmm_options* opt,
+              int inputs_on_device) {
+    int rc = build_impl(out, n, positions, charges, polarizabilities, order_p, tree_depth, opt, inputs_on_device,
+                        false);
+    if (rc != POLFMM_OK || !(*out)->opt.dipole_tree) return rc;
+    if ((rc = build_dipole_tree(*out)) != POLFMM_OK) {
+        destroy_impl(*out);
+        *out = nullptr;
+    }
+    return rc;
+}
+
+// the solve on the dipole tree: its polarizing field from this tree, its dipoles
+// back to this tree (zero at the sites that are not polarizable)
+static int solve_on_dipole_tree(polfmm_ctx* c, double tol, int* iters_out, double* res_out) {
+    polfmm_ctx* t = c->tmu;
+    const int64_t m = c->nmu;
+    scatter_sites(c, polarizing_field(c), c->tmu_caller, 3);
+    {
+        LaunchScope ls(c, F_SOLVER);
+        take_rows_kernel<<<grid_for(3 * m, 256), 256, 0, c->stream>>>(m, 3, c->mu_rows, c->tmu_caller, c->tmu_rows);
+    }
+    gather_sites(t, c->tmu_rows, t->Eq, 3);
+    const int status = fmm_solve_induced_dipoles(t, tol, iters_out, res_out);
+    if (status != POLFMM_OK && status != POLFMM_ERR_NOT_CONVERGED) return status;
+    // dipoles back (the last good iterate when the solve did not converge)
+    scatter_sites(t, t->mu, c->tmu_rows, 3);
+    cudaMemsetAsync(c->tmu_caller, 0, sizeof(double) * 3 * c->n, c->stream);
+    {
+        LaunchScope ls(c, F_SOLVER);
+        put_rows_kernel<<<grid_for(3 * m, 256), 256, 0, c->stream>>>(m, 3, c->mu_rows, c->tmu_rows, c->tmu_caller);
+    }
+    gather_sites(c, c->tmu_caller, c->mu, 3);
+    c->have_mu = true;
+    int rc = read_err(c);
+    return rc != POLFMM_OK ? rc : status;
+}
+
 int fmm_solve_induced_dipoles(polfmm_ctx* c, double tol, int* iters_out, double* res_out) {
     if (!c || !(tol >= 0.0)) return POLFMM_ERR_INVALID_ARG;
+    if (c->tmu) return solve_on_dipole_tree(c, tol, iters_out, res_out);
     const bool jacobi = c->opt.solver == POLFMM_SOLVER_JACOBI;
     solver_init(c, c->have_mu);
     c->have_mu = true;
@@ -960,6 +1067,12 @@ int fmm_set_dipoles(polfmm_ctx* c, const double* mu, int on_device) {
     mask_dipoles(c, c->mu);
     c->have_mu = true;
     c->have_hist = false;  // the predictor's history restarts
+    if (c->tmu) {
+        LaunchScope ls(c, F_SOLVER);
+        take_rows_kernel<<<grid_for(3 * c->nmu, 256), 256, 0, c->stream>>>(c->nmu, 3, c->mu_rows, c->in_buf + 5 * c->n,
+                                                                           c->tmu_rows);
+        if ((rc = fmm_set_dipoles(c->tmu, c->tmu_rows, 1)) != POLFMM_OK) return rc;
+    }
     return read_err(c);
 }
 
@@ -967,7 +1080,7 @@ int fmm_reset_dipoles(polfmm_ctx* c) {
     if (!c) return POLFMM_ERR_INVALID_ARG;
     c->have_mu = false;
     c->have_hist = false;
-    return POLFMM_OK;
+    return c->tmu ? fmm_reset_dipoles(c->tmu) : POLFMM_OK;
 }
 
 int fmm_set_field_charges(polfmm_ctx* c, const double* qE, int on_device) {
@@ -1061,6 +1174,19 @@ int fmm_set_exclusions(polfmm_ctx* c, int64_t npairs, const int32_t* pairs, int 
     c->pcg_graph_dirty = true;  // the solver pass gains (or loses) the correction kernel
     c->loop_dirty = true;
     c->have_dqE = false;
+    if (c->tmu) {
+        // the dipole tree excludes the pairs of polarizable sites, in its own indices
+        const std::vector<int>& ix = extra_of(c)->tmu_index;
+        std::vector<int32_t> sub;
+        for (int64_t k = 0; k < npairs; k++) {
+            const int a = ix[h[2 * k]], b = ix[h[2 * k + 1]];
+            if (a >= 0 && b >= 0) {
+                sub.push_back(a);
+                sub.push_back(b);
+            }
+        }
+        if ((rc = fmm_set_exclusions(c->tmu, (int64_t)sub.size() / 2, sub.data(), 0)) != POLFMM_OK) return rc;
+    }
     return read_err(c);
 }
 
@@ -1076,7 +1202,7 @@ int fmm_set_dipole_predictor(polfmm_ctx* c, int order) {
     }
     c->predictor = order;
     c->have_hist = false;
-    return POLFMM_OK;
+    return c->tmu ? fmm_set_dipole_predictor(c->tmu, order) : POLFMM_OK;
 }
 
 int fmm_set_thole(polfmm_ctx* c, double a) {
@@ -1109,6 +1235,7 @@ int fmm_set_thole(polfmm_ctx* c, double a) {
     if (rc != POLFMM_OK) return rc;
     c->pcg_graph_dirty = true;  // the solver pass gains (or loses) the correction kernel
     c->loop_dirty = true;
+    if (c->tmu && (rc = fmm_set_thole(c->tmu, a)) != POLFMM_OK) return rc;
     return read_err(c);
 }
 
@@ -1147,6 +1274,14 @@ int fmm_update_positions(polfmm_ctx* c, const double* positions, int on_device) 
     if (c->have_mu) {
         gather_sites(c, c->in_buf + 5 * n, c->mu, 3);
         mask_dipoles(c, c->mu);
+    }
+    if (c->tmu) {
+        {
+            LaunchScope ls(c, F_TREE);
+            take_rows_kernel<<<grid_for(3 * c->nmu, 256), 256, 0, c->stream>>>(c->nmu, 3, c->mu_rows, c->in_buf,
+                                                                               c->tmu_rows);
+        }
+        if ((rc = fmm_update_positions(c->tmu, c->tmu_rows, 1)) != POLFMM_OK) return rc;
     }
     return read_err(c);
 }

@@ -261,6 +261,13 @@ struct polfmm_ctx {
     int64_t loop_launches = 0;             // kernel launches per iteration of the body
     void* tc = nullptr;           // tensor-core M2L state
     void* ff = nullptr;           // FP32 CUDA-core M2L state
+    // the dipole solve's own tree over the polarizable sites (T^mu, Sec. III)
+    polfmm_ctx* tmu = nullptr;
+    int64_t nmu = 0;              // its sites
+    int* mu_rows = nullptr;       // [nmu] caller index of each of them (device)
+    double* tmu_caller = nullptr; // [3 n] scratch in caller order
+    double* tmu_rows = nullptr;   // [3 nmu] scratch in the second tree's caller order
+    bool dipole_only = false;     // this context is such a tree: no charges, no static passes
     // profiling
     cudaEvent_t ev_pool[2 * 4096];
     int ev_used = 0;
