@@ -69,6 +69,11 @@ def parse():
     ap.add_argument("--mode", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
     ap.add_argument("--m2l", default="auto", choices=["auto", "simt", "tensor", "ffma"])
+    ap.add_argument("--pol-frac", type=float, default=1.0,
+                    help="fraction of the sites that keep their polarizability (a seeded random subset; the "
+                         "others get alpha = 0)")
+    ap.add_argument("--dipole-tree", action="store_true",
+                    help="solve for the dipoles on a second tree over the polarizable sites (Sec. III)")
     ap.add_argument("--workload", default="globule30k",
                     choices=["globule30k", "cube1k", "ring300k", "globule100k", "shell250k", "shell1M", "shell4M"],
                     help="workload (the default is the one the headline metric is quoted on)")
@@ -368,11 +373,24 @@ def job_value(world, n, steps, total_ms):
     return world * n * steps / (total_ms / 1e3)
 
 
-def make_workload(name):
+def workload_extra(args):
+    """The workload name's suffix for the polarizable fraction and the dipole tree."""
+    extra = f" pol_frac={args.pol_frac:g}" if args.pol_frac < 1.0 else ""
+    return extra + (" dipole_tree" if args.dipole_tree else "")
+
+
+def make_workload(name, pol_frac=1.0):
+    """The named workload; with pol_frac < 1 only that fraction of the sites (a
+    seeded random subset) keeps its polarizability, the others get alpha = 0."""
     import synth
 
     idx, n = WORKLOADS[name]
-    return synth.workload(idx, n=n)
+    w = synth.workload(idx, n=n)
+    if pol_frac < 1.0:
+        rng = np.random.Generator(np.random.PCG64(4242))
+        off = rng.random(w.n) >= pol_frac
+        w.alpha[off] = 0.0
+    return w
 
 
 def run_gpu(args, rank, world, local_rank):
@@ -385,7 +403,7 @@ def run_gpu(args, rank, world, local_rank):
     dist = world > 1
     if dist:
         import torch.distributed as tdist
-    w = make_workload(args.workload)
+    w = make_workload(args.workload, args.pol_frac)
     n = w.n
     dev = lambda a: torch.as_tensor(a, dtype=torch.float64, device="cuda")
     pos_d, q_d, a_d = dev(w.pos), dev(w.q), dev(w.alpha)
@@ -395,7 +413,7 @@ def run_gpu(args, rank, world, local_rank):
     def make(mode, src=None, profile=False, max_iter=500):
         s = src if src is not None else (pos_d, q_d, a_d)
         return PolFMM(*s, p=w.p, depth=w.depth, mode=mode, max_iter=max_iter, m2l=args.m2l, profile=profile,
-                      graphs=not args.no_graphs)
+                      graphs=not args.no_graphs, dipole_tree=args.dipole_tree)
 
     def step(ctx, mode, pos, tol=None):
         ctx.update_positions(pos)
@@ -547,7 +565,8 @@ def run_gpu(args, rank, world, local_rank):
 
     # e2e: the same step through the public API with pinned host buffers
     pos_h = torch.from_numpy(w.pos.copy()).pin_memory()
-    ctxh = PolFMM(w.pos, w.q, w.alpha, p=w.p, depth=w.depth, mode=args.mode, max_iter=500, m2l=args.m2l)
+    ctxh = PolFMM(w.pos, w.q, w.alpha, p=w.p, depth=w.depth, mode=args.mode, max_iter=500, m2l=args.m2l,
+                  dipole_tree=args.dipole_tree)
     for _ in range(args.warmup):
         step(ctxh, args.mode, pos_h)
     e2e_s = 0.0
@@ -565,7 +584,8 @@ def run_gpu(args, rank, world, local_rank):
         "metric": METRIC, "value": round(value, 1), "unit": "atoms/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64" if args.mode == "mixed" else "f64", "data": "synthetic",
-        "config": {"workload": f"{w.name} {n} sites p={w.p} depth={w.depth} {args.mode}", "n_sites": n, "p": w.p,
+        "config": {"workload": f"{w.name} {n} sites p={w.p} depth={w.depth} {args.mode}" + workload_extra(args),
+                   "n_sites": n, "p": w.p,
                    "depth": w.depth, "mode": args.mode, "tol": tol_for(args.mode, n), "m2l": args.m2l,
                    "parallelism": "replicas" if world > 1 else "single",
                    "l2": "flushed before every step (256 MB write, outside the step interval)"},
@@ -627,7 +647,7 @@ def run_reference(args):
     import synth
     import oracle
 
-    w = make_workload(args.workload)
+    w = make_workload(args.workload, args.pol_frac)
     lo, side = oracle.root_box(w.pos)
     tol = tol_for(args.mode, w.n)
     for _ in range(args.warmup):
@@ -644,7 +664,7 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": round(value, 2), "unit": "atoms/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * total / args.steps, 2),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"{w.name} {w.n} sites p={w.p} depth={w.depth} {args.mode}", "n_sites": w.n,
+        "config": {"workload": f"{w.name} {w.n} sites p={w.p} depth={w.depth} {args.mode}" + workload_extra(args), "n_sites": w.n,
                    "p": w.p, "depth": w.depth, "mode": args.mode, "tol": tol},
         "cpu_baseline": {"value": round(value, 2), "unit": "atoms/s", "cores": cores, "kind": "oracle",
                          "sample": "each step one complete oracle step of the full workload"},
