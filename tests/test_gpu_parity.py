@@ -330,9 +330,9 @@ def test_tensor_core_m2l_matches_simt(case, w1, w2):
 # FP32 CUDA-core multipole-to-local (MIXED, p <= 6) against SIMT and FP64
 # ---------------------------------------------------------------------------
 
-@pytest.mark.parametrize("case", ["p2", "p3", "small", "cube", "globule", "deep"])
+@pytest.mark.parametrize("case", ["p1", "p2", "p3", "small", "cube", "globule", "deep"])
 def test_ffma_m2l_matches_simt(case, w1, w2):
-    if case in ("p2", "p3"):
+    if case in ("p1", "p2", "p3"):
         pos, q, alpha = synth.small_random(43, 500, box=16.0)
         p, depth = int(case[1]), 3
     elif case == "small":
