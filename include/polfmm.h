@@ -314,7 +314,9 @@ POLFMM_API int fmm_root_box(polfmm_ctx* ctx, double* lo, double* side);
 POLFMM_API int fmm_profile_get(polfmm_ctx* ctx, const char* family, double* total_ms, int64_t* launches);
 POLFMM_API int fmm_profile_reset(polfmm_ctx* ctx);
 
-/* Count of the library's own kernel launches on this context since creation. */
+/* Count of the library's own kernel launches on this context since creation
+ * (with polfmm_options.dipole_tree, those of its dipole tree included; the
+ * same holds for fmm_profile_get and fmm_profile_reset). */
 POLFMM_API int64_t fmm_launch_count(polfmm_ctx* ctx);
 
 /*

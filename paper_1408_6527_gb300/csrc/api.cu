@@ -1354,8 +1354,12 @@ int fmm_profile_get(polfmm_ctx* c, const char* family, double* total_ms, int64_t
     profile_flush(c);
     for (int f = 0; f < F_COUNT; f++)
         if (!strcmp(family, names[f])) {
-            if (total_ms) *total_ms = c->prof_ms[f];
-            if (launches) *launches = c->prof_n[f];
+            // with a dipole tree, its kernels count with the context's
+            double t_ms = 0.0;
+            int64_t t_n = 0;
+            if (c->tmu) fmm_profile_get(c->tmu, family, &t_ms, &t_n);
+            if (total_ms) *total_ms = c->prof_ms[f] + t_ms;
+            if (launches) *launches = c->prof_n[f] + t_n;
             return POLFMM_OK;
         }
     return POLFMM_ERR_INVALID_ARG;
@@ -1368,10 +1372,10 @@ int fmm_profile_reset(polfmm_ctx* c) {
         c->prof_ms[f] = 0;
         c->prof_n[f] = 0;
     }
-    return POLFMM_OK;
+    return c->tmu ? fmm_profile_reset(c->tmu) : POLFMM_OK;
 }
 
-int64_t fmm_launch_count(polfmm_ctx* c) { return c ? c->launches : 0; }
+int64_t fmm_launch_count(polfmm_ctx* c) { return c ? c->launches + fmm_launch_count(c->tmu) : 0; }
 
 int64_t fmm_testing_alloc_hook(int64_t fail_at) {
     const int64_t made = g_alloc_count.exchange(0);

@@ -117,3 +117,24 @@ def test_tree_work_counts_ffma_entries_by_brute_force():
             grp = rows[k][g:g + 32]
             total += sum(any(tuple(t[a] - o[a] for a in range(3)) in occ[l] for l, t in grp) for o in offs)
     assert entries == total
+
+
+def test_polarizable_fraction_workload():
+    """--pol-frac keeps alpha on a seeded random subset of about that fraction
+    of the sites and zeroes it elsewhere; positions and charges are unchanged."""
+    full = bench.make_workload("cube1k")
+    w = bench.make_workload("cube1k", 0.3)
+    again = bench.make_workload("cube1k", 0.3)
+    kept = w.alpha > 0
+    assert abs(kept.mean() - 0.3) < 0.05
+    assert np.array_equal(w.alpha[kept], full.alpha[kept]) and np.all(w.alpha[~kept] == 0.0)
+    assert np.array_equal(w.pos, full.pos) and np.array_equal(w.q, full.q)
+    assert np.array_equal(again.alpha, w.alpha)
+
+
+def test_workload_name_carries_the_options():
+    class A:
+        pol_frac, dipole_tree = 1.0, False
+    assert bench.workload_extra(A) == ""
+    A.pol_frac, A.dipole_tree = 0.3, True
+    assert bench.workload_extra(A) == " pol_frac=0.3 dipole_tree"
