@@ -329,6 +329,18 @@ POLFMM_API int64_t fmm_launch_count(polfmm_ctx* ctx);
 POLFMM_API int64_t fmm_testing_alloc_hook(int64_t fail_at);
 
 /*
+ * Testing: the schedule the FP32 CUDA-core M2L (MIXED, p <= 6) is compiled
+ * with, for checks on the CPU.  For order p and part (0: the warp with the
+ * outputs of degree <= split, 1: the warp with the others) it writes up to cap
+ * terms of L_n += D_k M_m in execution order: n (relative to the part's first
+ * output), m and k = index of n + m in the coefficient order, and load = 1
+ * where the term's float4 of D is loaded.  Returns the part's term count, and
+ * through split_out (if not NULL) the degree split; -1 for p outside 1..6 or
+ * a part other than 0, 1.  Host only, no device work.
+ */
+POLFMM_API int fmm_testing_m2l_plan(int p, int part, int cap, int* n, int* m, int* k, int* load, int* split_out);
+
+/*
  * Allocation-free tree set-up.  The paper has no counterpart: this entry point
  * exists for callers that cannot call cudaMalloc -- code whose host framework
  * owns all device memory through its own pool, or a time-critical loop that

@@ -81,6 +81,7 @@ SIGNATURES = {
     "fmm_profile_reset": (I, [P]),
     "fmm_launch_count": (I64, [P]),
     "fmm_testing_alloc_hook": (I64, [I64]),
+    "fmm_testing_m2l_plan": (I, [I, I, I, P, P, P, P, P]),
     "fmm_measure_peak": (I, [I, P, ctypes.POINTER(D)]),
     "fmm_kdtree_fields": (I, [I64, P, P, P, I, D, I, I, D, D, P, P, P, P, P, I]),
     "fmm_wall_create": (I, [ctypes.POINTER(P), I64, P]),

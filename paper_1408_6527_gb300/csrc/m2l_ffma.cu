@@ -602,3 +602,40 @@ void m2l_ffma_release(polfmm_ctx* c) {
 }
 
 }  // namespace polfmm
+
+// ---------------------------------------------------------------------------
+// the compiled schedule, for checks on the CPU
+// ---------------------------------------------------------------------------
+namespace {
+template <int P, int PART>
+int ff_plan_copy(int cap, int* n, int* m, int* k, int* load) {
+    constexpr const polfmm::FfPlan<P, PART>& pl = polfmm::kFfPlan<P, PART>;
+    const int nt = polfmm::FfPlan<P, PART>::NT;
+    for (int e = 0; e < nt && e < cap; e++) {
+        if (n) n[e] = pl.n[e];
+        if (m) m[e] = pl.m[e];
+        if (k) k[e] = pl.k[e];
+        if (load) load[e] = pl.load[e] ? 1 : 0;
+    }
+    return nt;
+}
+
+template <int P>
+int ff_plan_part(int part, int cap, int* n, int* m, int* k, int* load) {
+    return part == 0 ? ff_plan_copy<P, 0>(cap, n, m, k, load) : ff_plan_copy<P, 1>(cap, n, m, k, load);
+}
+}  // namespace
+
+extern "C" POLFMM_API int fmm_testing_m2l_plan(int p, int part, int cap, int* n, int* m, int* k, int* load,
+                                                int* split_out) {
+    if (p < 1 || p > polfmm::kFfMaxP || (part != 0 && part != 1)) return -1;
+    if (split_out) *split_out = polfmm::ff_split(p);
+    switch (p) {
+        case 1: return ff_plan_part<1>(part, cap, n, m, k, load);
+        case 2: return ff_plan_part<2>(part, cap, n, m, k, load);
+        case 3: return ff_plan_part<3>(part, cap, n, m, k, load);
+        case 4: return ff_plan_part<4>(part, cap, n, m, k, load);
+        case 5: return ff_plan_part<5>(part, cap, n, m, k, load);
+        default: return ff_plan_part<6>(part, cap, n, m, k, load);
+    }
+}
